@@ -1,0 +1,212 @@
+/*
+ * tacauchy.h -- C ABI of the GB300 (sm_103a) TaCauchy hot-path library.
+ *
+ * One implicit step of a tetrahedral hyperelastic gel pad under
+ * incremental-potential contact (IPC) with a rigid indenter, followed by the
+ * paper's stress extraction:
+ *   - Sec. III-B: Lame parameters (Eq. 1), stable Neo-Hookean material (Eq. 2),
+ *     IPC barrier distance dhat, at most 1024 Newton iterations per step;
+ *   - Sec. III-C: Cauchy stress per tet (Eq. 3, Eq. 4), traction t = sigma n
+ *     (Eq. 5-6), normal pressure (Eq. 7), tangential traction (Eq. 8),
+ *     Algorithm 1 (surface extraction + per-face decomposition);
+ *   - Algorithm 2: the simulation loop (step, stress, traction, contact force
+ *     f_k = -g_k / dt^2).
+ *
+ * Conventions
+ *   - Units are SI (metres, pascals, newtons, seconds).
+ *   - Every call returns tc_status (0 = TC_OK); nothing aborts or throws
+ *     across the ABI.  Device-side failures are collected in a per-env status
+ *     word and reported by the call that observes them.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the env's device (for example PyTorch tensors).
+ *     Caller-owned buffers are only read or written during the call
+ *     (device outputs: enqueued on the env's stream, complete when the call
+ *     returns because every public call synchronises that stream).
+ *   - The library owns all env state; it stays resident on the device between
+ *     calls.  Inputs are copied at create time.
+ *   - An env may be used by one host thread at a time.
+ *   - Sizes are counts of elements, not bytes.
+ */
+#ifndef TACAUCHY_H
+#define TACAUCHY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tc_status;
+enum {
+  TC_OK = 0,
+  TC_ERR_INVALID_ARG = 1,          /* null pointer, negative size, bad enum    */
+  TC_ERR_INVALID_MESH = 2,         /* tet with det(Dm) <= 0, index out of range */
+  TC_ERR_INITIAL_PENETRATION = 3,  /* indenter touches or crosses the gel      */
+  TC_ERR_NEWTON_MAXITER = 4,       /* Newton (or indenter substeps) hit the cap */
+  TC_ERR_PCG_MAXITER = 5,          /* reserved: PCG stops at pcg_max silently   */
+  TC_ERR_LINESEARCH = 6,           /* no energy decrease after 60 halvings     */
+  TC_ERR_NONFINITE = 7,            /* NaN/Inf in a pose, energy or direction   */
+  TC_ERR_CUDA = 8,                 /* a CUDA runtime call failed               */
+  TC_ERR_OOM = 9,                  /* device allocation failed                 */
+  TC_ERR_ADMISSION = 10,           /* serving: env does not fit the HBM budget */
+  TC_ERR_TIMEOUT = 11,             /* serving: wait ran out                    */
+  TC_ERR_CAPACITY = 12             /* an internal fixed-size table overflowed  */
+};
+
+enum { TC_FP64 = 0, TC_FP32_MIXED = 1 };
+
+/* Gel mesh (Algorithm 1 input (V, T)).  X: host, nv x 3 row-major rest
+ * positions; tets: host, nt x 4 vertex ids, positively oriented
+ * (det[X1-X0, X2-X0, X3-X0] > 0, else TC_ERR_INVALID_MESH). */
+typedef struct { const double* X; int32_t nv; const int32_t* tets; int32_t nt; } tc_mesh;
+
+/* Material (Sec. III-B, Eq. 1).  Young's modulus E (Pa), Poisson ratio nu in
+ * (-1, 0.5), density (kg/m^3, used only when dt > 0). */
+typedef struct { double E, nu, density; } tc_material;
+
+/* Solver options.
+ *   dhat        IPC barrier distance (m), Sec. III-B.
+ *   kappa       barrier stiffness (N/m); <= 0 selects E * mean rest length of
+ *               the contact-surface edges.
+ *   dt          time step (s); <= 0 selects the quasi-static problem.
+ *   newton_rtol Newton stops when |g| <= newton_rtol * |g_0| (g_0: gradient at
+ *               the first iterate of each indenter substep), or when
+ *               |g| <= 1e-12 E L^2, or when the Newton step's max-norm is
+ *               <= 1e-4 dhat (TC_FP64) / 1e-3 dhat (TC_FP32_MIXED), or when
+ *               that step is below 10x those bounds and its predicted energy
+ *               decrease is below the rounding level of the energy (1e-14 |E|
+ *               in FP64, 1e-7 |E| in FP32 mixed).
+ *   newton_max  Newton iterations per substep (1024 in Sec. III-B).
+ *   pcg_max     PCG iterations per Newton iteration.
+ *   precision   TC_FP64 (all device arithmetic in double) or TC_FP32_MIXED
+ *               (element, barrier, PCG in float; energies, line-search and
+ *               PCG dot-product accumulators in double; barrier distance in
+ *               double for pairs closer than 1e-2 dhat).
+ *   contact_axis thickness axis 0/1/2; -1 = thinnest bounding-box axis
+ *               (Sec. III-A). */
+typedef struct {
+  double dhat, kappa, dt, newton_rtol;
+  int32_t newton_max, pcg_max, precision, contact_axis;
+} tc_scene_opts;
+
+/* Rigid indenter surface in its body frame.  V: host nv x 3; F: host nf x 3. */
+typedef struct { const double* V; int32_t nv; const int32_t* F; int32_t nf; } tc_trimesh;
+
+/* Rigid pose: world = R * body + t, R row-major 3 x 3 (a rotation). */
+typedef struct { double R[9]; double t[3]; } tc_pose;
+
+/* Sensor pixel grid in the rest contact plane.  Pixel (r, c) has its centre
+ * at (origin[0] + (c + 1/2) pixel[0], origin[1] + (r + 1/2) pixel[1]) in the
+ * (axis_u, axis_v) coordinates of the rest configuration.  Coordinates are
+ * snapped to whole nanometres for binning. */
+typedef struct { int32_t axis_u, axis_v; double origin[2], pixel[2]; int32_t H, W; } tc_grid;
+
+/* Optional device-memory provider (for example a PyTorch caching allocator).
+ * alloc returns a device pointer aligned to 256 bytes or NULL; free releases
+ * it.  With a NULL tc_allocator the library uses cudaMallocAsync/cudaFreeAsync
+ * on the env's stream. */
+typedef struct {
+  void* (*alloc)(void* ctx, size_t bytes, void* stream);
+  void (*release)(void* ctx, void* ptr, size_t bytes, void* stream);
+  void* ctx;
+} tc_allocator;
+
+typedef struct tc_env tc_env;
+
+/* Counts and counters of an env (host struct filled by tc_env_info). */
+typedef struct {
+  int32_t nv, nt;            /* gel vertices, tets                          */
+  int32_t nf;                /* boundary faces (Algorithm 1, step 2)        */
+  int32_t nfc, nec, nvc;     /* contact faces, edges, vertices              */
+  int32_t ind_nv, ind_nf, ind_ne;
+  int32_t H, W;              /* pixel grid                                   */
+  int64_t newton_iters, pcg_iters, substeps, steps, line_search_halvings;
+  double kappa;              /* barrier stiffness in use (N/m)              */
+  size_t device_bytes;       /* device memory held by the env               */
+} tc_info;
+
+/* Scene setup (row a0): rest shape Dm^-1 and volumes, lumped masses, boundary
+ * faces with parent tets, contact band and contact surface, vertex/face
+ * incidence, pixel binning, indenter grid.  fixed: host, nfixed vertex ids
+ * held at their rest positions.  start_pose: indenter pose at time 0 (must not
+ * touch the gel: TC_ERR_INITIAL_PENETRATION).  grid may be NULL (no pressure
+ * map).  cuda_stream: cudaStream_t the env's work is enqueued on (NULL = the
+ * legacy default stream).  On success *out owns a new env. */
+tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material,
+                          const int32_t* fixed, int32_t nfixed,
+                          const tc_trimesh* indenter, const tc_pose* start_pose,
+                          const tc_scene_opts* opts, const tc_grid* grid,
+                          const tc_allocator* allocator, void* cuda_stream,
+                          tc_env** out);
+
+/* One step (Algorithm 2, physics line): move the indenter from its current
+ * pose to *target in CCD-limited substeps and minimise the incremental
+ * potential of the gel at each substep. */
+tc_status tc_step(tc_env* env, const tc_pose* target);
+
+/* Cauchy stress per tet (Eq. 4 with the rest-stable reading):
+ * sigma_out device float 6 x nt, component-major (component k of tet e at
+ * k * nt + e), components in the order (xx, yy, zz, xy, yz, zx). */
+tc_status tc_stress(tc_env* env, float* sigma_out);
+
+/* Algorithm 1 per contact face (in tc_surface_faces order): traction
+ * t = sigma n (device float 3 x nfc, component-major), pressure
+ * p = -n.sigma.n (compression positive; Eq. 7's p_n = -p) (device float nfc),
+ * tangential traction t_tau = t - (t.n) n (Eq. 8) (device float 3 x nfc).
+ * n is the unit outward normal of the deformed face.  Any pointer may be NULL
+ * to skip that output. */
+tc_status tc_traction(tc_env* env, float* t, float* p, float* t_tau);
+
+/* Pressure map: per-face pressure area-weighted to contact vertices (deformed
+ * areas), interpolated barycentrically at every pixel of the grid given at
+ * create time.  out: device float H x W; mask: device uint8 H x W (1 = pixel
+ * covered by a contact face) or NULL. */
+tc_status tc_pressure_map(tc_env* env, float* out, uint8_t* mask);
+
+/* Total contact force on the gel, sum_k f_k with f_k = -kappa dB/dx_k
+ * (Algorithm 2: f_k = -g_k / dt^2).  out: host double[3]. */
+tc_status tc_contact_force(tc_env* env, double* out);
+
+/* Contact faces (Algorithm 1, steps 1-3, restricted to the contact band):
+ * faces host int32 nfc x 3 (outward winding, smallest id first, ordered by
+ * sorted vertex triple), parent host int32 nfc.  Either may be NULL. */
+tc_status tc_surface_faces(tc_env* env, int32_t* faces, int32_t* parent);
+
+/* All boundary faces and parents (host int32 nf x 3 and nf), same order rules. */
+tc_status tc_boundary_faces(tc_env* env, int32_t* faces, int32_t* parent);
+
+/* Pixel binning table: face index per pixel (-1 = uncovered) host int32 H*W,
+ * barycentric weights host float H*W x 3.  Either may be NULL. */
+tc_status tc_pixel_table(tc_env* env, int32_t* pix_face, float* pix_w);
+
+/* Current gel positions, host double nv x 3 (get) / set (for evaluating the
+ * extraction on externally supplied positions). */
+tc_status tc_get_positions(tc_env* env, double* x);
+tc_status tc_set_positions(tc_env* env, const double* x);
+
+tc_status tc_env_info(tc_env* env, tc_info* info);
+
+/* Per-kernel timing with CUDA events on the env's stream (off by default).
+ * on != 0 enables it and clears the totals; on == 0 disables it.  While on,
+ * every kernel an API call launches for this env is bracketed by two events
+ * (a small launch overhead).  tc_profile_read fills up to max entries
+ * (kernel name, total milliseconds, launches) and sets *n to the number of
+ * distinct kernels seen. */
+typedef struct { char name[32]; double ms; int64_t launches; } tc_kernel_time;
+tc_status tc_profile_enable(tc_env* env, int32_t on);
+tc_status tc_profile_read(tc_env* env, tc_kernel_time* out, int32_t max, int32_t* n);
+void tc_destroy(tc_env* env);
+const char* tc_status_str(tc_status s);
+
+/* Standalone stress kernel over deformation gradients (no env): sigma of
+ * Eq. 4 (rest-stable reading) for n tets.  F: device float n x 9 (one
+ * row-major 3 x 3 matrix per tet); sigma_out: device float 6 x n,
+ * component-major as in tc_stress; stream: cudaStream_t or NULL. */
+tc_status tc_stress_from_F(const float* F, int64_t n, double E, double nu,
+                           float* sigma_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACAUCHY_H */

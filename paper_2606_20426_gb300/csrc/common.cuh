@@ -1,0 +1,203 @@
+// Shared device helpers for the TaCauchy sm_103a kernels.
+//
+// R is the compute type of a kernel (float in TC_FP32_MIXED, double in
+// TC_FP64); every reduction accumulates in double.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tacauchy.h"
+
+#define TC_HD __host__ __device__ __forceinline__
+#define TC_D __device__ __forceinline__
+
+namespace tc {
+
+constexpr int kBlock = 256;  // threads per block of the streaming kernels
+constexpr int kWarp = 32;
+
+// Device status bits, OR-ed into Scalars::status by kernels.
+enum : int {
+  ST_NONFINITE = 1,
+  ST_INVALID_MESH = 2,
+  ST_CAPACITY = 4,
+  ST_PENETRATION = 8,
+};
+
+// Per-env device scalars (one struct in device memory).
+struct Scalars {
+  double energy;       // last evaluated total energy
+  double gnorm2;       // |g_free|^2
+  double rz, rz_next;  // PCG r.z (current, and the value of the next iteration)
+  double pq;           // PCG p.(A p)
+  double rr;           // PCG r.r
+  double pcg_tol2;     // (eta |g|)^2
+  double pmax;         // max-norm of the Newton direction
+  double ccd_t;        // conservative fraction of the motion (min over pairs)
+  double reduce_tmp[8];
+  double force[3];     // contact force accumulator
+  int status;          // ST_* bits
+  int pcg_done;        // set when |r| <= tol
+  int pcg_iters;       // iterations taken by the last solve
+  int overflow;        // grid/pair capacity overflow
+};
+
+template <class R> struct Vec3 {
+  R x, y, z;
+};
+
+template <class R> TC_HD Vec3<R> v3(R x, R y, R z) { return Vec3<R>{x, y, z}; }
+template <class R> TC_HD Vec3<R> operator+(Vec3<R> a, Vec3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> TC_HD Vec3<R> operator-(Vec3<R> a, Vec3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R> TC_HD Vec3<R> operator*(R s, Vec3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class R> TC_HD R dot(Vec3<R> a, Vec3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R> TC_HD Vec3<R> cross(Vec3<R> a, Vec3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <class R> TC_HD R& at(Vec3<R>& a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
+
+// SoA triple of arrays (x, y, z components).
+template <class R> struct SoA3 {
+  R* x;
+  R* y;
+  R* z;
+  TC_HD Vec3<R> get(int64_t i) const { return {x[i], y[i], z[i]}; }
+  TC_HD void set(int64_t i, Vec3<R> v) const { x[i] = v.x; y[i] = v.y; z[i] = v.z; }
+};
+
+// ---------------------------------------------------------------- reductions
+
+TC_D double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+TC_D double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+TC_D double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block sum of one double per thread; result valid in thread 0.
+// Fixed combination order -> deterministic.
+template <int NT> TC_D double block_sum(double v) {
+  __shared__ double s[NT / kWarp];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s[w] = v;
+  __syncthreads();
+  double r = 0.0;
+  if (w == 0) {
+    r = lane < NT / kWarp ? s[lane] : 0.0;
+    r = warp_sum(r);
+  }
+  __syncthreads();
+  return r;
+}
+template <int NT> TC_D double block_max(double v) {
+  __shared__ double s[NT / kWarp];
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s[w] = v;
+  __syncthreads();
+  double r = -1e308;
+  if (w == 0) {
+    r = lane < NT / kWarp ? s[lane] : -1e308;
+    r = warp_max(r);
+  }
+  __syncthreads();
+  return r;
+}
+template <int NT> TC_D double block_min(double v) {
+  __shared__ double s[NT / kWarp];
+  v = warp_min(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) s[w] = v;
+  __syncthreads();
+  double r = 1e308;
+  if (w == 0) {
+    r = lane < NT / kWarp ? s[lane] : 1e308;
+    r = warp_min(r);
+  }
+  __syncthreads();
+  return r;
+}
+
+inline unsigned grid_for(int64_t n, int nt = kBlock) {
+  int64_t b = (n + nt - 1) / nt;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------- symmetric eigen (Jacobi)
+
+// Cyclic Jacobi on a symmetric N x N matrix A (row-major, overwritten by its
+// eigenvalues on the diagonal); Q receives the eigenvectors as columns.
+template <class R, int N> TC_D void jacobi_eig(R* A, R* Q, int sweeps) {
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) Q[i * N + j] = (i == j) ? R(1) : R(0);
+  for (int s = 0; s < sweeps; ++s) {
+    R off = 0, diag = 0;
+    for (int i = 0; i < N; ++i) {
+      diag += A[i * N + i] * A[i * N + i];
+      for (int j = i + 1; j < N; ++j) off += A[i * N + j] * A[i * N + j];
+    }
+    if (!(off > R(1e-30) * diag) || off == R(0)) break;
+    for (int p = 0; p < N - 1; ++p) {
+      for (int q = p + 1; q < N; ++q) {
+        const R apq = A[p * N + q];
+        if (apq == R(0)) continue;
+        const R theta = (A[q * N + q] - A[p * N + p]) / (R(2) * apq);
+        const R t = (theta >= R(0) ? R(1) : R(-1)) / (fabs(theta) + sqrt(theta * theta + R(1)));
+        const R c = R(1) / sqrt(t * t + R(1));
+        const R sn = t * c;
+        for (int k = 0; k < N; ++k) {  // columns p, q
+          const R akp = A[k * N + p], akq = A[k * N + q];
+          A[k * N + p] = c * akp - sn * akq;
+          A[k * N + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < N; ++k) {  // rows p, q
+          const R apk = A[p * N + k], aqk = A[q * N + k];
+          A[p * N + k] = c * apk - sn * aqk;
+          A[q * N + k] = sn * apk + c * aqk;
+        }
+        for (int k = 0; k < N; ++k) {
+          const R qkp = Q[k * N + p], qkq = Q[k * N + q];
+          Q[k * N + p] = c * qkp - sn * qkq;
+          Q[k * N + q] = sn * qkp + c * qkq;
+        }
+      }
+    }
+  }
+}
+
+// Replace symmetric A (N x N, row-major) by its projection onto the PSD cone
+// (negative eigenvalues clamped to zero).
+template <class R, int N> TC_D void project_psd(R* A) {
+  R Q[N * N];
+  R W[N * N];
+  for (int i = 0; i < N * N; ++i) W[i] = A[i];
+  jacobi_eig<R, N>(W, Q, sizeof(R) == 4 ? 12 : 20);
+  for (int i = 0; i < N; ++i)
+    for (int j = i; j < N; ++j) {
+      R s = 0;
+      for (int k = 0; k < N; ++k) {
+        const R lk = W[k * N + k];
+        if (lk > R(0)) s += Q[i * N + k] * lk * Q[j * N + k];
+      }
+      A[i * N + j] = s;
+      A[j * N + i] = s;
+    }
+}
+
+// Index of (i, j), i <= j, in packed upper-triangular storage of an N x N
+// symmetric matrix (row-major upper triangle).
+TC_HD int sym_index(int i, int j, int N) {
+  if (i > j) { int t = i; i = j; j = t; }
+  return i * N - (i * (i - 1)) / 2 + (j - i);
+}
+
+TC_D bool finite_d(double v) { return isfinite(v); }
+
+}  // namespace tc

@@ -1,0 +1,557 @@
+// Contact (K2 query, K3 barrier, K6 CCD, K11 force).
+//
+// The indenter is rigid, so its primitives are binned once, in its body
+// frame, into a uniform grid (built at scene setup).  Every Newton iteration
+// each gel contact primitive (vertex, edge, face) maps its points into the
+// body frame, walks the grid cells its padded box overlaps, and visits each
+// indenter primitive once (in the cell holding the low corner of the
+// intersection of the two boxes).  The pairs are
+//   gel vertex  - indenter triangle   (point-triangle, gel slot 0)
+//   gel face    - indenter vertex     (point-triangle, gel slots 1, 2, 3)
+//   gel edge    - indenter edge       (edge-edge, gel slots 0, 1, mollified)
+// and every pair with d < dhat contributes kappa * b(d) (Li et al. 2020).
+//
+// Precision: the body-frame coordinates of a pair are formed in FP64
+// relative to the primitive's first gel point and rounded once, so the pair
+// arithmetic runs in the kernel type R on small numbers; pairs closer than
+// 1e-2 dhat are redone in FP64.
+//
+// Hessian: each pair adds kappa J^T [d2f]_+ J, where f is the barrier as a
+// function of the distance d (and, for edge-edge pairs, of the mollifier
+// argument c), J stacks the gradients of d and c on the gel points, and
+// [.]_+ clamps the 1x1 or 2x2 Hessian of f to PSD in closed form.  This is
+// PSD by construction and needs no eigensolver; it drops the curvature of
+// d itself, which only changes the Newton path, not the minimiser.
+//
+// One thread owns one gel primitive and sums its pairs in registers, so the
+// result per primitive is deterministic and the per-vertex assembly needs no
+// atomics.
+#include "env.cuh"
+#include "geom.cuh"
+#include "prof.cuh"
+
+namespace tc {
+
+TC_D void to_body(const double* Rm, const double* tr, const double* x, double* b) {
+  const double dx = x[0] - tr[0], dy = x[1] - tr[1], dz = x[2] - tr[2];
+  b[0] = Rm[0] * dx + Rm[3] * dy + Rm[6] * dz;
+  b[1] = Rm[1] * dx + Rm[4] * dy + Rm[7] * dz;
+  b[2] = Rm[2] * dx + Rm[5] * dy + Rm[8] * dz;
+}
+
+// gel primitive kinds
+enum { GV = 0, GE = 1, GF = 2 };
+// indenter primitive kind queried by each gel kind: vertex->faces, edge->edges, face->vertices
+TC_HD int ind_kind_for(int gk) { return gk == GV ? 2 : (gk == GE ? 1 : 0); }
+
+template <class R> TC_D int prim_count(const EnvView<R>& e, int gk) { return gk == GV ? e.nvc : (gk == GE ? e.nec : e.nfc); }
+
+template <class R> TC_D int gel_vertex(const EnvView<R>& e, int gk, int prim, int l) {
+  if (gk == GV) return e.cverts[prim];
+  if (gk == GE) return e.cedges[l * e.nec + prim];
+  return e.cfaces[l * e.nfc + prim];
+}
+
+template <class R> TC_D void gel_world(const EnvView<R>& e, const R* u, int v, double* x) {
+  for (int d = 0; d < 3; ++d) x[d] = e.X0[d * e.nv + v] + (double)u[d * e.nv + v];
+}
+
+template <class R> TC_D int ind_vertex(const EnvView<R>& e, int ik, int prim, int l) {
+  if (ik == 0) return prim;
+  if (ik == 1) return e.IE[l * e.ind_ne + prim];
+  return e.IF[l * e.ind_nf + prim];
+}
+
+// Origin of a primitive's local frame (its first gel point, body frame) in
+// FP64 and as an FP32 hi/lo pair.
+struct Origin {
+  double d[3];
+  float hi[3], lo[3];
+};
+
+TC_D Origin make_origin(const double* o) {
+  Origin r;
+  for (int k = 0; k < 3; ++k) {
+    r.d[k] = o[k];
+    r.hi[k] = __double2float_rn(o[k]);
+    r.lo[k] = __double2float_rn(o[k] - (double)r.hi[k]);
+  }
+  return r;
+}
+
+// indenter vertex v in the body frame relative to the origin: FP64
+// difference rounded once (double path), or the same difference formed from
+// FP32 hi/lo pairs without FP64 instructions (float path; both hi parts are
+// close to each other, so hi - hi is exact)
+template <class T, class R> TC_D Vec3<T> ind_rel(const EnvView<R>& e, int v, const Origin& o) {
+  const int n = e.ind_nv;
+  if constexpr (sizeof(T) == 4) {
+    return v3<T>((e.IVhi[v] - o.hi[0]) + (e.IVlo[v] - o.lo[0]), (e.IVhi[n + v] - o.hi[1]) + (e.IVlo[n + v] - o.lo[1]),
+                 (e.IVhi[2 * n + v] - o.hi[2]) + (e.IVlo[2 * n + v] - o.lo[2]));
+  } else {
+    return v3<T>((T)(e.IV[v] - o.d[0]), (T)(e.IV[n + v] - o.d[1]), (T)(e.IV[2 * n + v] - o.d[2]));
+  }
+}
+
+template <class T> TC_D Vec3<T> rel(const double* b, const double* o) {
+  return v3<T>((T)(b[0] - o[0]), (T)(b[1] - o[1]), (T)(b[2] - o[2]));
+}
+
+// Visit the indenter primitives of kind ik whose boxes overlap the FP32
+// body-frame query box [lo, hi]; f(prim) is called once per primitive.
+template <class R, class F> TC_D void grid_visit(const EnvView<R>& e, int ik, const float* lo, const float* hi, F f) {
+  const GridView& g = e.grid;
+  const float cell = 1.0f / g.inv_cell;
+  for (int d = 0; d < 3; ++d)
+    if (hi[d] < g.org[d] || lo[d] > g.org[d] + g.dims[d] * cell) return;
+  int c0[3], c1[3];
+  for (int d = 0; d < 3; ++d) {
+    c0[d] = grid_cell(lo[d], g.org[d], g.inv_cell, g.dims[d]);
+    c1[d] = grid_cell(hi[d], g.org[d], g.inv_cell, g.dims[d]);
+  }
+  const int32_t* start = g.start[ik];
+  const int32_t* items = g.items[ik];
+  const float* box = g.box[ik];
+  for (int z = c0[2]; z <= c1[2]; ++z)
+    for (int y = c0[1]; y <= c1[1]; ++y)
+      for (int x = c0[0]; x <= c1[0]; ++x) {
+        const int cell_id = x + g.dims[0] * (y + g.dims[1] * z);
+        const int k1 = start[cell_id + 1];
+        for (int k = start[cell_id]; k < k1; ++k) {
+          const int p = items[k];
+          const float* b = box + 6 * (int64_t)p;
+          if (b[0] > hi[0] || b[1] > hi[1] || b[2] > hi[2] || b[3] < lo[0] || b[4] < lo[1] || b[5] < lo[2]) continue;
+          // visit in the cell of the low corner of the intersection box
+          if (grid_cell(fmaxf(lo[0], b[0]), g.org[0], g.inv_cell, g.dims[0]) != x ||
+              grid_cell(fmaxf(lo[1], b[1]), g.org[1], g.inv_cell, g.dims[1]) != y ||
+              grid_cell(fmaxf(lo[2], b[2]), g.org[2], g.inv_cell, g.dims[2]) != z)
+            continue;
+          f(p);
+        }
+      }
+}
+
+// Mollifier of an edge-edge pair in its dimensionless argument
+// t = c / eps_x, c = |(x1-x0) x (x3-x2)|^2: m(t) = (2 - t) t for t < 1, its
+// first two derivatives in t, and grad t on the gel edge (points 0, 1).
+// Working in t keeps every factor in range (1/eps_x^2 overflows FP32).
+template <class T> TC_D void mollifier_t(const Vec3<T>* x, T eps_x, T* m, T* mt, T* mtt, T* gt) {
+  const Vec3<T> u = x[1] - x[0], v = x[3] - x[2];
+  const T uu = dot(u, u), vv = dot(v, v), uv = dot(u, v);
+  const T c = uu * vv - uv * uv;
+  const T t = c / eps_x;
+  if (!(t < T(1))) {
+    *m = T(1);
+    *mt = *mtt = T(0);
+    for (int i = 0; i < 6; ++i) gt[i] = T(0);
+    return;
+  }
+  *m = (T(2) - t) * t;
+  *mt = T(2) - T(2) * t;
+  *mtt = T(-2);
+  const T s = T(2) / eps_x;
+  const T gu[3] = {s * (vv * u.x - uv * v.x), s * (vv * u.y - uv * v.y), s * (vv * u.z - uv * v.z)};
+  for (int j = 0; j < 3; ++j) {
+    gt[j] = -gu[j];
+    gt[3 + j] = gu[j];
+  }
+}
+
+// Barrier of one pair in arithmetic T.  Adds kappa * grad to g[NG] and the
+// PSD Gauss-Newton block to the packed upper triangle Hp[NG(NG+1)/2].
+template <class T, int NG>
+TC_D T pair_gn(int kind, const Vec3<T>* x, const int* gs, T dhat, T kappa, bool ee, T eps_x, bool hess, T* g,
+               T* Hp) {
+  int which;
+  const T d2 = pair_dist2<T>(kind, x, &which);
+  const T d = sqrt(d2);
+  if (!(d < dhat) || !(d > T(0)) || which < 0) return T(0);
+  T b, b1, b2;
+  barrier3<T>(d, dhat, &b, &b1, &b2);
+  T m = T(1), mt = T(0), mtt = T(0);
+  T gt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+  if (NG == 6 && ee) mollifier_t<T>(x, eps_x, &m, &mt, &mtt, gt);
+  if (!hess) return kappa * m * b;
+  const CandEval<T> ev = eval_cand<T>(kind == 0 ? c_pt_cand[which] : c_ee_cand[which], x);
+  const T id = T(1) / d;
+  T gd[NG];
+#pragma unroll
+  for (int s = 0; s < NG / 3; ++s) {
+    const T w = ev.w[gs[s]] * id;
+    gd[3 * s + 0] = w * ev.r.x;
+    gd[3 * s + 1] = w * ev.r.y;
+    gd[3 * s + 2] = w * ev.r.z;
+  }
+  if (NG == 6 && ee && mt != T(0)) {
+    // f(d, t) = m(t) b(d): 2x2 Hessian in (d, t), clamped to PSD
+    const T a = m * b2, bb = mt * b1, c = mtt * b;
+    const T tr = T(0.5) * (a + c), df = T(0.5) * (a - c);
+    const T disc = sqrt(df * df + bb * bb);
+    const T l1 = tr + disc, l2 = tr - disc;
+    T P00 = T(0), P01 = T(0), P11 = T(0);
+    if (disc > T(0)) {
+      // unit eigenvector of l1: (l1 - c, bb), or (bb, l1 - a) when that vanishes
+      T v1x = df + disc, v1y = bb;
+      if (fabs(v1x) + fabs(v1y) == T(0)) { v1x = bb; v1y = disc - df; }
+      const T nv = sqrt(v1x * v1x + v1y * v1y);
+      v1x /= nv;
+      v1y /= nv;
+      const T v2x = -v1y, v2y = v1x;
+      const T L1 = l1 > T(0) ? l1 : T(0), L2 = l2 > T(0) ? l2 : T(0);
+      P00 = L1 * v1x * v1x + L2 * v2x * v2x;
+      P01 = L1 * v1x * v1y + L2 * v2x * v2y;
+      P11 = L1 * v1y * v1y + L2 * v2y * v2y;
+    } else {
+      P00 = a > T(0) ? a : T(0);
+      P11 = c > T(0) ? c : T(0);
+    }
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      g[i] += kappa * (m * b1 * gd[i] + mt * b * gt[i]);
+#pragma unroll
+      for (int j = i; j < NG; ++j)
+        Hp[idx++] += kappa * (P00 * gd[i] * gd[j] + P01 * (gd[i] * gt[j] + gt[i] * gd[j]) + P11 * gt[i] * gt[j]);
+    }
+  } else {
+    const T s1 = kappa * m * b1, s2 = kappa * m * (b2 > T(0) ? b2 : T(0));
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < NG; ++i) {
+      g[i] += s1 * gd[i];
+#pragma unroll
+      for (int j = i; j < NG; ++j) Hp[idx++] += s2 * gd[i] * gd[j];
+    }
+  }
+  return kappa * m * b;
+}
+
+// Pair points of gel primitive gk with indenter primitive ip, relative to o.
+template <class T, class R, int GK>
+TC_D void pair_points(const EnvView<R>& e, const Vec3<T>* xg, int ip, const Origin& o, Vec3<T>* x) {
+  constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
+  if (GK == GV) {
+    x[0] = xg[0];
+    for (int l = 0; l < 3; ++l) x[1 + l] = ind_rel<T>(e, ind_vertex(e, ik, ip, l), o);
+  } else if (GK == GF) {
+    x[0] = ind_rel<T>(e, ip, o);
+    for (int l = 0; l < 3; ++l) x[1 + l] = xg[l];
+  } else {
+    x[0] = xg[0];
+    x[1] = xg[1];
+    for (int l = 0; l < 2; ++l) x[2 + l] = ind_rel<T>(e, ind_vertex(e, ik, ip, l), o);
+  }
+}
+
+// One contact primitive pass over the candidate lists built by the last CCD
+// pass.  MODE 0: energy only; 1: energy + slots.
+template <class R, int GK, int MODE>
+__global__ void __launch_bounds__(128) k_contact(const EnvView<R> e, const R* __restrict__ u, double* part_out) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  constexpr int NG = 3 * NGP;
+  constexpr int NH = NG * (NG + 1) / 2;
+  const int prim = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = prim_count(e, GK);
+  double energy = 0.0;
+  double dmin2 = 1e300;
+  if (prim < n) {
+    double bw[3][3];
+    for (int l = 0; l < NGP; ++l) {
+      double w[3];
+      gel_world(e, u, gel_vertex(e, GK, prim, l), w);
+      to_body(e.Rm, e.tr, w, bw[l]);
+    }
+    const Origin o = make_origin(bw[0]);
+    Vec3<R> xg[NGP];
+    for (int l = 0; l < NGP; ++l) xg[l] = rel<R>(bw[l], o.d);
+    R gacc[NG];
+    R hacc[NH];
+#pragma unroll
+    for (int a = 0; a < NG; ++a) gacc[a] = R(0);
+#pragma unroll
+    for (int a = 0; a < NH; ++a) hacc[a] = R(0);
+    const int kind = GK == GE ? 1 : 0;
+    int gs[3];
+    if (GK == GV) { gs[0] = 0; gs[1] = 0; gs[2] = 0; }
+    else if (GK == GE) { gs[0] = 0; gs[1] = 1; gs[2] = 0; }
+    else { gs[0] = 1; gs[1] = 2; gs[2] = 3; }
+    const double eps_base = GK == GE ? 1e-3 * e.gel_elen2[prim] : 0.0;
+    const R dhat2 = (R)(e.dhat * e.dhat);
+    const int32_t* cl = e.cand[GK];
+    const int nc = min(e.cand_n[GK][prim], e.cand_cap);
+    for (int j = 0; j < nc; ++j) {
+      const int ip = cl[(int64_t)j * n + prim];
+      Vec3<R> x[4];
+      pair_points<R, R, GK>(e, xg, ip, o, x);
+      const R d2 = pair_dist2<R>(kind, x, nullptr);
+      dmin2 = fmin(dmin2, (double)d2);
+      if (!(d2 < dhat2)) continue;
+      const double eps_x = GK == GE ? eps_base * e.ind_elen2[ip] : 0.0;
+      if (sizeof(R) == 4 && d2 < (R)(1e-4 * e.dhat * e.dhat)) {  // FP64 island for very close pairs
+        Vec3<double> xgd[NGP];
+        for (int l = 0; l < NGP; ++l) xgd[l] = rel<double>(bw[l], o.d);
+        Vec3<double> xd[4];
+        pair_points<double, R, GK>(e, xgd, ip, o, xd);
+        double gp[NG], hp[NH];
+        for (int a = 0; a < NG; ++a) gp[a] = 0.0;
+        for (int a = 0; a < NH; ++a) hp[a] = 0.0;
+        energy += pair_gn<double, NG>(kind, xd, gs, e.dhat, e.kappa, GK == GE, eps_x, MODE == 1, gp, hp);
+        if (MODE == 1) {
+          for (int a = 0; a < NG; ++a) gacc[a] += (R)gp[a];
+          for (int a = 0; a < NH; ++a) hacc[a] += (R)hp[a];
+        }
+      } else {
+        energy += (double)pair_gn<R, NG>(kind, x, gs, (R)e.dhat, (R)e.kappa, GK == GE, (R)eps_x, MODE == 1, gacc, hacc);
+      }
+    }
+    if (MODE == 1) {
+      // body -> world: g_w = R g_b per point, H_w = R H_b R^T per 3x3 block
+      R Rm[9];
+      for (int k = 0; k < 9; ++k) Rm[k] = (R)e.Rm[k];
+      R* slot = GK == GV ? e.cv_slot : (GK == GE ? e.ce_slot : e.cf_slot);
+      for (int l = 0; l < NGP; ++l)
+        for (int i = 0; i < 3; ++i) {
+          R s = 0;
+          for (int k = 0; k < 3; ++k) s += Rm[3 * i + k] * gacc[3 * l + k];
+          slot[(int64_t)(3 * l + i) * n + prim] = s;
+        }
+      for (int la = 0; la < NGP; ++la)
+        for (int lb = la; lb < NGP; ++lb) {
+          R B[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) B[i][j] = hacc[sym_index(3 * la + i, 3 * lb + j, NG)];
+          R T1[3][3];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) T1[i][j] = Rm[3 * i + 0] * B[0][j] + Rm[3 * i + 1] * B[1][j] + Rm[3 * i + 2] * B[2][j];
+          for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+              const int ra = 3 * la + i, cb = 3 * lb + j;
+              if (ra > cb) continue;  // packed upper triangle
+              const R v = T1[i][0] * Rm[3 * j + 0] + T1[i][1] * Rm[3 * j + 1] + T1[i][2] * Rm[3 * j + 2];
+              slot[(int64_t)(NG + sym_index(ra, cb, NG)) * n + prim] = v;
+            }
+        }
+    }
+  }
+  energy = block_sum<128>(energy);
+  dmin2 = block_min<128>(dmin2);
+  if (threadIdx.x == 0) {
+    part_out[2 * blockIdx.x] = energy;
+    part_out[2 * blockIdx.x + 1] = dmin2;
+  }
+}
+
+template <class R> struct ContactGrid {
+  static unsigned blocks(int n) { return (unsigned)std::max(1, (n + 127) / 128); }
+};
+
+// Partials layout in e.part: [elem blocks][contact V][contact E][contact F],
+// each contact block writing (energy, dmin2).
+template <class R> void launch_contact(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s) {
+  const unsigned bv = ContactGrid<R>::blocks(e.nvc), be = ContactGrid<R>::blocks(e.nec), bf = ContactGrid<R>::blocks(e.nfc);
+  double* base = e.part + grid_for(e.nt);
+  if (with_hessian) {
+    TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<bv, 128, 0, s>>>(e, u_eval, base));
+    TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<be, 128, 0, s>>>(e, u_eval, base + 2 * bv));
+    TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<bf, 128, 0, s>>>(e, u_eval, base + 2 * (bv + be)));
+  } else {
+    TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<bv, 128, 0, s>>>(e, u_eval, base));
+    TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<be, 128, 0, s>>>(e, u_eval, base + 2 * bv));
+    TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<bf, 128, 0, s>>>(e, u_eval, base + 2 * (bv + be)));
+  }
+}
+
+// ------------------------------------------------------------------- CCD
+// Gel points move linearly in the indenter's body frame from b0 to b1 (the
+// indenter is static there); additive CCD per candidate pair in type R on
+// coordinates relative to the primitive's first gel point.
+
+struct Motion {
+  double Ra[9], ta[3], Rb[9], tb[3];
+};
+
+template <class R, int GK>
+__global__ void __launch_bounds__(128) k_ccd(const EnvView<R> e, const R* __restrict__ dir, const Motion mo,
+                                            double* part_out) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
+  const int prim = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = prim_count(e, GK);
+  double tmin = 1.0;
+  if (prim < n) {
+    double b0[3][3], b1[3][3];
+    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+    for (int l = 0; l < NGP; ++l) {
+      const int v = gel_vertex(e, GK, prim, l);
+      double w[3];
+      gel_world(e, e.u, v, w);
+      to_body(mo.Ra, mo.ta, w, b0[l]);
+      if (dir)
+        for (int d = 0; d < 3; ++d) w[d] += (double)dir[d * e.nv + v];
+      to_body(mo.Rb, mo.tb, w, b1[l]);
+      for (int d = 0; d < 3; ++d) {
+        lo[d] = fminf(lo[d], __double2float_rd(fmin(b0[l][d], b1[l][d]) - e.dhat));
+        hi[d] = fmaxf(hi[d], __double2float_ru(fmax(b0[l][d], b1[l][d]) + e.dhat));
+      }
+    }
+    const Origin o = make_origin(b0[0]);
+    Vec3<R> xg[NGP], pg[NGP];
+    for (int l = 0; l < NGP; ++l) {
+      xg[l] = rel<R>(b0[l], o.d);
+      pg[l] = rel<R>(b1[l], b0[l]);
+    }
+    const int kind = GK == GE ? 1 : 0;
+    int32_t* cl = e.cand[GK];
+    int cnt = 0;
+    grid_visit<R>(e, ik, lo, hi, [&](int ip) {
+      // every pair the swept boxes admit is a candidate for the contact and
+      // energy passes until the next CCD pass
+      if (cnt < e.cand_cap) cl[(int64_t)cnt * n + prim] = ip;
+      ++cnt;
+      Vec3<R> x0[4], p[4];
+      pair_points<R, R, GK>(e, xg, ip, o, x0);
+      const Vec3<R> zero = v3<R>(0, 0, 0);
+      if (GK == GV) {
+        p[0] = pg[0];
+        p[1] = p[2] = p[3] = zero;
+      } else if (GK == GF) {
+        p[0] = zero;
+        for (int l = 0; l < 3; ++l) p[1 + l] = pg[l];
+      } else {
+        p[0] = pg[0];
+        p[1] = pg[1];
+        p[2] = p[3] = zero;
+      }
+      const R t = accd<R>(kind, x0, p, (R)1.0, 4096);
+      tmin = fmin(tmin, (double)t);
+    });
+    e.cand_n[GK][prim] = cnt;
+    if (cnt > e.cand_cap) atomicMax(&e.sc->overflow, cnt);
+  }
+  tmin = block_min<128>(tmin);
+  if (threadIdx.x == 0) part_out[blockIdx.x] = tmin;
+}
+
+__global__ void k_min_partials(const double* part, int n, double* out) {
+  double m = 1.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, part[i]);
+  m = block_min<kBlock>(m);
+  if (threadIdx.x == 0) *out = m;
+}
+
+template <class R>
+void launch_ccd(const EnvView<R>& e, const R* dir, const double* Ra, const double* ta, const double* Rb, const double* tb,
+                cudaStream_t s) {
+  const unsigned bv = ContactGrid<R>::blocks(e.nvc), be = ContactGrid<R>::blocks(e.nec), bf = ContactGrid<R>::blocks(e.nfc);
+  double* base = e.part;
+  Motion mo;
+  for (int k = 0; k < 9; ++k) { mo.Ra[k] = Ra[k]; mo.Rb[k] = Rb[k]; }
+  for (int k = 0; k < 3; ++k) { mo.ta[k] = ta[k]; mo.tb[k] = tb[k]; }
+  TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<bv, 128, 0, s>>>(e, dir, mo, base));
+  TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<be, 128, 0, s>>>(e, dir, mo, base + bv));
+  TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<bf, 128, 0, s>>>(e, dir, mo, base + bv + be));
+  TC_LAUNCH("k_min_partials", s, k_min_partials<<<1, kBlock, 0, s>>>(base, (int)(bv + be + bf), &e.sc->ccd_t));
+}
+
+// ------------------------------------------------------------ contact force
+// f = -sum over all gel points of the barrier gradient (Algorithm 2:
+// f_k = -g_k / dt^2 with the potential scaled by dt^2).
+template <class R>
+__global__ void k_force(const EnvView<R> e, double* out) {
+  double f[3] = {0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nvc + e.nec + e.nfc; i += gridDim.x * blockDim.x) {
+    if (i < e.nvc) {
+      for (int d = 0; d < 3; ++d) f[d] -= (double)e.cv_slot[(int64_t)d * e.nvc + i];
+    } else if (i < e.nvc + e.nec) {
+      const int p = i - e.nvc;
+      for (int l = 0; l < 2; ++l)
+        for (int d = 0; d < 3; ++d) f[d] -= (double)e.ce_slot[(int64_t)(3 * l + d) * e.nec + p];
+    } else {
+      const int p = i - e.nvc - e.nec;
+      for (int l = 0; l < 3; ++l)
+        for (int d = 0; d < 3; ++d) f[d] -= (double)e.cf_slot[(int64_t)(3 * l + d) * e.nfc + p];
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    const double s = block_sum<kBlock>(f[d]);
+    if (threadIdx.x == 0) out[d] = s;
+  }
+}
+
+template <class R> void launch_contact_force(const EnvView<R>& e, cudaStream_t s) {
+  TC_LAUNCH("k_force", s, k_force<R><<<1, kBlock, 0, s>>>(e, e.sc->force));
+}
+
+// ------------------------------------------------------ intersection test
+// Closed segment vs triangle with orientation signs in FP64 (used once, to
+// reject a start pose where the indenter already crosses the gel surface).
+
+TC_D double orient3(const double* a, const double* b, const double* c, const double* d) {
+  const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  const double v[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  const double w[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+  return u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) + u[2] * (v[0] * w[1] - v[1] * w[0]);
+}
+
+TC_D bool seg_tri(const double* a, const double* b, const double* p0, const double* p1, const double* p2) {
+  const double sa = orient3(p0, p1, p2, a), sb = orient3(p0, p1, p2, b);
+  const bool straddle = (sa <= 0 && sb >= 0) || (sa >= 0 && sb <= 0);
+  if (!straddle || (sa == 0 && sb == 0)) return false;
+  const double s0 = orient3(a, b, p0, p1), s1 = orient3(a, b, p1, p2), s2 = orient3(a, b, p2, p0);
+  return (s0 >= 0 && s1 >= 0 && s2 >= 0) || (s0 <= 0 && s1 <= 0 && s2 <= 0);
+}
+
+template <class R, int GK>
+__global__ void k_intersect(const EnvView<R> e, int* flag) {
+  // GK == GE: gel edges vs indenter faces; GK == GF: gel faces vs indenter edges
+  constexpr int NGP = GK == GE ? 2 : 3;
+  const int prim = blockIdx.x * blockDim.x + threadIdx.x;
+  if (prim >= prim_count(e, GK)) return;
+  double gw[3][3];
+  float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
+  for (int l = 0; l < NGP; ++l) {
+    gel_world(e, e.u, gel_vertex(e, GK, prim, l), gw[l]);
+    double b[3];
+    to_body(e.Rm, e.tr, gw[l], b);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], __double2float_rd(b[d]));
+      hi[d] = fmaxf(hi[d], __double2float_ru(b[d]));
+    }
+  }
+  const int ik = GK == GE ? 2 : 1;
+  grid_visit<R>(e, ik, lo, hi, [&](int ip) {
+    double w[3][3];
+    const int nI = GK == GE ? 3 : 2;
+    for (int l = 0; l < nI; ++l) {
+      const int v = ind_vertex(e, ik, ip, l);
+      const double yb[3] = {e.IV[v], e.IV[e.ind_nv + v], e.IV[2 * e.ind_nv + v]};
+      for (int i = 0; i < 3; ++i)
+        w[l][i] = e.Rm[3 * i] * yb[0] + e.Rm[3 * i + 1] * yb[1] + e.Rm[3 * i + 2] * yb[2] + e.tr[i];
+    }
+    const bool hit = GK == GE ? seg_tri(gw[0], gw[1], w[0], w[1], w[2]) : seg_tri(w[0], w[1], gw[0], gw[1], gw[2]);
+    if (hit) atomicOr(flag, 1);
+  });
+}
+
+template <class R> int intersect_test(const EnvView<R>& e, int* dflag, cudaStream_t s) {
+  cudaMemsetAsync(dflag, 0, sizeof(int), s);
+  TC_LAUNCH("k_intersect", s, k_intersect<R, GE><<<ContactGrid<R>::blocks(e.nec), 128, 0, s>>>(e, dflag));
+  TC_LAUNCH("k_intersect", s, k_intersect<R, GF><<<ContactGrid<R>::blocks(e.nfc), 128, 0, s>>>(e, dflag));
+  int h = 0;
+  cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return h;
+}
+
+template void launch_contact<float>(const EnvView<float>&, bool, const float*, cudaStream_t);
+template void launch_contact<double>(const EnvView<double>&, bool, const double*, cudaStream_t);
+template void launch_ccd<float>(const EnvView<float>&, const float*, const double*, const double*, const double*,
+                                const double*, cudaStream_t);
+template void launch_ccd<double>(const EnvView<double>&, const double*, const double*, const double*, const double*,
+                                 const double*, cudaStream_t);
+template void launch_contact_force<float>(const EnvView<float>&, cudaStream_t);
+template void launch_contact_force<double>(const EnvView<double>&, cudaStream_t);
+template int intersect_test<float>(const EnvView<float>&, int*, cudaStream_t);
+template int intersect_test<double>(const EnvView<double>&, int*, cudaStream_t);
+
+}  // namespace tc

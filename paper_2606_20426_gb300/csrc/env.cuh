@@ -1,0 +1,247 @@
+// Device layout of one environment (gel pad + rigid indenter + pixel grid).
+//
+// Everything is structure-of-arrays in HBM so that per-tet and per-vertex
+// passes are coalesced:
+//   per tet   : tets (int4), Dm^-1 (9 x nt), vol, H9 (45 x nt, PSD dP/dF),
+//               eslot (36 x nt: 12 gradient + 24 diagonal-block entries),
+//               yslot (12 x nt: element share of H p in PCG)
+//   per vertex: rest X (double, 3 x nv), displacement u, velocity v, Newton
+//               and PCG vectors (3 x nv each), block-Jacobi inverse (6 x nv)
+//   contact   : gel contact vertices / edges / faces with per-primitive
+//               slots (gradient + packed symmetric Hessian block) filled by
+//               the barrier kernels and gathered per vertex
+//   indenter  : body-frame vertices (double), faces, edges, uniform grid
+//   pixels    : covering face + barycentric weights per pixel
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "prims.cuh"
+#include "prof.cuh"
+
+namespace tc {
+
+// Uniform grid over the indenter's body-frame bounding box.  Boxes are FP32,
+// rounded outward from the FP64 geometry, and cells are computed with
+// grid_cell() both when binning and when querying, so every query visits
+// exactly the cells a primitive was binned into.
+struct GridView {
+  float org[3];
+  float inv_cell;
+  int dims[3];
+  const int32_t* start[3];   // per primitive kind (0 vert, 1 edge, 2 face): ncells + 1
+  const int32_t* items[3];   // primitive ids, ascending within a cell
+  const float* box[3];       // per primitive body-frame AABB (lo xyz, hi xyz)
+};
+
+TC_HD int grid_cell(float x, float org, float inv_cell, int dim) {
+  const float f = floorf((x - org) * inv_cell);
+  int c = f < 0.f ? 0 : (f >= (float)dim ? dim - 1 : (int)f);
+  return c;
+}
+
+// Everything a kernel needs, passed by value.
+template <class R> struct EnvView {
+  int nv, nt, nfc, nec, nvc, ind_nv, ind_nf, ind_ne, npix;
+  R mu, lam_hat, alpha;       // material (rest-stable Neo-Hookean)
+  R inv_h2;                   // 1/dt^2 (dynamic) or 0
+  double dhat, kappa;
+  // topology
+  const int4* tets;
+  const double* X0;           // rest positions, SoA x|y|z, each nv
+  const uint8_t* fixed;       // 1 = fixed vertex
+  const int32_t* vt_off;      // vertex -> (tet*4+corner), CSR
+  const int32_t* vt_idx;
+  // per tet
+  const R* Dminv;             // 9 x nt (row-major entry k at k*nt + e)
+  const R* vol;
+  R* H9;                      // 45 x nt packed upper triangle of PSD dP/dF
+  R* eslot;                   // 36 x nt
+  R* yslot;                   // 12 x nt
+  // per vertex
+  const R* mass;              // nv (dynamic) or null
+  R* u;                       // 3 x nv displacement
+  const R* utilde;            // 3 x nv (dynamic)
+  R* g;                       // 3 x nv gradient
+  R* Minv;                    // 6 x nv block-Jacobi inverse (xx,yy,zz,xy,yz,zx)
+  R *dx, *r, *z, *p, *q;      // 3 x nv PCG vectors
+  // contact surface
+  const int32_t* cverts;      // nvc vertex ids
+  const int32_t* cedges;      // 2 x nec
+  const int32_t* cfaces;      // 3 x nfc vertex ids
+  const int32_t* vslot;       // nv -> contact vertex slot or -1
+  const int32_t* cv_face_off; // contact vertex -> face*4+local
+  const int32_t* cv_face_idx;
+  const int32_t* cv_edge_off; // contact vertex -> edge*4+local
+  const int32_t* cv_edge_idx;
+  const double* gel_elen2;    // nec rest squared lengths
+  R* cv_slot;                 // 9 x nvc  (3 g + 6 H)
+  R* ce_slot;                 // 27 x nec (6 g + 21 H)
+  R* cf_slot;                 // 54 x nfc (9 g + 45 H)
+  R* cv_y;                    // 3 x nvc contact share of H p
+  R* ce_y;                    // 6 x nec
+  R* cf_y;                    // 9 x nfc
+  // indenter (body frame)
+  const double* IV;           // 3 x ind_nv SoA
+  const float* IVhi;          // IV as FP32 hi + lo pairs (hi = fl(IV), lo = fl(IV - hi))
+  const float* IVlo;
+  const int32_t* IF;          // 3 x ind_nf
+  const int32_t* IE;          // 2 x ind_ne
+  const double* ind_elen2;    // ind_ne
+  GridView grid;
+  // candidate indenter primitives per gel contact primitive (kind 0 vertex,
+  // 1 edge, 2 face): cand[k][j * n_k + prim], j < min(cand_n[k][prim], cand_cap)
+  int32_t* cand[3];
+  int32_t* cand_n[3];
+  int cand_cap;
+  double Rm[9], tr[3];        // current indenter pose (world = R body + t)
+  // reductions
+  double* part;               // per-block partials
+  Scalars* sc;
+};
+
+struct EnvStats {
+  int64_t newton = 0, pcg = 0, substeps = 0, steps = 0, halvings = 0;
+};
+
+// Host-side environment.
+struct Env {
+  int device = 0;
+  int precision = TC_FP64;
+  cudaStream_t stream = nullptr;
+  Arena arena;
+  // sizes
+  int nv = 0, nt = 0, nf = 0, nfc = 0, nec = 0, nvc = 0;
+  int ind_nv = 0, ind_nf = 0, ind_ne = 0, H = 0, W = 0;
+  // material / options
+  double E = 0, nu = 0, rho = 0, mu = 0, lam = 0, lam_hat = 0, alpha = 0;
+  double dhat = 0, kappa = 0, dt = 0, rtol = 1e-6, gabs = 0, ptol = 0;
+  int newton_max = 1024, pcg_max = 1000, thick_axis = 2;
+  bool dynamic = false;
+  tc_pose pose{};
+  EnvStats stats;
+  // device integer topology
+  int4* tets = nullptr;
+  double* X0 = nullptr;
+  uint8_t* fixed = nullptr;
+  int32_t *vt_off = nullptr, *vt_idx = nullptr;
+  int32_t *cverts = nullptr, *cedges = nullptr, *cfaces = nullptr, *cparent = nullptr, *vslot = nullptr;
+  int32_t *cface_slot = nullptr;  // 3 x nfc contact-vertex slots of each face
+  int32_t *cv_face_off = nullptr, *cv_face_idx = nullptr, *cv_edge_off = nullptr, *cv_edge_idx = nullptr;
+  double* gel_elen2 = nullptr;
+  int32_t* pix_face = nullptr;
+  float* pix_w = nullptr;
+  // indenter
+  double* IV = nullptr;
+  float *IVhi = nullptr, *IVlo = nullptr;
+  int32_t *IF = nullptr, *IE = nullptr;
+  int32_t* cand[3] = {nullptr, nullptr, nullptr};
+  int32_t* cand_n[3] = {nullptr, nullptr, nullptr};
+  int cand_cap = 0;
+  bool cand_valid = false;    // lists cover the current state (see the CCD pass)
+  double* ind_elen2 = nullptr;
+  float grid_org[3] = {0, 0, 0}, grid_inv_cell = 1;
+  int grid_dims[3] = {1, 1, 1};
+  int32_t* grid_start[3] = {nullptr, nullptr, nullptr};
+  int32_t* grid_items[3] = {nullptr, nullptr, nullptr};
+  float* prim_box[3] = {nullptr, nullptr, nullptr};
+  // typed fields (one of the two sets is allocated)
+  void* Dminv = nullptr;
+  void* vol = nullptr;
+  void* mass = nullptr;
+  void *u = nullptr, *ut = nullptr, *vel = nullptr, *utilde = nullptr;
+  void *H9 = nullptr, *eslot = nullptr, *yslot = nullptr;
+  void *g = nullptr, *Minv = nullptr, *dx = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+  void *cv_slot = nullptr, *ce_slot = nullptr, *cf_slot = nullptr, *cv_y = nullptr, *ce_y = nullptr, *cf_y = nullptr;
+  void* utrial = nullptr;
+  // extraction scratch (float)
+  float *sigma = nullptr, *face_p = nullptr, *face_A = nullptr, *vert_p = nullptr;
+  double* part = nullptr;
+  int part_len = 0;
+  Scalars* sc = nullptr;      // device
+  Scalars* sc_host = nullptr; // pinned host mirror
+  // host copies of integer outputs
+  std::vector<int32_t> h_bfaces, h_bparent, h_cfaces, h_cparent, h_pix_face;
+  std::vector<float> h_pix_w;
+  int last_status = TC_OK;
+  Profiler* prof = nullptr;  // per-kernel timing, null unless enabled
+
+  template <class R> EnvView<R> view() const;
+};
+
+template <class R> EnvView<R> Env::view() const {
+  EnvView<R> e{};
+  e.nv = nv; e.nt = nt; e.nfc = nfc; e.nec = nec; e.nvc = nvc;
+  e.ind_nv = ind_nv; e.ind_nf = ind_nf; e.ind_ne = ind_ne; e.npix = H * W;
+  e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
+  e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
+  e.dhat = dhat; e.kappa = kappa;
+  e.tets = tets; e.X0 = X0; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
+  e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.H9 = (R*)H9; e.eslot = (R*)eslot; e.yslot = (R*)yslot;
+  e.mass = (const R*)mass; e.u = (R*)u; e.utilde = (const R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
+  e.dx = (R*)dx; e.r = (R*)r; e.z = (R*)z; e.p = (R*)p; e.q = (R*)q;
+  e.cverts = cverts; e.cedges = cedges; e.cfaces = cfaces; e.vslot = vslot;
+  e.cv_face_off = cv_face_off; e.cv_face_idx = cv_face_idx; e.cv_edge_off = cv_edge_off; e.cv_edge_idx = cv_edge_idx;
+  e.gel_elen2 = gel_elen2;
+  e.cv_slot = (R*)cv_slot; e.ce_slot = (R*)ce_slot; e.cf_slot = (R*)cf_slot;
+  e.cv_y = (R*)cv_y; e.ce_y = (R*)ce_y; e.cf_y = (R*)cf_y;
+  e.IV = IV; e.IVhi = IVhi; e.IVlo = IVlo; e.IF = IF; e.IE = IE; e.ind_elen2 = ind_elen2;
+  for (int k = 0; k < 3; ++k) { e.cand[k] = cand[k]; e.cand_n[k] = cand_n[k]; }
+  e.cand_cap = cand_cap;
+  for (int d = 0; d < 3; ++d) {
+    e.grid.org[d] = grid_org[d];
+    e.grid.dims[d] = grid_dims[d];
+    e.grid.start[d] = grid_start[d];
+    e.grid.items[d] = grid_items[d];
+    e.grid.box[d] = prim_box[d];
+  }
+  e.grid.inv_cell = grid_inv_cell;
+  for (int k = 0; k < 9; ++k) e.Rm[k] = pose.R[k];
+  for (int k = 0; k < 3; ++k) e.tr[k] = pose.t[k];
+  e.part = part; e.sc = sc;
+  return e;
+}
+
+// ------------------------------------------------------------ entry points
+// (defined in the .cu files; all return tc_status)
+
+tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32_t nfixed,
+                      const tc_trimesh* ind, const tc_grid* grid);
+tc_status check_initial(Env& env);
+
+// Element pass (energy, gradient slots, PSD H9, diagonal slots); energy only.
+template <class R> void launch_elem(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s);
+// Contact pass (energy + per-primitive slots) at displacement u_eval.
+template <class R> void launch_contact(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s);
+// Assemble gradient + preconditioner; writes sc->energy, sc->gnorm2.
+template <class R> void launch_assemble(const EnvView<R>& e, cudaStream_t s);
+// Total energy at u_eval (elastic + contact + inertia) into sc->energy.
+template <class R> void launch_energy(const EnvView<R>& e, const R* u_eval, cudaStream_t s);
+// PCG pieces.
+template <class R> void launch_pcg_init(const EnvView<R>& e, double eta, cudaStream_t s);
+template <class R> void launch_pcg_iter(const EnvView<R>& e, int max_iter, cudaStream_t s);
+template <class R> bool launch_pcg_persistent(const EnvView<R>& e, int max_iter, cudaStream_t s);
+template <class R> void launch_trial(const EnvView<R>& e, R* out, cudaStream_t s);
+template <class R> void launch_pmax(const EnvView<R>& e, cudaStream_t s);
+// CCD: gel moving by alpha_max * dx with a fixed indenter (line search), or
+// the indenter moving from pose a to pose b with a static gel.
+template <class R> void launch_ccd(const EnvView<R>& e, const R* dir, const double* Ra, const double* ta,
+                                   const double* Rb, const double* tb, cudaStream_t s);
+template <class R> void launch_axpy_u(const EnvView<R>& e, R* out, const R* u, R alpha, const R* d, cudaStream_t s);
+// Extraction.
+template <class R> void launch_stress(const EnvView<R>& e, float* sigma, cudaStream_t s);
+template <class R> void launch_traction(const EnvView<R>& e, const int32_t* cparent, float* t, float* p, float* tt,
+                                        float* face_p, float* face_A, cudaStream_t s);
+template <class R> int intersect_test(const EnvView<R>& e, int* dflag, cudaStream_t s);
+void launch_vertex_avg(int nvc, const int32_t* off, const int32_t* idx, const float* face_p, const float* face_A,
+                       float* vert_p, cudaStream_t s);
+void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const int32_t* cface_slot, int nfc,
+                  const float* vert_p, float* out, uint8_t* mask, cudaStream_t s);
+template <class R> void launch_contact_force(const EnvView<R>& e, cudaStream_t s);
+void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, float alpha, float* sigma,
+                          cudaStream_t s);
+
+}  // namespace tc

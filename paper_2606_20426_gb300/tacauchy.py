@@ -1,0 +1,320 @@
+"""Python binding of the C ABI in include/tacauchy.h (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+(paper_2606_20426_gb300/libtacauchy.so).  PyTorch supplies device memory
+(its caching allocator backs every env allocation) and streams; outputs are
+torch CUDA tensors.  There is no CPU fallback: importing works without a GPU
+(for builds and symbol checks), but every call that computes needs the
+library and a CUDA device and raises otherwise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtacauchy.so")
+
+TC_FP64, TC_FP32_MIXED = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "initial penetration", 4: "newton maxiter",
+          5: "pcg maxiter", 6: "line search", 7: "non-finite", 8: "cuda error", 9: "out of memory",
+          10: "admission", 11: "timeout", 12: "capacity"}
+
+# every symbol include/tacauchy.h declares
+EXPORTS = ["tc_create_scene", "tc_step", "tc_stress", "tc_traction", "tc_pressure_map", "tc_contact_force",
+           "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
+           "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
+           "tc_profile_read"]
+
+
+class TcError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} (status {code})")
+
+
+class Mesh(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("nv", ctypes.c_int32), ("tets", ctypes.c_void_p), ("nt", ctypes.c_int32)]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double)]
+
+
+class SceneOpts(ctypes.Structure):
+    _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("dt", ctypes.c_double),
+                ("newton_rtol", ctypes.c_double), ("newton_max", ctypes.c_int32), ("pcg_max", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("contact_axis", ctypes.c_int32)]
+
+
+class TriMesh(ctypes.Structure):
+    _fields_ = [("V", ctypes.c_void_p), ("nv", ctypes.c_int32), ("F", ctypes.c_void_p), ("nf", ctypes.c_int32)]
+
+
+class Pose(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("axis_u", ctypes.c_int32), ("axis_v", ctypes.c_int32), ("origin", ctypes.c_double * 2),
+                ("pixel", ctypes.c_double * 2), ("H", ctypes.c_int32), ("W", ctypes.c_int32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("release", RELEASE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("nf", ctypes.c_int32), ("nfc", ctypes.c_int32),
+                ("nec", ctypes.c_int32), ("nvc", ctypes.c_int32), ("ind_nv", ctypes.c_int32),
+                ("ind_nf", ctypes.c_int32), ("ind_ne", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("newton_iters", ctypes.c_int64), ("pcg_iters", ctypes.c_int64),
+                ("substeps", ctypes.c_int64), ("steps", ctypes.c_int64), ("line_search_halvings", ctypes.c_int64),
+                ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load():
+    """Load libtacauchy.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2606_20426_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    sig = {
+        "tc_create_scene": [ctypes.POINTER(Mesh), ctypes.POINTER(Material), P, ctypes.c_int32,
+                            ctypes.POINTER(TriMesh), ctypes.POINTER(Pose), ctypes.POINTER(SceneOpts),
+                            ctypes.POINTER(Grid), ctypes.POINTER(Allocator), P, ctypes.POINTER(P)],
+        "tc_step": [P, ctypes.POINTER(Pose)],
+        "tc_stress": [P, P],
+        "tc_traction": [P, P, P, P],
+        "tc_pressure_map": [P, P, P],
+        "tc_contact_force": [P, P],
+        "tc_surface_faces": [P, P, P],
+        "tc_boundary_faces": [P, P, P],
+        "tc_pixel_table": [P, P, P],
+        "tc_get_positions": [P, P],
+        "tc_set_positions": [P, P],
+        "tc_env_info": [P, ctypes.POINTER(Info)],
+        "tc_stress_from_F": [P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, P, P],
+        "tc_profile_enable": [P, ctypes.c_int32],
+        "tc_profile_read": [P, ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int32
+    lib.tc_destroy.argtypes = [P]
+    lib.tc_destroy.restype = None
+    lib.tc_status_str.argtypes = [ctypes.c_int32]
+    lib.tc_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise TcError(code, where)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("tacauchy needs a CUDA device")
+    return torch
+
+
+def make_pose(p):
+    """dict(R=(3,3), t=(3,)) or Pose -> Pose."""
+    if isinstance(p, Pose):
+        return p
+    out = Pose()
+    R = np.asarray(p["R"], dtype=np.float64).reshape(9)
+    t = np.asarray(p["t"], dtype=np.float64).reshape(3)
+    for k in range(9):
+        out.R[k] = R[k]
+    for k in range(3):
+        out.t[k] = t[k]
+    return out
+
+
+class _TorchAllocator:
+    """tc_allocator backed by the PyTorch caching allocator."""
+
+    def __init__(self, torch):
+        self.torch = torch
+
+        def alloc(ctx, nbytes, stream):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:
+                return None
+
+        def release(ctx, ptr, nbytes, stream):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self._alloc = ALLOC_FN(alloc)
+        self._release = RELEASE_FN(release)
+        self.struct = Allocator(self._alloc, self._release, None)
+
+
+class Env:
+    """One simulated sensor: gel pad + rigid indenter + pixel grid."""
+
+    def __init__(self, env, precision=None, stream=None, torch_allocator=True):
+        torch = _torch()
+        lib = load()
+        self.torch, self.lib = torch, lib
+        X = np.ascontiguousarray(env["X"], dtype=np.float64)
+        T = np.ascontiguousarray(env["tets"], dtype=np.int32)
+        fixed = np.ascontiguousarray(env["fixed"], dtype=np.int32)
+        V = np.ascontiguousarray(env["ind_V"], dtype=np.float64)
+        F = np.ascontiguousarray(env["ind_F"], dtype=np.int32)
+        self._keep = (X, T, fixed, V, F)
+        m, o = env["material"], env["opts"]
+        prec = precision if precision is not None else o.get("precision", "fp64")
+        if isinstance(prec, str):
+            prec = TC_FP64 if prec == "fp64" else TC_FP32_MIXED
+        self.precision = prec
+        mesh = Mesh(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0])
+        mat = Material(m["E"], m["nu"], m["density"])
+        opts = SceneOpts(o["dhat"], o.get("kappa", 0.0), o.get("dt", 0.0), o.get("newton_rtol", 1e-6),
+                         o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1))
+        ind = TriMesh(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
+        g = env.get("grid")
+        grid = None
+        if g is not None:
+            grid = Grid(g["axis_u"], g["axis_v"], (ctypes.c_double * 2)(*g["origin"]),
+                        (ctypes.c_double * 2)(*g["pixel"]), g["H"], g["W"])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._allocator = _TorchAllocator(torch) if torch_allocator else None
+        handle = ctypes.c_void_p()
+        pose = make_pose(env["start_pose"])
+        code = lib.tc_create_scene(ctypes.byref(mesh), ctypes.byref(mat), fixed.ctypes.data, len(fixed),
+                                   ctypes.byref(ind), ctypes.byref(pose), ctypes.byref(opts),
+                                   ctypes.byref(grid) if grid is not None else None,
+                                   ctypes.byref(self._allocator.struct) if self._allocator else None,
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(handle))
+        _check(code, "tc_create_scene")
+        self.h = handle
+        self.info = self.get_info()
+
+    # ------------------------------------------------------------- calls
+    def get_info(self):
+        inf = Info()
+        _check(self.lib.tc_env_info(self.h, ctypes.byref(inf)), "tc_env_info")
+        return {k: getattr(inf, k) for k, _ in Info._fields_}
+
+    def step(self, pose):
+        p = make_pose(pose)
+        _check(self.lib.tc_step(self.h, ctypes.byref(p)), "tc_step")
+
+    def stress(self, out=None):
+        """(6, nt) float32 CUDA tensor: xx, yy, zz, xy, yz, zx."""
+        nt = self.info["nt"]
+        if out is None:
+            out = self.torch.empty((6, nt), dtype=self.torch.float32, device="cuda")
+        _check(self.lib.tc_stress(self.h, ctypes.c_void_p(out.data_ptr())), "tc_stress")
+        return out
+
+    def traction(self):
+        n = self.info["nfc"]
+        t = self.torch.empty((3, n), dtype=self.torch.float32, device="cuda")
+        p = self.torch.empty((n,), dtype=self.torch.float32, device="cuda")
+        tt = self.torch.empty((3, n), dtype=self.torch.float32, device="cuda")
+        _check(self.lib.tc_traction(self.h, ctypes.c_void_p(t.data_ptr()), ctypes.c_void_p(p.data_ptr()),
+                                    ctypes.c_void_p(tt.data_ptr())), "tc_traction")
+        return t, p, tt
+
+    def pressure_map(self, out=None, mask=None, want_mask=True):
+        H, W = self.info["H"], self.info["W"]
+        if out is None:
+            out = self.torch.empty((H, W), dtype=self.torch.float32, device="cuda")
+        if mask is None and want_mask:
+            mask = self.torch.empty((H, W), dtype=self.torch.uint8, device="cuda")
+        _check(self.lib.tc_pressure_map(self.h, ctypes.c_void_p(out.data_ptr()),
+                                        ctypes.c_void_p(mask.data_ptr()) if mask is not None else None),
+               "tc_pressure_map")
+        return out, mask
+
+    def contact_force(self):
+        f = np.zeros(3)
+        _check(self.lib.tc_contact_force(self.h, f.ctypes.data), "tc_contact_force")
+        return f
+
+    def surface_faces(self):
+        n = self.info["nfc"]
+        f = np.zeros((n, 3), dtype=np.int32)
+        p = np.zeros(n, dtype=np.int32)
+        _check(self.lib.tc_surface_faces(self.h, f.ctypes.data, p.ctypes.data), "tc_surface_faces")
+        return f, p
+
+    def boundary_faces(self):
+        n = self.info["nf"]
+        f = np.zeros((n, 3), dtype=np.int32)
+        p = np.zeros(n, dtype=np.int32)
+        _check(self.lib.tc_boundary_faces(self.h, f.ctypes.data, p.ctypes.data), "tc_boundary_faces")
+        return f, p
+
+    def pixel_table(self):
+        n = self.info["H"] * self.info["W"]
+        f = np.zeros(n, dtype=np.int32)
+        w = np.zeros((n, 3), dtype=np.float32)
+        _check(self.lib.tc_pixel_table(self.h, f.ctypes.data, w.ctypes.data), "tc_pixel_table")
+        return f, w
+
+    def positions(self):
+        x = np.zeros((self.info["nv"], 3))
+        _check(self.lib.tc_get_positions(self.h, x.ctypes.data), "tc_get_positions")
+        return x
+
+    def set_positions(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        _check(self.lib.tc_set_positions(self.h, x.ctypes.data), "tc_set_positions")
+
+    def profile(self, on=True):
+        """Enable (and clear) or disable per-kernel timing."""
+        _check(self.lib.tc_profile_enable(self.h, 1 if on else 0), "tc_profile_enable")
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} since profiling was enabled."""
+        buf = (KernelTime * 64)()
+        n = ctypes.c_int32()
+        _check(self.lib.tc_profile_read(self.h, buf, 64, ctypes.byref(n)), "tc_profile_read")
+        return {buf[i].name.decode(): (buf[i].ms, buf[i].launches) for i in range(min(n.value, 64))}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def stress_from_F(F, E, nu, out=None, stream=None):
+    """sigma (6, n) from a CUDA float32 tensor F of shape (n, 9) or (n, 3, 3)."""
+    torch = _torch()
+    lib = load()
+    n = F.shape[0]
+    if out is None:
+        out = torch.empty((6, n), dtype=torch.float32, device=F.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib.tc_stress_from_F(ctypes.c_void_p(F.data_ptr()), n, E, nu, ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(s.cuda_stream)), "tc_stress_from_F")
+    return out
