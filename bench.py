@@ -43,10 +43,30 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def pcg_iteration_bytes(info):
+    """Algorithmic bytes of one PCG iteration of one env (FP32): element SpMV
+    (tet ids 16, Dm^-1 36, volume 4, H9 180 read, 12 slot values 48 written, p
+    read once per vertex), contact SpMV (per primitive: ids, packed block,
+    result), per-vertex gather of the slots (CSR offset, incidence id and 3
+    values per incidence; q written), the update (dx, r read+write; p, q,
+    M^-1 read; z written) and the direction update (z, p read; p written)."""
+    nt, nv = info["nt"], info["nv"]
+    nvc, nec, nfc = info["nvc"], info["nec"], info["nfc"]
+    deg = 4.0 * nt / nv
+    spmv = nt * (16 + 36 + 4 + 180 + 48) + 12 * nv
+    contact = nvc * (4 + 24 + 12 + 12) + nec * (8 + 84 + 24 + 24) + nfc * (12 + 180 + 36 + 36)
+    gather = nv * (4 + deg * (4 + 12) + 12 + 12 + 1)
+    update = nv * (24 + 24 + 12 + 12 + 24 + 12)
+    pupdate = nv * (12 + 24)
+    return spmv + contact + gather + update + pupdate
+
+
 # algorithmic bytes per launch of the kernels of one env (FP32 mixed mode)
-def algorithmic_bytes(name, info):
+def algorithmic_bytes(name, info, pcg_iters_per_launch=None):
     nt, nv = info["nt"], info["nv"]
     deg = 4.0 * nt / nv  # tet incidences per vertex
+    if name == "k_pcg_persistent":
+        return pcg_iteration_bytes(info) * pcg_iters_per_launch if pcg_iters_per_launch else None
     table = {
         # idx 16 + Dm^-1 36 + vol 4 + H9 180 (read) + 12 outputs 48 (write); p read once per vertex
         "k_spmv_elem": nt * (16 + 36 + 4 + 180 + 48) + 12 * nv,
@@ -66,7 +86,7 @@ def algorithmic_bytes(name, info):
     return table.get(name)
 
 
-KERNEL_SRC = {"k_spmv_elem": "solver.cu", "k_pcg_q": "solver.cu", "k_pcg_update": "solver.cu",
+KERNEL_SRC = {"k_pcg_persistent": "solver.cu", "k_spmv_elem": "solver.cu", "k_pcg_q": "solver.cu", "k_pcg_update": "solver.cu",
               "k_pcg_p": "solver.cu", "k_assemble": "solver.cu", "k_elem_hess": "elem.cu",
               "k_elem_energy": "elem.cu", "k_stress": "elem.cu", "k_axpy": "solver.cu"}
 
@@ -226,6 +246,7 @@ def run_ours(args):
         d2h = sum(4 * 6 * i["nt"] + 4 * i["H"] * i["W"] for i in infos)
         h2d = B * 96  # the target pose (12 doubles) per env-step
         # ---------------- per-kernel times of a profiled repeat of the timed steps
+        pcg0 = sum(e.get_info()["pcg_iters"] for e in envs)
         for e in envs:
             e.profile(True)
         for k in range(args.steps):
@@ -234,6 +255,7 @@ def run_ours(args):
             for b in range(B):
                 env_step(b)
         torch.cuda.synchronize(dev)
+        pcg_profiled = sum(e.get_info()["pcg_iters"] for e in envs) - pcg0
         prof = {}
         for e in envs:
             for name, (ms, n) in e.kernel_times().items():
@@ -245,7 +267,8 @@ def run_ours(args):
     roof = None
     peak, peak_kind = peaks()
     for name, (ms, n) in top:
-        per = [algorithmic_bytes(name, i) for i in infos]
+        it_per_launch = pcg_profiled / n if name == "k_pcg_persistent" and n else None
+        per = [algorithmic_bytes(name, i, it_per_launch) for i in infos]
         if per[0] is None or n == 0:
             continue
         # launches spread evenly over the B envs of this rank
@@ -256,6 +279,7 @@ def run_ours(args):
         if tr and tr["sha"] == src_sha(KERNEL_SRC[name]):
             traffic = tr["bytes_per_unit"] * (sum(i["nt"] for i in infos) / len(infos))
         roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "units_per_launch": (round(it_per_launch, 2) if it_per_launch else None),
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "bytes_per_launch": int(bytes_per_launch), "avg_launch_us": ms / n * 1e3,
                 "share_of_kernel_time": round(ms / sum(v[0] for v in prof.values()), 4)}
