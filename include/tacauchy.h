@@ -206,6 +206,38 @@ const char* tc_status_str(tc_status s);
 tc_status tc_stress_from_F(const float* F, int64_t n, double E, double nu,
                            float* sigma_out, void* stream);
 
+/* Pressure map that allocates nothing (the paper has no counterpart: this
+ * entry point exists for callers, not for the method).  It is for callers
+ * that cannot obtain device memory at the time of the call -- for example a
+ * real-time control loop that forbids allocator calls after start-up, or code
+ * running inside a foreign memory pool -- so it never calls cudaMalloc,
+ * cudaFree or an allocating library routine.  It computes what
+ * tc_pressure_map computes, from caller-supplied device arrays:
+ *   x          float 3 x nv   deformed positions, component-major
+ *   sigma      float 6 x nt   Cauchy stress as written by tc_stress
+ *   cfaces     int32 3 x nfc  contact faces (outward winding), component-major
+ *   cparent    int32 nfc      parent tet of each face
+ *   cface_slot int32 3 x nfc  index of each face vertex among the nvc contact
+ *                             vertices (sorted by vertex id)
+ *   cv_face_off int32 nvc+1, cv_face_idx int32: per contact vertex, the
+ *                             incident contact faces encoded face*4 + corner
+ *   pix_face int32 npix, pix_w float 3 x npix: the binning of tc_pixel_table
+ *   out float npix, mask uint8 npix (nullable)
+ * Per-face and per-vertex intermediates live in one file-scope device array
+ * of fixed size, shared by every call: at most 262,144 contact faces and
+ * 262,144 contact vertices (TC_ERR_CAPACITY beyond), about 3 MB held on every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * it once per device before any stream capture.  Calls that overlap on the
+ * GPU (different streams, or different host threads) race on the shared
+ * array; serialise them.  Synchronises `stream` before returning. */
+tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const float* sigma, int32_t nt,
+                                  const int32_t* cfaces, const int32_t* cparent,
+                                  const int32_t* cface_slot, int32_t nfc,
+                                  const int32_t* cv_face_off, const int32_t* cv_face_idx, int32_t nvc,
+                                  const int32_t* pix_face, const float* pix_w, int32_t npix,
+                                  float* out, uint8_t* mask, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "initial penetra
 EXPORTS = ["tc_create_scene", "tc_step", "tc_stress", "tc_traction", "tc_pressure_map", "tc_contact_force",
            "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
-           "tc_profile_read"]
+           "tc_profile_read", "tc_pressure_map_noalloc"]
 
 
 class TcError(RuntimeError):
@@ -111,6 +111,8 @@ def load():
         "tc_stress_from_F": [P, ctypes.c_int64, ctypes.c_double, ctypes.c_double, P, P],
         "tc_profile_enable": [P, ctypes.c_int32],
         "tc_profile_read": [P, ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+        "tc_pressure_map_noalloc": [P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P,
+                                    ctypes.c_int32, P, P, ctypes.c_int32, P, P, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -317,4 +319,24 @@ def stress_from_F(F, E, nu, out=None, stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
     _check(lib.tc_stress_from_F(ctypes.c_void_p(F.data_ptr()), n, E, nu, ctypes.c_void_p(out.data_ptr()),
                                 ctypes.c_void_p(s.cuda_stream)), "tc_stress_from_F")
+    return out
+
+
+def pressure_map_noalloc(x, sigma, cfaces, cparent, cface_slot, cv_face_off, cv_face_idx, pix_face, pix_w, out,
+                         mask=None, stream=None):
+    """Pressure map from caller-owned CUDA tensors, with no device allocation
+    inside the library (see tc_pressure_map_noalloc in include/tacauchy.h).
+    x (3, nv) float32, sigma (6, nt) float32, cfaces / cface_slot (3, nfc)
+    int32, cparent (nfc,) int32, cv_face_off (nvc+1,) int32, cv_face_idx int32,
+    pix_face (npix,) int32, pix_w (3, npix) float32, out (npix,) float32,
+    mask (npix,) uint8 or None."""
+    torch = _torch()
+    lib = load()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(lib.tc_pressure_map_noalloc(vp(x), x.shape[1], vp(sigma), sigma.shape[1], vp(cfaces), vp(cparent),
+                                       vp(cface_slot), cfaces.shape[1], vp(cv_face_off), vp(cv_face_idx),
+                                       cv_face_off.shape[0] - 1, vp(pix_face), vp(pix_w), pix_face.shape[0],
+                                       vp(out), vp(mask), ctypes.c_void_p(s.cuda_stream)),
+           "tc_pressure_map_noalloc")
     return out
