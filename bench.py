@@ -61,34 +61,29 @@ def pcg_iteration_bytes(info):
     return spmv + contact + gather + update + pupdate
 
 
-# algorithmic bytes per launch of the kernels of one env (FP32 mixed mode)
-def algorithmic_bytes(name, info, pcg_iters_per_launch=None):
-    nt, nv = info["nt"], info["nv"]
-    deg = 4.0 * nt / nv  # tet incidences per vertex
-    if name == "k_pcg_persistent":
-        return pcg_iteration_bytes(info) * pcg_iters_per_launch if pcg_iters_per_launch else None
+# algorithmic bytes per launch of the per-env kernels (FP32 mixed mode)
+def algorithmic_bytes(name, info):
+    nt, nv, nfc, nvc = info["nt"], info["nv"], info["nfc"], info["nvc"]
+    npix = info["H"] * info["W"]
     table = {
-        # idx 16 + Dm^-1 36 + vol 4 + H9 180 (read) + 12 outputs 48 (write); p read once per vertex
-        "k_spmv_elem": nt * (16 + 36 + 4 + 180 + 48) + 12 * nv,
-        # idx 16 + Dm^-1 36 + vol 4 (read) + H9 180 + 36 slots 144 (write); u read once per vertex
-        "k_elem_hess": nt * (16 + 36 + 4 + 180 + 144) + 12 * nv,
-        "k_elem_energy": nt * (16 + 36 + 4) + 12 * nv,
-        # CSR offsets + incidence ids + 12 slot values per incidence; p read, q write
-        "k_pcg_q": nv * (4 + deg * (4 + 12) + 12 + 12 + 1),
-        # dx, r (read+write), p, q, Minv (read), z (write)
-        "k_pcg_update": nv * (24 + 24 + 12 + 12 + 24 + 12),
-        "k_pcg_p": nv * (12 + 24),
-        # CSR + 36 slot values per incidence; g and Minv written
-        "k_assemble": nv * (4 + deg * (4 + 36) + 12 + 24 + 1),
+        # tet ids 16 + Dm^-1 36 + sigma 24 written; displacement read once per vertex
         "k_stress": nt * (16 + 36 + 24) + 12 * nv,
-        "k_axpy": nv * 36,
+        # parent 4 + tet ids 16 + Dm^-1 36 + face ids 12 + (p, A) 8 written + the
+        # parent's fourth vertex 12; contact vertices: displacement 12 + rest
+        # position 24 (FP64)
+        "k_traction": nfc * (4 + 16 + 36 + 12 + 8 + 12) + nvc * 36,
+        # CSR offsets 8 per vertex, incidence ids 4 x ~3 per face, (p, A) 8 per
+        # face, vertex value 4 written
+        "k_vertex_avg": nvc * (8 + 4) + nfc * (12 + 8),
+        # covering face 4 + weights 12 + value 4 + mask 1 per pixel; face slots
+        # and vertex values once
+        "k_splat": npix * 21 + nfc * 12 + nvc * 4,
     }
     return table.get(name)
 
 
-KERNEL_SRC = {"k_pcg_persistent": "solver.cu", "k_spmv_elem": "solver.cu", "k_pcg_q": "solver.cu", "k_pcg_update": "solver.cu",
-              "k_pcg_p": "solver.cu", "k_assemble": "solver.cu", "k_elem_hess": "elem.cu",
-              "k_elem_energy": "elem.cu", "k_stress": "elem.cu", "k_axpy": "solver.cu"}
+KERNEL_SRC = {"k_pcg_batched": "solver.cu", "k_stress": "elem.cu", "k_traction": "extract.cu",
+              "k_vertex_avg": "extract.cu", "k_splat": "extract.cu"}
 
 
 def src_sha(fname):
@@ -161,11 +156,91 @@ def make_envs(B, rank):
     return envs
 
 
+def _kernel_table(prof):
+    tot = sum(v[0] for v in prof.values()) or 1.0
+    top = sorted(prof.items(), key=lambda kv: -kv[1][0])
+    return top, {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot, 4)} for k, v in top[:14]}
+
+
+def _roofline(top, infos, pcg_iters_by_env, peak, peak_kind):
+    """Roofline of the dominant kernel whose algorithmic bytes are known.
+    k_pcg_batched: one launch runs every env of the phase for its own number of
+    iterations, so bytes = sum over envs of (bytes per iteration x iterations)
+    over the profiled region, divided by the kernel's total time there."""
+    tot = sum(v[0] for _, v in top) or 1.0
+    for name, (ms, n) in top:
+        if n == 0:
+            continue
+        if name == "k_pcg_batched":
+            total_bytes = sum(pcg_iteration_bytes(i) * it for i, it in zip(infos, pcg_iters_by_env))
+            units = sum(pcg_iters_by_env) / n
+        else:
+            per = [algorithmic_bytes(name, i) for i in infos]
+            if per[0] is None:
+                continue
+            total_bytes = sum(per) / len(per) * n  # per-env launches spread evenly over the envs
+            units = None
+        bytes_per_launch = total_bytes / n
+        achieved = bytes_per_launch / (ms / n / 1e3) / 1e9
+        tr = NCU_TRAFFIC.get(name)
+        traffic = None
+        if tr and tr["sha"] == src_sha(KERNEL_SRC[name]):
+            traffic = tr["bytes_per_launch"]
+        return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "bytes_per_launch": int(bytes_per_launch),
+                "avg_launch_us": round(ms / n * 1e3, 2), "units_per_launch": (round(units, 2) if units else None),
+                "share_of_kernel_time": round(ms / tot, 4)}
+    return None
+
+
+def _extraction_fracs(prof, infos, peak):
+    out = {}
+    for name in ("k_stress", "k_traction", "k_vertex_avg", "k_splat"):
+        if name not in prof or prof[name][1] == 0:
+            continue
+        ms, n = prof[name]
+        b = sum(algorithmic_bytes(name, i) for i in infos) / len(infos)
+        out[name] = {"avg_launch_us": round(ms / n * 1e3, 2), "bytes_per_launch": int(b),
+                     "frac": round(b / (ms / n / 1e3) / 1e9 / peak, 4)}
+    return out
+
+
+def stress_sweep(dev, stream, peak, sizes=(100_000, 1_000_000, 10_000_000), reps=10):
+    """tc_stress_from_F over nt random SPD-perturbed F (||F - I|| <= 0.3):
+    60 algorithmic bytes per tet (F read 36, sigma written 24)."""
+    import torch
+    from paper_2606_20426_gb300 import stress_from_F
+    from synth.workloads import random_deformation_gradients
+    res = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for nt in sizes:
+        F = torch.from_numpy(random_deformation_gradients(7, nt).reshape(nt, 9).astype("float32")).to(dev)
+        out = torch.empty((6, nt), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                stress_from_F(F, 0.3e6, 0.45, out=out, stream=stream)
+            ts = []
+            for r in range(reps):
+                flush.fill_(float(r))
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                stress_from_F(F, 0.3e6, 0.45, out=out, stream=stream)
+                z.record(stream)
+                z.synchronize()
+                ts.append(a.elapsed_time(z))
+        ms = statistics.median(ts)
+        gbs = 60.0 * nt / (ms / 1e3) / 1e9
+        res[str(nt)] = {"us": round(ms * 1e3, 2), "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+        del F, out
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2606_20426_gb300 import Env
+    from paper_2606_20426_gb300 import Env, step_batch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,21 +253,41 @@ def run_ours(args):
     B = args.envs
     cfgs = make_envs(B, rank)
     with torch.cuda.stream(stream):
-        envs = [Env(c, precision="fp32", stream=stream) for c in cfgs]
-    infos = [e.info for e in envs]
+        served = [Env(c, precision="fp32", stream=stream) for c in cfgs]
+        plain = [Env(c, precision="fp32", stream=stream) for c in cfgs] if args.plain else []
+    infos = [e.info for e in served]
     sig = [torch.empty((6, i["nt"]), dtype=torch.float32, device=dev) for i in infos]
     maps = [torch.empty((i["H"], i["W"]), dtype=torch.float32, device=dev) for i in infos]
     masks = [torch.empty((i["H"], i["W"]), dtype=torch.uint8, device=dev) for i in infos]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
-    cursor = [0] * B
+    cur = {"served": 0, "plain": [0] * B}
 
-    def env_step(b, host=None):
-        e, c = envs[b], cfgs[b]
-        pose = c["bench_poses"][cursor[b] % len(c["bench_poses"])]
-        cursor[b] += 1
-        e.step(pose)
-        e.stress(sig[b])
-        e.pressure_map(maps[b], masks[b])
+    def pose_of(b, k):
+        c = cfgs[b]["bench_poses"]
+        return c[k % len(c)]
+
+    def extract(envs, host=None):
+        for b, e in enumerate(envs):
+            e.stress(sig[b])
+            e.pressure_map(maps[b], masks[b])
+            if host is not None:
+                host[0][b].copy_(sig[b], non_blocking=True)
+                host[1][b].copy_(maps[b], non_blocking=True)
+
+    def served_step(host=None):
+        k = cur["served"]
+        cur["served"] += 1
+        codes = step_batch(served, [pose_of(b, k) for b in range(B)])
+        if any(codes):
+            raise RuntimeError(f"tc_step_batch statuses {codes}")
+        extract(served, host)
+
+    def plain_step(b, host=None):
+        k = cur["plain"][b]
+        cur["plain"][b] += 1
+        plain[b].step(pose_of(b, k))
+        plain[b].stress(sig[b])
+        plain[b].pressure_map(maps[b], masks[b])
         if host is not None:
             host[0][b].copy_(sig[b], non_blocking=True)
             host[1][b].copy_(maps[b], non_blocking=True)
@@ -202,113 +297,119 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    def max_over_ranks(x):
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            for b in range(B):
-                env_step(b)
+            served_step()
+            for b in range(len(plain)):
+                plain_step(b)
         barrier()
-        # ---------------- timed region (device time, L2 flushed between steps)
-        lat = []
-        total_ms = 0.0
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(B)]
+        # ------------- timed region, served form: one batched call per step
+        lat, total_ms = [], 0.0
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
         with ClockSampler(local) as clk:
             for k in range(args.steps):
                 flush.fill_(float(k))
                 torch.cuda.synchronize(dev)
-                for b in range(B):
-                    ev[b][0].record(stream)
-                    env_step(b)
-                    ev[b][1].record(stream)
+                ev[0].record(stream)
+                served_step()
+                ev[1].record(stream)
                 torch.cuda.synchronize(dev)
-                step_ms = sum(a.elapsed_time(z) for a, z in ev)
-                lat += [a.elapsed_time(z) for a, z in ev]
-                total_ms += step_ms
+                ms = ev[0].elapsed_time(ev[1])
+                total_ms += ms
+                lat += [ms] * B  # every env's result is ready when the batch returns
         barrier()
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms)
         clocks = clk.summary()
         value = world * B * args.steps / (total_ms / 1e3)
-        # ---------------- end-to-end through the API with host buffers
+        # ------------- plain form: one env per launch sequence, same requests
+        plain_out = None
+        if plain:
+            plat, ptotal = [], 0.0
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(B)]
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                torch.cuda.synchronize(dev)
+                for b in range(B):
+                    evs[b][0].record(stream)
+                    plain_step(b)
+                    evs[b][1].record(stream)
+                torch.cuda.synchronize(dev)
+                plat += [a.elapsed_time(z) for a, z in evs]
+                ptotal += sum(a.elapsed_time(z) for a, z in evs)
+            barrier()
+            ptotal = max_over_ranks(ptotal)
+            plain_out = {"value": round(world * B * args.steps / (ptotal / 1e3), 3), "unit": UNIT,
+                         "ms_per_step": round(ptotal / args.steps, 3),
+                         "latency_ms": {"p50": round(float(np.percentile(plat, 50)), 3),
+                                        "p99": round(float(np.percentile(plat, 99)), 3)},
+                         "form": "plain: tc_step + tc_stress + tc_pressure_map per env, one env after another"}
+        # ------------- end to end through the API with pinned host buffers
         host = ([torch.empty((6, i["nt"]), dtype=torch.float32).pin_memory() for i in infos],
                 [torch.empty((i["H"], i["W"]), dtype=torch.float32).pin_memory() for i in infos])
         e2e_steps = max(1, min(args.steps, 3))
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            for b in range(B):
-                env_step(b, host)
+            served_step(host)
             torch.cuda.synchronize(dev)
         barrier()
-        e2e_s = time.perf_counter() - t0
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
         e2e_value = world * B * e2e_steps / e2e_s
         d2h = sum(4 * 6 * i["nt"] + 4 * i["H"] * i["W"] for i in infos)
         h2d = B * 96  # the target pose (12 doubles) per env-step
-        # ---------------- per-kernel times of a profiled repeat of the timed steps
-        pcg0 = sum(e.get_info()["pcg_iters"] for e in envs)
-        for e in envs:
+        # ------------- per-kernel times of a profiled repeat of the served steps
+        pcg0 = [e.get_info()["pcg_iters"] for e in served]
+        for e in served:
             e.profile(True)
         for k in range(args.steps):
             flush.fill_(float(k))
             torch.cuda.synchronize(dev)
-            for b in range(B):
-                env_step(b)
+            served_step()
         torch.cuda.synchronize(dev)
-        pcg_profiled = sum(e.get_info()["pcg_iters"] for e in envs) - pcg0
+        pcg_by_env = [e.get_info()["pcg_iters"] - p0 for e, p0 in zip(served, pcg0)]
         prof = {}
-        for e in envs:
+        for e in served:
             for name, (ms, n) in e.kernel_times().items():
                 a, c = prof.get(name, (0.0, 0))
                 prof[name] = (a + ms, c + n)
             e.profile(False)
     launches = sum(n for _, n in prof.values())
-    top = sorted(prof.items(), key=lambda kv: -kv[1][0])
-    roof = None
     peak, peak_kind = peaks()
-    for name, (ms, n) in top:
-        it_per_launch = pcg_profiled / n if name == "k_pcg_persistent" and n else None
-        per = [algorithmic_bytes(name, i, it_per_launch) for i in infos]
-        if per[0] is None or n == 0:
-            continue
-        # launches spread evenly over the B envs of this rank
-        bytes_per_launch = sum(per) / len(per)
-        achieved = bytes_per_launch / (ms / n / 1e3) / 1e9
-        tr = NCU_TRAFFIC.get(name)
-        traffic = None
-        if tr and tr["sha"] == src_sha(KERNEL_SRC[name]):
-            traffic = tr["bytes_per_unit"] * (sum(i["nt"] for i in infos) / len(infos))
-        roof = {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
-                "units_per_launch": (round(it_per_launch, 2) if it_per_launch else None),
-                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "traffic": traffic, "bytes_per_launch": int(bytes_per_launch), "avg_launch_us": ms / n * 1e3,
-                "share_of_kernel_time": round(ms / sum(v[0] for v in prof.values()), 4)}
-        break
-    tot_ms = sum(v[0] for v in prof.values())
-    kernel_table = {k: {"ms": round(v[0], 3), "launches": v[1], "share": round(v[0] / tot_ms, 4)}
-                    for k, v in top[:12]}
+    top, kernel_table = _kernel_table(prof)
+    roof = _roofline(top, infos, pcg_by_env, peak, peak_kind)
+    steps_done = max(1, sum(e.get_info()["steps"] for e in served))
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "envs_per_gpu": B, "form": "plain (one env per launch sequence)",
-                   "l2": "flushed between timed steps (256 MB write)", "tets_per_env": infos[0]["nt"],
-                   "verts_per_env": infos[0]["nv"]},
+        "config": {"workload": WORKLOAD, "envs_per_gpu": B,
+                   "form": "batched: one tc_step_batch over all envs (one launch per Newton phase), "
+                           "then tc_stress + tc_pressure_map per env",
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "tets_per_env": [i["nt"] for i in infos][:4], "verts_per_env": [i["nv"] for i in infos][:4]},
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3), "p99": round(float(np.percentile(lat, 99)), 3)},
+        "plain": plain_out,
         "clocks": clocks,
         "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(launches // max(1, args.steps) * args.steps),
+        "gpu_launches": int(launches),
         "roofline": roof,
+        "extraction": _extraction_fracs(prof, infos, peak),
         "kernels": kernel_table,
-        "solver": {"newton_per_env_step": sum(e.get_info()["newton_iters"] for e in envs) /
-                   max(1, sum(e.get_info()["steps"] for e in envs)),
-                   "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in envs) /
-                   max(1, sum(e.get_info()["steps"] for e in envs))},
+        "solver": {"newton_per_env_step": sum(e.get_info()["newton_iters"] for e in served) / steps_done,
+                   "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in served) / steps_done},
     }
+    for e in served + plain:
+        e.close()
+    if args.sweep:
+        out["stress_sweep"] = stress_sweep(dev, stream, peak)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(out["solver"]["newton_per_env_step"], args.cpu_seconds)
-    for e in envs:
-        e.close()
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
@@ -396,7 +497,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--envs", type=int, default=4)
+    ap.add_argument("--envs", type=int, default=8)
+    ap.add_argument("--plain", type=int, default=1, help="also time the plain one-env-per-launch form")
+    ap.add_argument("--sweep", type=int, default=1, help="also run the tc_stress_from_F size sweep")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

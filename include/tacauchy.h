@@ -145,6 +145,21 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material,
  * potential of the gel at each substep. */
 tc_status tc_step(tc_env* env, const tc_pose* target);
 
+/* One step of each of n independent envs (Algorithm 2, physics line, applied
+ * to every env), run together: each Newton phase (element pass, barrier pass,
+ * assembly, PCG, CCD, line-search energy) is one launch over all envs still
+ * iterating, so small envs share the GPU instead of running one after another.
+ * Each env's result is the one tc_step would give it alone (the per-env
+ * reductions are folded in the same order).  envs: host array of n distinct
+ * envs of one precision and device; targets: host array of n poses;
+ * statuses: host array of n, receiving each env's own status (a non-finite
+ * target gives TC_ERR_NONFINITE for that env and leaves it unchanged).  The
+ * work runs on the first env's stream after every other env's stream has
+ * drained.  Returns TC_OK unless the call as a whole failed (invalid
+ * arguments, CUDA error, allocation failure); n = 0 is a no-op. */
+tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets,
+                        tc_status* statuses);
+
 /* Cauchy stress per tet (Eq. 4 with the rest-stable reading):
  * sigma_out device float 6 x nt, component-major (component k of tet e at
  * k * nt + e), components in the order (xx, yy, zz, xy, yz, zx). */

@@ -1,14 +1,8 @@
-// C ABI (include/tacauchy.h) and the host side of one implicit step.
+// C ABI (include/tacauchy.h): scene lifetime, steps, extraction, profiling.
 //
-// tc_step (Algorithm 2, physics line) runs, on the env's stream:
-//   indenter substeps s in [0, 1] (kinematic indenter, CCD-limited advance)
-//     Newton iterations
-//       K1 element pass + K3 barrier pass + K4 assembly   -> E, |g|
-//       K5 PCG (chunks of iterations between flag reads)  -> dx
-//       K6 CCD along dx                                    -> alpha_max
-//       K7 backtracking line search on E(u + alpha dx)
-// The host reads a handful of scalars per Newton iteration (energy, |g|,
-// PCG flag, CCD bound, trial energies); everything else stays on the device.
+// tc_step is a batch of one and tc_step_batch a batch of many; both run the
+// implicit step of Algorithm 2 (physics line) through the batch executor,
+// where every Newton phase is one launch over all envs taking part in it.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -17,6 +11,7 @@
 #include <cstring>
 #include <new>
 
+#include "batch.cuh"
 #include "env.cuh"
 
 struct tc_env {
@@ -40,251 +35,31 @@ struct ProfGuard {
     if (e_ != cudaSuccess) return TC_ERR_CUDA;      \
   } while (0)
 
-static void pose_interp(const tc_pose& a, const tc_pose& b, double s, tc_pose* out) {
-  for (int k = 0; k < 3; ++k) out->t[k] = (1.0 - s) * a.t[k] + s * b.t[k];
-  bool same = true;
-  for (int k = 0; k < 9; ++k) same = same && a.R[k] == b.R[k];
-  if (same || s <= 0.0 || s >= 1.0) {
-    std::memcpy(out->R, s >= 1.0 ? b.R : a.R, sizeof(out->R));
-    return;
-  }
-  // geodesic interpolation R(s) = Ra exp(s log(Ra^T Rb)) via axis-angle
-  double M[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double acc = 0;
-      for (int k = 0; k < 3; ++k) acc += a.R[3 * k + i] * b.R[3 * k + j];
-      M[3 * i + j] = acc;
-    }
-  const double c = std::max(-1.0, std::min(1.0, 0.5 * (M[0] + M[4] + M[8] - 1.0)));
-  const double th = std::acos(c);
-  double ax[3] = {M[7] - M[5], M[2] - M[6], M[3] - M[1]};
-  const double n = std::sqrt(ax[0] * ax[0] + ax[1] * ax[1] + ax[2] * ax[2]);
-  if (n < 1e-15) {
-    std::memcpy(out->R, a.R, sizeof(out->R));
-    return;
-  }
-  for (double& v : ax) v /= n;
-  const double ts = s * th, cs = std::cos(ts), sn = std::sin(ts), C = 1 - cs;
-  const double x = ax[0], y = ax[1], z = ax[2];
-  const double Rr[9] = {cs + x * x * C, x * y * C - z * sn, x * z * C + y * sn, y * x * C + z * sn, cs + y * y * C,
-                        y * z * C - x * sn, z * x * C - y * sn, z * y * C + x * sn, cs + z * z * C};
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      double acc = 0;
-      for (int k = 0; k < 3; ++k) acc += a.R[3 * i + k] * Rr[3 * k + j];
-      out->R[3 * i + j] = acc;
-    }
+template <class R> static BatchExec<R>& exec_of(Env& env) { return *static_cast<BatchExec<R>*>(env.exec); }
+
+static void destroy_exec(Env& env) {
+  if (!env.exec) return;
+  if (env.precision == TC_FP64) delete static_cast<BatchExec<double>*>(env.exec);
+  else delete static_cast<BatchExec<float>*>(env.exec);
+  env.exec = nullptr;
 }
 
-// TACAUCHY_TRACE=1 prints one line per Newton iteration and substep to stderr.
-static bool trace_on() {
-  const char* v = std::getenv("TACAUCHY_TRACE");
-  return v && v[0] && v[0] != '0';
-}
-
-static double now_ms() {
-  using namespace std::chrono;
-  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
-}
-
-static tc_status read_scalars(Env& env) {
-  TC_CHECK(cudaMemcpyAsync(env.sc_host, env.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, env.stream));
-  TC_CHECK(cudaStreamSynchronize(env.stream));
-  if (env.prof) env.prof->collect();
-  if (env.sc_host->status & ST_NONFINITE) return TC_ERR_NONFINITE;
+template <class R> static tc_status make_exec(Env& env) {
+  auto* x = new (std::nothrow) BatchExec<R>();
+  if (!x) return TC_ERR_OOM;
+  x->arena = &env.arena;
+  x->stream = env.stream;
+  env.exec = x;
   return TC_OK;
-}
-
-// (Re)allocate the candidate lists for `cap` entries per gel primitive.
-static tc_status alloc_candidates(Env& env, int cap) {
-  Arena& a = env.arena;
-  const int n[3] = {env.nvc, env.nec, env.nfc};
-  for (int k = 0; k < 3; ++k) {
-    a.put(env.cand[k]);
-    a.put(env.cand_n[k]);
-    env.cand[k] = a.alloc<int32_t>((int64_t)cap * std::max(n[k], 1));
-    env.cand_n[k] = a.alloc<int32_t>(std::max(n[k], 1));
-    if (!env.cand[k] || !env.cand_n[k]) return TC_ERR_OOM;
-    TC_CHECK(cudaMemsetAsync(env.cand_n[k], 0, sizeof(int32_t) * std::max(n[k], 1), env.stream));
-  }
-  env.cand_cap = cap;
-  env.cand_valid = false;
-  return TC_OK;
-}
-
-// One CCD pass (gel moving by dir from pose a to pose b), which also rebuilds
-// the candidate lists; with `trial`, also the first line-search point
-// u + min(1, TOI) dir and its energy.  Grows the lists and repeats when a
-// primitive had more candidates than fit.
-template <class R>
-static tc_status ccd_pass(Env& env, const R* dir, const tc_pose& a, const tc_pose& b, bool trial) {
-  for (int attempt = 0; attempt < 16; ++attempt) {
-    EnvView<R> e = env.view<R>();
-    launch_ccd<R>(e, dir, a.R, a.t, b.R, b.t, env.stream);
-    if (trial) {
-      launch_trial<R>(e, (R*)env.utrial, env.stream);
-      launch_energy<R>(e, (R*)env.utrial, env.stream);
-    }
-    tc_status st = read_scalars(env);
-    if (st != TC_OK && st != TC_ERR_NONFINITE) return st;
-    const int need = env.sc_host->overflow;
-    if (need > env.cand_cap) {
-      int cap = env.cand_cap;
-      while (cap < need) cap *= 2;
-      TC_CHECK(cudaMemsetAsync(&env.sc->overflow, 0, sizeof(int), env.stream));
-      const tc_status sa = alloc_candidates(env, cap);
-      if (sa != TC_OK) return sa;
-      continue;
-    }
-    env.cand_valid = true;
-    return st;
-  }
-  return TC_ERR_CAPACITY;
-}
-
-// Candidate lists for the current state (static pass) if none are valid.
-template <class R> static tc_status ensure_candidates(Env& env) {
-  if (env.cand_valid) return TC_OK;
-  const tc_status st = ccd_pass<R>(env, nullptr, env.pose, env.pose, false);
-  return st == TC_ERR_NONFINITE ? TC_OK : st;
-}
-
-template <class R> static tc_status newton_solve(Env& env) {
-  double g0 = -1.0;
-  const int chunk = 8;
-  for (int it = 0; it < env.newton_max; ++it) {
-    const double t_iter0 = trace_on() ? now_ms() : 0.0;
-    EnvView<R> e = env.view<R>();
-    launch_elem<R>(e, true, e.u, env.stream);
-    launch_contact<R>(e, true, e.u, env.stream);
-    launch_assemble<R>(e, env.stream);
-    tc_status st = read_scalars(env);
-    if (st != TC_OK) return st;
-    const double E0 = env.sc_host->energy;
-    const double gn = std::sqrt(env.sc_host->gnorm2);
-    if (!std::isfinite(gn) || !std::isfinite(E0)) return TC_ERR_NONFINITE;
-    if (g0 < 0) g0 = gn;
-    env.stats.newton++;
-    if (gn <= std::max(env.rtol * g0, env.gabs)) return TC_OK;
-    double eta = std::min(0.5, std::sqrt(gn / std::max(g0, 1e-300)));
-    eta = std::max(eta, env.precision == TC_FP64 ? 1e-10 : 1e-5);
-    launch_pcg_init<R>(e, eta, env.stream);
-    if (!launch_pcg_persistent<R>(e, env.pcg_max, env.stream)) {
-      int done_iters = 0;
-      while (done_iters < env.pcg_max) {
-        const int n = std::min(chunk, env.pcg_max - done_iters);
-        for (int k = 0; k < n; ++k) launch_pcg_iter<R>(e, env.pcg_max, env.stream);
-        done_iters += n;
-        st = read_scalars(env);
-        if (st != TC_OK) return st;
-        if (env.sc_host->pcg_done) break;
-      }
-    }
-    // direction bound, CCD along dx (rebuilding the candidate lists), and
-    // the first trial point u + min(1, TOI) dx with its energy, all before
-    // the next host read
-    launch_pmax<R>(e, env.stream);
-    st = ccd_pass<R>(env, e.dx, env.pose, env.pose, true);
-    if (st != TC_OK && st != TC_ERR_NONFINITE) return st;
-    e = env.view<R>();
-    R* ut = (R*)env.utrial;
-    env.stats.pcg += env.sc_host->pcg_iters;
-    const int pcg_it = env.sc_host->pcg_iters;
-    const double pcg_rr = env.sc_host->rr, pcg_tol2 = env.sc_host->pcg_tol2;
-    const double t_pcg = trace_on() ? now_ms() : 0.0;
-    double alpha = std::min(1.0, env.sc_host->ccd_t);
-    if (trace_on())
-      std::fprintf(stderr,
-                   "[tc] newton %d E=%.17g |g|=%.6e g0=%.6e pcg=%d rr/tol=%.3e pq=%.3e rz=%.3e pmax=%.3e ccd=%.6f "
-                   "Etrial=%.17g dmin=%.3e st=%d t=%.2fms\n",
-                   it, E0, gn, g0, pcg_it, pcg_rr / std::max(pcg_tol2, 1e-300), env.sc_host->pq, env.sc_host->rz,
-                   env.sc_host->pmax, env.sc_host->ccd_t, env.sc_host->energy, std::sqrt(env.sc_host->reduce_tmp[1]),
-                   env.sc_host->status, t_pcg - t_iter0);
-    // Converged when the full step is below ptol, or when it is below 10 ptol
-    // and the predicted decrease -g.dx/2 is below the rounding level of the
-    // energy (the line search could no longer measure progress): the step is
-    // then taken without the energy test.
-    const double decrement = -0.5 * env.sc_host->reduce_tmp[3];
-    const double e_noise = (env.precision == TC_FP64 ? 1e-14 : 1e-7) * std::fabs(E0);
-    if (env.sc_host->pmax <= env.ptol || (env.sc_host->pmax <= 10.0 * env.ptol && decrement <= e_noise)) {
-      if (st == TC_ERR_NONFINITE) return st;
-      std::swap(env.u, env.utrial);
-      return TC_OK;
-    }
-    bool ok = false;
-    for (int ls = 0; ls <= 60; ++ls) {
-      if (ls > 0) {
-        launch_axpy_u<R>(e, ut, e.u, (R)alpha, e.dx, env.stream);
-        launch_energy<R>(e, ut, env.stream);
-        st = read_scalars(env);
-        if (st != TC_OK && st != TC_ERR_NONFINITE) return st;
-      }
-      const double Et = env.sc_host->energy;
-      if (st == TC_OK && std::isfinite(Et) && Et <= E0) {
-        ok = true;
-        break;
-      }
-      if (st == TC_ERR_NONFINITE) {  // a trial point outside the barrier's domain: clear and keep halving
-        int zero = 0;
-        TC_CHECK(cudaMemcpyAsync(&env.sc->status, &zero, sizeof(int), cudaMemcpyHostToDevice, env.stream));
-      }
-      alpha *= 0.5;
-      env.stats.halvings++;
-    }
-    if (trace_on())
-      std::fprintf(stderr, "[tc]   line search alpha=%.6e ok=%d E_trial=%.17g dE=%.3e\n", alpha, (int)ok,
-                   env.sc_host->energy, env.sc_host->energy - E0);
-    if (!ok) return TC_ERR_LINESEARCH;
-    std::swap(env.u, env.utrial);
-    // Noise floor: the full Newton step is within 10 ptol and the energy can
-    // no longer tell the trial point from the current one.
-    if (env.sc_host->energy == E0 && env.sc_host->pmax <= 10.0 * env.ptol) return TC_OK;
-  }
-  return TC_ERR_NEWTON_MAXITER;
 }
 
 template <class R> static tc_status do_step(Env& env, const tc_pose& target) {
-  const int64_t n3 = 3 * (int64_t)env.nv;
-  TC_CHECK(cudaMemcpyAsync(env.ut, env.u, sizeof(R) * n3, cudaMemcpyDeviceToDevice, env.stream));
-  if (env.dynamic) {  // u_tilde = u + h v
-    EnvView<R> e = env.view<R>();
-    launch_axpy_u<R>(e, (R*)env.utilde, (const R*)env.u, (R)env.dt, (const R*)env.vel, env.stream);
-  }
-  const tc_pose pose0 = env.pose;
-  double s = 0.0;
-  bool reached = false;
-  for (int sub = 0; sub < 256; ++sub) {
-    tc_pose ps;
-    pose_interp(pose0, target, s, &ps);
-    env.pose = ps;
-    EnvView<R> e = env.view<R>();
-    // indenter advance against the static gel (body frame: gel moves)
-    tc_status st = ccd_pass<R>(env, (const R*)nullptr, ps, target, false);
-    if (st != TC_OK) return st;
-    const double frac = env.sc_host->ccd_t;
-    s = frac >= 1.0 ? 1.0 : s + (1.0 - s) * frac;
-    if (trace_on()) std::fprintf(stderr, "[tc] substep %d advance frac=%.6e s=%.9f\n", sub, frac, s);
-    pose_interp(pose0, target, s, &env.pose);
-    st = newton_solve<R>(env);
-    env.stats.substeps++;
-    if (st != TC_OK) return st;
-    if (s >= 1.0) {
-      reached = true;
-      break;
-    }
-  }
-  if (!reached) return TC_ERR_NEWTON_MAXITER;
-  env.pose = target;
-  if (env.dynamic) {  // v = (u - u_t) / h
-    EnvView<R> e = env.view<R>();
-    launch_axpy_u<R>(e, (R*)env.vel, (const R*)env.u, (R)-1.0, (const R*)env.ut, env.stream);
-    launch_axpy_u<R>(e, (R*)env.vel, (R*)env.vel, (R)(1.0 / env.dt - 1.0), (const R*)env.vel, env.stream);
-  }
-  env.stats.steps++;
-  TC_CHECK(cudaStreamSynchronize(env.stream));
+  std::vector<Env*> one{&env};
+  std::vector<tc_pose> tg{target};
+  std::vector<tc_status> res;
+  tc_status st = step_batch<R>(exec_of<R>(env), one, tg, res);
   if (env.prof) env.prof->collect();
-  return TC_OK;
+  return st != TC_OK ? st : res[0];
 }
 
 template <class R> static tc_status alloc_state(Env& env) {
@@ -308,47 +83,31 @@ template <class R> static tc_status alloc_state(Env& env) {
     TC_CHECK(cudaMemsetAsync(env.vel, 0, sizeof(R) * 3 * nv, env.stream));
     TC_CHECK(cudaMemsetAsync(env.utilde, 0, sizeof(R) * 3 * nv, env.stream));
   }
-  const int nc = (int)(std::max(1, (env.nvc + 127) / 128) + std::max(1, (env.nec + 127) / 128) +
-                       std::max(1, (env.nfc + 127) / 128));
-  // per-block partials: element + contact + assembly passes, or 3 per block
-  // of the persistent PCG (at most grid_for(nt) + grid_for(nv) blocks)
-  const int nbt = (int)grid_for(nt), nbv = (int)grid_for(nv), nbq = (int)grid_for(8 * (nv + 3));
-  env.part_len = nbt + 2 * nc + 2 * nbq + 3 * (nbt + nbv) + nbq + 2 * nbv + 3 * nbv + 64;
-  env.part = a.alloc<double>(env.part_len);
   const tc_status sc0 = alloc_candidates(env, 32);
   if (sc0 != TC_OK) return sc0;
   env.face_p = a.alloc<float>(std::max(env.nfc, 1));
   env.face_A = a.alloc<float>(std::max(env.nfc, 1));
   env.vert_p = a.alloc<float>(std::max(env.nvc, 1));
-  if (!env.part || !env.face_p || !env.face_A || !env.vert_p) return TC_ERR_OOM;
+  if (!env.face_p || !env.face_A || !env.vert_p) return TC_ERR_OOM;
   return TC_OK;
 }
 
 template <class R> static tc_status initial_check(Env& env) {
-  tc_status sc0 = ensure_candidates<R>(env);
-  if (sc0 != TC_OK) return sc0;
-  EnvView<R> e = env.view<R>();
-  launch_energy<R>(e, e.u, env.stream);
-  tc_status st = read_scalars(env);
-  if (st != TC_OK) return st == TC_ERR_NONFINITE ? TC_ERR_INITIAL_PENETRATION : st;
-  if (!(env.sc_host->reduce_tmp[1] > 0.0)) return TC_ERR_INITIAL_PENETRATION;
+  Scalars sc{};
+  tc_status st = energy_at_state<R>(exec_of<R>(env), env, &sc);
+  if (st != TC_OK) return st;
+  if ((sc.status & ST_NONFINITE) || !(sc.reduce_tmp[1] > 0.0)) return TC_ERR_INITIAL_PENETRATION;
   int* flag = env.arena.alloc<int>(1);
   if (!flag) return TC_ERR_OOM;
-  const int hit = intersect_test<R>(e, flag, env.stream);
+  const int hit = intersect_test<R>(env.view<R>(), flag, env.stream);
   env.arena.put(flag);
   return hit ? TC_ERR_INITIAL_PENETRATION : TC_OK;
 }
 
 template <class R> static tc_status contact_force(Env& env, double* out) {
-  const tc_status sc0 = ensure_candidates<R>(env);
-  if (sc0 != TC_OK) return sc0;
-  EnvView<R> e = env.view<R>();
-  launch_contact<R>(e, true, e.u, env.stream);
-  launch_contact_force<R>(e, env.stream);
-  tc_status st = read_scalars(env);
-  if (st != TC_OK) return st;
-  for (int d = 0; d < 3; ++d) out[d] = env.sc_host->force[d];
-  return TC_OK;
+  const tc_status st = contact_force_at_state<R>(exec_of<R>(env), env, out);
+  if (env.prof) env.prof->collect();
+  return st;
 }
 
 template <class R> static tc_status pressure_map(Env& env, float* out, uint8_t* mask) {
@@ -480,7 +239,11 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
     }
   const double L2 = (hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) + (hi[2] - lo[2]) * (hi[2] - lo[2]);
   env.gabs = 1e-12 * env.E * L2;
-  tc_status st = TC_OK;
+  tc_status st = env.precision == TC_FP64 ? tc::make_exec<double>(env) : tc::make_exec<float>(env);
+  if (st != TC_OK) {
+    delete h;
+    return st;
+  }
   env.sc = env.arena.alloc<tc::Scalars>(1);
   if (!env.sc || cudaMallocHost(&env.sc_host, sizeof(tc::Scalars)) != cudaSuccess) st = TC_ERR_OOM;
   if (st == TC_OK && cudaMemsetAsync(env.sc, 0, sizeof(tc::Scalars), env.stream) != cudaSuccess) st = TC_ERR_CUDA;
@@ -506,6 +269,46 @@ tc_status tc_step(tc_env* h, const tc_pose* target) {
   tc_status st = env.precision == TC_FP64 ? tc::do_step<double>(env, *target) : tc::do_step<float>(env, *target);
   env.last_status = st;
   return st;
+}
+
+tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets, tc_status* statuses) {
+  if (n < 0 || (n > 0 && (!envs || !targets || !statuses))) return TC_ERR_INVALID_ARG;
+  if (n == 0) return TC_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!envs[i]) return TC_ERR_INVALID_ARG;
+    if (envs[i]->impl.precision != envs[0]->impl.precision || envs[i]->impl.device != envs[0]->impl.device)
+      return TC_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (envs[j] == envs[i]) return TC_ERR_INVALID_ARG;
+  }
+  std::vector<Env*> set;
+  std::vector<tc_pose> tg;
+  std::vector<int> idx;
+  for (int i = 0; i < n; ++i) {
+    if (!pose_ok(&targets[i])) {
+      statuses[i] = TC_ERR_NONFINITE;
+      continue;
+    }
+    set.push_back(&envs[i]->impl);
+    tg.push_back(targets[i]);
+    idx.push_back(i);
+  }
+  if (set.empty()) return TC_OK;
+  Env& lead = *set[0];
+  // every env's pending work must be complete before the lead stream runs
+  for (Env* e : set)
+    if (e->stream != lead.stream) cudaStreamSynchronize(e->stream);
+  tc::ProfGuard pg(lead);
+  std::vector<tc_status> res;
+  tc_status st = lead.precision == TC_FP64 ? tc::step_batch<double>(tc::exec_of<double>(lead), set, tg, res)
+                                           : tc::step_batch<float>(tc::exec_of<float>(lead), set, tg, res);
+  if (st != TC_OK) return st;
+  for (size_t k = 0; k < idx.size(); ++k) {
+    statuses[idx[k]] = res[k];
+    set[k]->last_status = res[k];
+  }
+  if (lead.prof) lead.prof->collect();
+  return TC_OK;
 }
 
 tc_status tc_stress(tc_env* h, float* sigma_out) {
@@ -646,6 +449,7 @@ void tc_destroy(tc_env* h) {
   cudaStreamSynchronize(env.stream);
   delete env.prof;
   env.prof = nullptr;
+  tc::destroy_exec(env);
   env.arena.release_all();
   cudaStreamSynchronize(env.stream);
   if (env.sc_host) cudaFreeHost(env.sc_host);

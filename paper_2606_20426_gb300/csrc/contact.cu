@@ -29,6 +29,7 @@
 #include "env.cuh"
 #include "geom.cuh"
 #include "prof.cuh"
+#include "solver.cuh"
 
 namespace tc {
 
@@ -246,11 +247,15 @@ TC_D void pair_points(const EnvView<R>& e, const Vec3<T>* xg, int ip, const Orig
 // One contact primitive pass over the candidate lists built by the last CCD
 // pass.  MODE 0: energy only; 1: energy + slots.
 template <class R, int GK, int MODE>
-__global__ void __launch_bounds__(128) k_contact(const EnvView<R> e, const R* __restrict__ u, double* part_out) {
+__global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int NG = 3 * NGP;
   constexpr int NH = NG * (NG + 1) / 2;
-  const int prim = blockIdx.x * blockDim.x + threadIdx.x;
+  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
+  const EnvView<R>& e = bv.views[lc.env];
+  const R* __restrict__ u = trial ? e.ut : e.u;
+  double* part_out = bv.part + L.cont[GK];
+  const int prim = lc.chunk * 128 + threadIdx.x;
   const int n = prim_count(e, GK);
   double energy = 0.0;
   double dmin2 = 1e300;
@@ -345,19 +350,18 @@ template <class R> struct ContactGrid {
   static unsigned blocks(int n) { return (unsigned)std::max(1, (n + 127) / 128); }
 };
 
-// Partials layout in e.part: [elem blocks][contact V][contact E][contact F],
-// each contact block writing (energy, dmin2).
-template <class R> void launch_contact(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s) {
-  const unsigned bv = ContactGrid<R>::blocks(e.nvc), be = ContactGrid<R>::blocks(e.nec), bf = ContactGrid<R>::blocks(e.nfc);
-  double* base = e.part + grid_for(e.nt);
-  if (with_hessian) {
-    TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<bv, 128, 0, s>>>(e, u_eval, base));
-    TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<be, 128, 0, s>>>(e, u_eval, base + 2 * bv));
-    TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<bf, 128, 0, s>>>(e, u_eval, base + 2 * (bv + be)));
+// (energy, min d^2) per unit into the contact partial regions
+template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s) {
+  const int t = trial ? 1 : 0;
+  const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
+  if (hess) {
+    if (nv) TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<nv, 128, 0, s>>>(b.bv, b.L, t));
+    if (ne) TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<ne, 128, 0, s>>>(b.bv, b.L, t));
+    if (nf) TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<nf, 128, 0, s>>>(b.bv, b.L, t));
   } else {
-    TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<bv, 128, 0, s>>>(e, u_eval, base));
-    TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<be, 128, 0, s>>>(e, u_eval, base + 2 * bv));
-    TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<bf, 128, 0, s>>>(e, u_eval, base + 2 * (bv + be)));
+    if (nv) TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<nv, 128, 0, s>>>(b.bv, b.L, t));
+    if (ne) TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<ne, 128, 0, s>>>(b.bv, b.L, t));
+    if (nf) TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<nf, 128, 0, s>>>(b.bv, b.L, t));
   }
 }
 
@@ -366,16 +370,16 @@ template <class R> void launch_contact(const EnvView<R>& e, bool with_hessian, c
 // indenter is static there); additive CCD per candidate pair in type R on
 // coordinates relative to the primitive's first gel point.
 
-struct Motion {
-  double Ra[9], ta[3], Rb[9], tb[3];
-};
-
 template <class R, int GK>
-__global__ void __launch_bounds__(128) k_ccd(const EnvView<R> e, const R* __restrict__ dir, const Motion mo,
-                                            double* part_out) {
+__global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
-  const int prim = blockIdx.x * blockDim.x + threadIdx.x;
+  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
+  const EnvView<R>& e = bv.views[lc.env];
+  const Motion& mo = bv.motion[lc.env];
+  const R* __restrict__ dir = mo.use_dir ? e.dx : nullptr;
+  double* part_out = bv.part + L.ccd[GK];
+  const int prim = lc.chunk * 128 + threadIdx.x;
   const int n = prim_count(e, GK);
   double tmin = 1.0;
   if (prim < n) {
@@ -432,34 +436,36 @@ __global__ void __launch_bounds__(128) k_ccd(const EnvView<R> e, const R* __rest
   if (threadIdx.x == 0) part_out[blockIdx.x] = tmin;
 }
 
-__global__ void k_min_partials(const double* part, int n, double* out) {
+// per env: min TOI over its contact units -> ccd_t
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_ccd_env(const BatchView<R> bv, PartLayout L) {
+  const int env = blockIdx.x;
   double m = 1.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmin(m, part[i]);
+  for (int k = 0; k < 3; ++k) {
+    const int* p = bv.prefix + (K_CV + k) * (bv.nenv + 1);
+    for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) m = fmin(m, bv.part[L.ccd[k] + u]);
+  }
   m = block_min<kBlock>(m);
-  if (threadIdx.x == 0) *out = m;
+  if (threadIdx.x == 0) bv.views[env].sc->ccd_t = m;
 }
 
-template <class R>
-void launch_ccd(const EnvView<R>& e, const R* dir, const double* Ra, const double* ta, const double* Rb, const double* tb,
-                cudaStream_t s) {
-  const unsigned bv = ContactGrid<R>::blocks(e.nvc), be = ContactGrid<R>::blocks(e.nec), bf = ContactGrid<R>::blocks(e.nfc);
-  double* base = e.part;
-  Motion mo;
-  for (int k = 0; k < 9; ++k) { mo.Ra[k] = Ra[k]; mo.Rb[k] = Rb[k]; }
-  for (int k = 0; k < 3; ++k) { mo.ta[k] = ta[k]; mo.tb[k] = tb[k]; }
-  TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<bv, 128, 0, s>>>(e, dir, mo, base));
-  TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<be, 128, 0, s>>>(e, dir, mo, base + bv));
-  TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<bf, 128, 0, s>>>(e, dir, mo, base + bv + be));
-  TC_LAUNCH("k_min_partials", s, k_min_partials<<<1, kBlock, 0, s>>>(base, (int)(bv + be + bf), &e.sc->ccd_t));
+template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s) {
+  const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
+  if (nv) TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<nv, 128, 0, s>>>(b.bv, b.L));
+  if (ne) TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<ne, 128, 0, s>>>(b.bv, b.L));
+  if (nf) TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<nf, 128, 0, s>>>(b.bv, b.L));
+  TC_LAUNCH("k_ccd_env", s, k_ccd_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
 }
 
 // ------------------------------------------------------------ contact force
 // f = -sum over all gel points of the barrier gradient (Algorithm 2:
 // f_k = -g_k / dt^2 with the potential scaled by dt^2).
 template <class R>
-__global__ void k_force(const EnvView<R> e, double* out) {
+__global__ void k_force(const BatchView<R> bv) {
+  const EnvView<R>& e = bv.views[blockIdx.x];
+  double* out = e.sc->force;
   double f[3] = {0, 0, 0};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < e.nvc + e.nec + e.nfc; i += gridDim.x * blockDim.x) {
+  for (int i = threadIdx.x; i < e.nvc + e.nec + e.nfc; i += blockDim.x) {
     if (i < e.nvc) {
       for (int d = 0; d < 3; ++d) f[d] -= (double)e.cv_slot[(int64_t)d * e.nvc + i];
     } else if (i < e.nvc + e.nec) {
@@ -478,8 +484,8 @@ __global__ void k_force(const EnvView<R> e, double* out) {
   }
 }
 
-template <class R> void launch_contact_force(const EnvView<R>& e, cudaStream_t s) {
-  TC_LAUNCH("k_force", s, k_force<R><<<1, kBlock, 0, s>>>(e, e.sc->force));
+template <class R> void b_force(const BatchHost<R>& b, cudaStream_t s) {
+  TC_LAUNCH("k_force", s, k_force<R><<<b.nenv, kBlock, 0, s>>>(b.bv));
 }
 
 // ------------------------------------------------------ intersection test
@@ -543,14 +549,12 @@ template <class R> int intersect_test(const EnvView<R>& e, int* dflag, cudaStrea
   return h;
 }
 
-template void launch_contact<float>(const EnvView<float>&, bool, const float*, cudaStream_t);
-template void launch_contact<double>(const EnvView<double>&, bool, const double*, cudaStream_t);
-template void launch_ccd<float>(const EnvView<float>&, const float*, const double*, const double*, const double*,
-                                const double*, cudaStream_t);
-template void launch_ccd<double>(const EnvView<double>&, const double*, const double*, const double*, const double*,
-                                 const double*, cudaStream_t);
-template void launch_contact_force<float>(const EnvView<float>&, cudaStream_t);
-template void launch_contact_force<double>(const EnvView<double>&, cudaStream_t);
+template void b_contact<float>(const BatchHost<float>&, bool, bool, cudaStream_t);
+template void b_contact<double>(const BatchHost<double>&, bool, bool, cudaStream_t);
+template void b_ccd<float>(const BatchHost<float>&, cudaStream_t);
+template void b_ccd<double>(const BatchHost<double>&, cudaStream_t);
+template void b_force<float>(const BatchHost<float>&, cudaStream_t);
+template void b_force<double>(const BatchHost<double>&, cudaStream_t);
 template int intersect_test<float>(const EnvView<float>&, int*, cudaStream_t);
 template int intersect_test<double>(const EnvView<double>&, int*, cudaStream_t);
 

@@ -19,6 +19,7 @@
 // them to zero leaves the projected Newton method converging only linearly.
 #include "env.cuh"
 #include "prof.cuh"
+#include "solver.cuh"
 
 namespace tc {
 
@@ -228,8 +229,11 @@ TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R H[45]
 
 // K1: energy (per-block partial), gradient slots, H9, diagonal-block slots.
 template <class R, bool HESS>
-__global__ void __launch_bounds__(kBlock) k_elem(const EnvView<R> e, const R* __restrict__ u) {
-  const int el = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayout L, int trial) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_TET, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const R* __restrict__ u = trial ? e.ut : e.u;
+  const int el = l.chunk * kBlock + threadIdx.x;
   double energy = 0.0;
   if (el < e.nt) {
     const int4 t = e.tets[el];
@@ -283,12 +287,13 @@ __global__ void __launch_bounds__(kBlock) k_elem(const EnvView<R> e, const R* __
     }
   }
   energy = block_sum<kBlock>(energy);
-  if (threadIdx.x == 0) e.part[blockIdx.x] = energy;
+  if (threadIdx.x == 0) bv.part[L.elem + blockIdx.x] = energy;
 }
 
-template <class R> void launch_elem(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s) {
-  if (with_hessian) TC_LAUNCH("k_elem_hess", s, k_elem<R, true><<<grid_for(e.nt), kBlock, 0, s>>>(e, u_eval));
-  else TC_LAUNCH("k_elem_energy", s, k_elem<R, false><<<grid_for(e.nt), kBlock, 0, s>>>(e, u_eval));
+template <class R> void b_elem(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s) {
+  if (b.units[K_TET] == 0) return;
+  if (hess) TC_LAUNCH("k_elem_hess", s, k_elem<R, true><<<b.units[K_TET], kBlock, 0, s>>>(b.bv, b.L, trial ? 1 : 0));
+  else TC_LAUNCH("k_elem_energy", s, k_elem<R, false><<<b.units[K_TET], kBlock, 0, s>>>(b.bv, b.L, trial ? 1 : 0));
 }
 
 // ---------------------------------------------------------------- stress (K8)
@@ -361,8 +366,8 @@ void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, fl
   TC_LAUNCH("k_stress_from_F", s, k_stress_from_F<<<(unsigned)blocks, kBlock, 0, s>>>(F, n, mu, lam_hat, sigma));
 }
 
-template void launch_elem<float>(const EnvView<float>&, bool, const float*, cudaStream_t);
-template void launch_elem<double>(const EnvView<double>&, bool, const double*, cudaStream_t);
+template void b_elem<float>(const BatchHost<float>&, bool, bool, cudaStream_t);
+template void b_elem<double>(const BatchHost<double>&, bool, bool, cudaStream_t);
 template void launch_stress<float>(const EnvView<float>&, float*, cudaStream_t);
 template void launch_stress<double>(const EnvView<double>&, float*, cudaStream_t);
 

@@ -64,7 +64,11 @@ template <class R> struct EnvView {
   // per vertex
   const R* mass;              // nv (dynamic) or null
   R* u;                       // 3 x nv displacement
-  const R* utilde;            // 3 x nv (dynamic)
+  R* ut;                      // 3 x nv line-search trial displacement
+  R* utilde;                  // 3 x nv inertial target u_t + h v (dynamic)
+  R* u0;                      // 3 x nv displacement at the start of the step
+  R* vel;                     // 3 x nv velocity (dynamic)
+  double dt;                  // time step (<= 0: quasi-static)
   R* g;                       // 3 x nv gradient
   R* Minv;                    // 6 x nv block-Jacobi inverse (xx,yy,zz,xy,yz,zx)
   R *dx, *r, *z, *p, *q;      // 3 x nv PCG vectors
@@ -98,10 +102,64 @@ template <class R> struct EnvView {
   int32_t* cand_n[3];
   int cand_cap;
   double Rm[9], tr[3];        // current indenter pose (world = R body + t)
-  // reductions
-  double* part;               // per-block partials
-  Scalars* sc;
+  Scalars* sc;                // this env's scalars (per phase in a batch)
 };
+
+// ------------------------------------------------------------ batching
+//
+// Every Newton phase runs as one launch over all envs taking part in it.
+// Work is cut into units (one block each) of one item kind; per kind, a
+// prefix table over the batch's envs maps a block to (env, chunk).  Per-unit
+// partial sums are folded per env, in unit order, by per-env finalize kernels,
+// so results do not depend on scheduling or on the batch composition.
+
+enum Kind : int {
+  K_TET = 0,   // tets, 256 per unit
+  K_VERT,      // vertices, 256 per unit
+  K_VGRP,      // vertices gathered by 8-lane groups, 32 per unit
+  K_CV,        // contact vertices, 128 per unit
+  K_CE,        // contact edges, 128 per unit
+  K_CF,        // contact faces, 128 per unit
+  K_NKIND
+};
+
+TC_HD int unit_items(int kind) {
+  return kind == K_VGRP ? 32 : (kind >= K_CV ? 128 : 256);
+}
+
+// Indenter motion of one env for a CCD pass: gel positions (moved by dx when
+// use_dir) seen from pose (Ra, ta) at the start and (Rb, tb) at the end.
+struct Motion {
+  double Ra[9], ta[3], Rb[9], tb[3];
+  int use_dir;
+};
+
+template <class R> struct BatchView {
+  const EnvView<R>* views;   // nenv device views
+  int nenv;
+  const int* prefix;         // K_NKIND rows of nenv + 1 unit offsets
+  double* part;              // per-unit partials (layout chosen by the launcher)
+  const double* param;       // per-env scalar parameter (eta, alpha), or null
+  const Motion* motion;      // per-env CCD motion, or null
+};
+
+struct Loc {
+  int env, chunk;
+};
+
+// block -> (env, chunk) for one kind (binary search over the prefix row)
+TC_D Loc locate(const int* prefix, int nenv, int kind, int unit) {
+  const int* p = prefix + kind * (nenv + 1);
+  int lo = 0, hi = nenv - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p[mid] <= unit) lo = mid;
+    else hi = mid - 1;
+  }
+  return {lo, unit - p[lo]};
+}
+
+TC_HD int units_for(int count, int kind) { return (count + unit_items(kind) - 1) / unit_items(kind); }
 
 struct EnvStats {
   int64_t newton = 0, pcg = 0, substeps = 0, steps = 0, halvings = 0;
@@ -159,15 +217,14 @@ struct Env {
   void* utrial = nullptr;
   // extraction scratch (float)
   float *sigma = nullptr, *face_p = nullptr, *face_A = nullptr, *vert_p = nullptr;
-  double* part = nullptr;
-  int part_len = 0;
-  Scalars* sc = nullptr;      // device
+  Scalars* sc = nullptr;      // device (setup checks)
   Scalars* sc_host = nullptr; // pinned host mirror
   // host copies of integer outputs
   std::vector<int32_t> h_bfaces, h_bparent, h_cfaces, h_cparent, h_pix_face;
   std::vector<float> h_pix_w;
   int last_status = TC_OK;
   Profiler* prof = nullptr;  // per-kernel timing, null unless enabled
+  void* exec = nullptr;      // BatchExec<R> of this env (batches of one)
 
   template <class R> EnvView<R> view() const;
 };
@@ -181,7 +238,8 @@ template <class R> EnvView<R> Env::view() const {
   e.dhat = dhat; e.kappa = kappa;
   e.tets = tets; e.X0 = X0; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
   e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.H9 = (R*)H9; e.eslot = (R*)eslot; e.yslot = (R*)yslot;
-  e.mass = (const R*)mass; e.u = (R*)u; e.utilde = (const R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
+  e.mass = (const R*)mass; e.u = (R*)u; e.ut = (R*)utrial; e.utilde = (R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
+  e.u0 = (R*)ut; e.vel = (R*)vel; e.dt = dynamic ? dt : 0.0;
   e.dx = (R*)dx; e.r = (R*)r; e.z = (R*)z; e.p = (R*)p; e.q = (R*)q;
   e.cverts = cverts; e.cedges = cedges; e.cfaces = cfaces; e.vslot = vslot;
   e.cv_face_off = cv_face_off; e.cv_face_idx = cv_face_idx; e.cv_edge_off = cv_edge_off; e.cv_edge_idx = cv_edge_idx;
@@ -201,7 +259,7 @@ template <class R> EnvView<R> Env::view() const {
   e.grid.inv_cell = grid_inv_cell;
   for (int k = 0; k < 9; ++k) e.Rm[k] = pose.R[k];
   for (int k = 0; k < 3; ++k) e.tr[k] = pose.t[k];
-  e.part = part; e.sc = sc;
+  e.sc = sc;
   return e;
 }
 
@@ -212,25 +270,6 @@ tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32
                       const tc_trimesh* ind, const tc_grid* grid);
 tc_status check_initial(Env& env);
 
-// Element pass (energy, gradient slots, PSD H9, diagonal slots); energy only.
-template <class R> void launch_elem(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s);
-// Contact pass (energy + per-primitive slots) at displacement u_eval.
-template <class R> void launch_contact(const EnvView<R>& e, bool with_hessian, const R* u_eval, cudaStream_t s);
-// Assemble gradient + preconditioner; writes sc->energy, sc->gnorm2.
-template <class R> void launch_assemble(const EnvView<R>& e, cudaStream_t s);
-// Total energy at u_eval (elastic + contact + inertia) into sc->energy.
-template <class R> void launch_energy(const EnvView<R>& e, const R* u_eval, cudaStream_t s);
-// PCG pieces.
-template <class R> void launch_pcg_init(const EnvView<R>& e, double eta, cudaStream_t s);
-template <class R> void launch_pcg_iter(const EnvView<R>& e, int max_iter, cudaStream_t s);
-template <class R> bool launch_pcg_persistent(const EnvView<R>& e, int max_iter, cudaStream_t s);
-template <class R> void launch_trial(const EnvView<R>& e, R* out, cudaStream_t s);
-template <class R> void launch_pmax(const EnvView<R>& e, cudaStream_t s);
-// CCD: gel moving by alpha_max * dx with a fixed indenter (line search), or
-// the indenter moving from pose a to pose b with a static gel.
-template <class R> void launch_ccd(const EnvView<R>& e, const R* dir, const double* Ra, const double* ta,
-                                   const double* Rb, const double* tb, cudaStream_t s);
-template <class R> void launch_axpy_u(const EnvView<R>& e, R* out, const R* u, R alpha, const R* d, cudaStream_t s);
 // Extraction.
 template <class R> void launch_stress(const EnvView<R>& e, float* sigma, cudaStream_t s);
 template <class R> void launch_traction(const EnvView<R>& e, const int32_t* cparent, float* t, float* p, float* tt,
@@ -240,7 +279,6 @@ void launch_vertex_avg(int nvc, const int32_t* off, const int32_t* idx, const fl
                        float* vert_p, cudaStream_t s);
 void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const int32_t* cface_slot, int nfc,
                   const float* vert_p, float* out, uint8_t* mask, cudaStream_t s);
-template <class R> void launch_contact_force(const EnvView<R>& e, cudaStream_t s);
 void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, float alpha, float* sigma,
                           cudaStream_t s);
 

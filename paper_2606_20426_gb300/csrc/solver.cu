@@ -1,54 +1,35 @@
-// Newton-step kernels: per-vertex assembly (K4), matrix-free block-Jacobi
-// PCG (K5), energy reductions for the line search (K7), step updates.
+// Newton-step kernels over a batch of envs: per-vertex assembly (K4),
+// matrix-free block-Jacobi PCG (K5), energies for the line search (K7) and
+// step updates.
 //
 // Assembly and SpMV are atomic-free: element and contact passes write their
-// per-element / per-primitive contributions to slots, and one thread per
-// vertex sums its incident slots through fixed incidence lists, so results
-// do not depend on scheduling.  All dot products accumulate in double;
-// block partials are combined in a fixed order by every block that needs the
-// scalar (no separate finalize launch).
+// per-element / per-primitive contributions to slots, and one lane group per
+// vertex sums its incident slots through fixed incidence lists.  Every block
+// reduction writes one partial per work unit; per-env finalize blocks fold an
+// env's partials in unit order.  Dot products and energies accumulate in
+// double.  Results do not depend on the batch composition or the schedule.
 #include <cooperative_groups.h>
 
 #include "env.cuh"
 #include "prof.cuh"
+#include "solver.cuh"
 
 namespace cg = cooperative_groups;
 
 namespace tc {
 
-// ------------------------------------------------------------------ helpers
-
-// Sum of partials[0..n) in a fixed order, computed by every block that needs
-// it (n is a few hundred at most per env phase).
-TC_D double sum_partials(const double* part, int n, int stride = 1, int offset = 0) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[(int64_t)i * stride + offset];
-  return block_sum<kBlock>(s);
-}
-
-__shared__ double s_bcast;
-
-TC_D double bcast(double v) {
-  if (threadIdx.x == 0) s_bcast = v;
-  __syncthreads();
-  const double r = s_bcast;
-  __syncthreads();
-  return r;
-}
-
-// Per-vertex gathers are done by a group of kLanes consecutive lanes: each
-// lane sums every kLanes-th incidence and the group combines the partial sums
-// with a fixed shuffle tree (deterministic), which gives the gathers kLanes
-// times more independent loads in flight than one thread per vertex.
+// Per-vertex gathers use a group of kLanes consecutive lanes: each lane sums
+// every kLanes-th incidence and the group combines the partial sums with a
+// fixed shuffle tree (deterministic), giving kLanes times more independent
+// loads in flight than one thread per vertex.
 constexpr int kLanes = 8;
+static_assert(kBlock / kLanes == 32, "K_VGRP units hold 32 vertices");
 
 template <class T> TC_D T group_sum(T v) {
 #pragma unroll
   for (int o = kLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, kLanes);
   return v;
 }
-
-TC_HD int round_up(int n, int m) { return (n + m - 1) / m * m; }
 
 template <class R> struct Sym3 {
   R xx, yy, zz, xy, yz, zx;
@@ -64,17 +45,38 @@ template <class R> TC_D void add_packed_block(Sym3<R>& D, const R* slot, int64_t
   D.zx += slot[(int64_t)sym_index(b + 2, b + 0, N) * stride + prim];
 }
 
+// An env's per-unit partials part[u * stride + offset], u over its units of
+// `kind`, folded in unit order by one block.
+template <class R>
+TC_D double env_unit_sum(const BatchView<R>& bv, int kind, int env, const double* part, int stride = 1,
+                         int offset = 0) {
+  const int* p = bv.prefix + kind * (bv.nenv + 1);
+  double s = 0.0;
+  for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) s += part[(int64_t)u * stride + offset];
+  return block_sum<kBlock>(s);
+}
+template <class R>
+TC_D double env_unit_min(const BatchView<R>& bv, int kind, int env, const double* part, int stride = 1,
+                         int offset = 0) {
+  const int* p = bv.prefix + kind * (bv.nenv + 1);
+  double s = 1e300;
+  for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) s = fmin(s, part[(int64_t)u * stride + offset]);
+  return block_min<kBlock>(s);
+}
+
 // ---------------------------------------------------------------- assembly
 // g_v = sum of element and contact gradient slots (+ inertia), 3x3 diagonal
-// block -> inverse for block-Jacobi.  part layout: [0..nb) gnorm2, [nb..2nb)
-// inertia energy.
+// block -> inverse for block-Jacobi.  Partials per K_VGRP unit: |g|^2 and the
+// inertia energy 1/(2h^2)|u - u_tilde|_M^2.
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_assemble(const EnvView<R> e, double* part) {
+__global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, PartLayout L) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VGRP, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
   const int lane = threadIdx.x & (kLanes - 1);
-  const int v = (blockIdx.x * blockDim.x + threadIdx.x) / kLanes;
-  const bool valid = v < e.nv;
-  double gn2 = 0.0, ein = 0.0;
+  const int v = l.chunk * 32 + threadIdx.x / kLanes;
   const int nt = e.nt, nv = e.nv;
+  const bool valid = v < nv;
+  double gn2 = 0.0, ein = 0.0;
   R g[3] = {0, 0, 0};
   Sym3<R> D{0, 0, 0, 0, 0, 0};
   if (valid) {
@@ -97,14 +99,14 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const EnvView<R> e, double*
         add_packed_block<R>(D, e.cv_slot + 3 * (int64_t)e.nvc, e.nvc, s, 0, 3);
       }
       for (int k = e.cv_edge_off[s] + lane; k < e.cv_edge_off[s + 1]; k += kLanes) {
-        const int code = e.cv_edge_idx[k], p = code >> 2, l = code & 3;
-        for (int i = 0; i < 3; ++i) g[i] += e.ce_slot[(int64_t)(3 * l + i) * e.nec + p];
-        add_packed_block<R>(D, e.ce_slot + 6 * (int64_t)e.nec, e.nec, p, l, 6);
+        const int code = e.cv_edge_idx[k], p = code >> 2, q = code & 3;
+        for (int i = 0; i < 3; ++i) g[i] += e.ce_slot[(int64_t)(3 * q + i) * e.nec + p];
+        add_packed_block<R>(D, e.ce_slot + 6 * (int64_t)e.nec, e.nec, p, q, 6);
       }
       for (int k = e.cv_face_off[s] + lane; k < e.cv_face_off[s + 1]; k += kLanes) {
-        const int code = e.cv_face_idx[k], p = code >> 2, l = code & 3;
-        for (int i = 0; i < 3; ++i) g[i] += e.cf_slot[(int64_t)(3 * l + i) * e.nfc + p];
-        add_packed_block<R>(D, e.cf_slot + 9 * (int64_t)e.nfc, e.nfc, p, l, 9);
+        const int code = e.cv_face_idx[k], p = code >> 2, q = code & 3;
+        for (int i = 0; i < 3; ++i) g[i] += e.cf_slot[(int64_t)(3 * q + i) * e.nfc + p];
+        add_packed_block<R>(D, e.cf_slot + 9 * (int64_t)e.nfc, e.nfc, p, q, 9);
       }
     }
   }
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const EnvView<R> e, double*
   D.yz = group_sum(D.yz);
   D.zx = group_sum(D.zx);
   if (valid && lane == 0) {
-    if (e.mass) {  // inertia 1/(2h^2) |u - u_tilde|_M^2
+    if (e.mass) {
       const R mh = e.mass[v] * e.inv_h2;
       for (int i = 0; i < 3; ++i) {
         const R du = e.u[i * nv + v] - e.utilde[i * nv + v];
@@ -163,77 +165,70 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const EnvView<R> e, double*
   gn2 = block_sum<kBlock>(gn2);
   ein = block_sum<kBlock>(ein);
   if (threadIdx.x == 0) {
-    part[blockIdx.x] = gn2;
-    part[gridDim.x + blockIdx.x] = ein;
+    bv.part[L.asmb + 2 * (int64_t)blockIdx.x] = gn2;
+    bv.part[L.asmb + 2 * (int64_t)blockIdx.x + 1] = ein;
   }
 }
 
-// total energy = elastic partials + contact partials + inertia partials
-__global__ void k_energy_total(const double* part_elem, int ne, const double* part_contact, int nc,
-                               const double* part_in, int ni, int in_stride_off, Scalars* sc, int write_gn2,
-                               const double* part_gn2) {
-  double s = 0.0;
-  for (int i = threadIdx.x; i < ne; i += blockDim.x) s += part_elem[i];
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) s += part_contact[2 * i];
-  for (int i = threadIdx.x; i < ni; i += blockDim.x) s += part_in[in_stride_off + i];
-  s = block_sum<kBlock>(s);
-  double g = 0.0;
-  if (write_gn2)
-    for (int i = threadIdx.x; i < ni; i += blockDim.x) g += part_gn2[i];
-  g = block_sum<kBlock>(g);
-  double dm = 1e300;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) dm = fmin(dm, part_contact[2 * i + 1]);
-  dm = block_min<kBlock>(dm);
-  if (threadIdx.x == 0) {
-    sc->energy = s;
-    if (write_gn2) sc->gnorm2 = g;
-    sc->reduce_tmp[1] = dm;  // min squared pair distance seen by the contact pass
-    if (!isfinite(s)) sc->status |= ST_NONFINITE;
-  }
-}
-
-static unsigned contact_blocks(int n) { return (unsigned)std::max(1, (n + 127) / 128); }
-
-template <class R> static int n_contact_blocks(const EnvView<R>& e) {
-  return (int)(contact_blocks(e.nvc) + contact_blocks(e.nec) + contact_blocks(e.nfc));
-}
-
-// part layout during assembly: [elem nb_t][contact 2*nc][assemble gn2 nb_v][assemble inertia nb_v]
-template <class R> void launch_assemble(const EnvView<R>& e, cudaStream_t s) {
-  const int nbt = (int)grid_for(e.nt), nc = n_contact_blocks(e);
-  const int nba = (int)grid_for((int64_t)round_up(e.nv, kWarp / kLanes) * kLanes);
-  double* pa = e.part + nbt + 2 * nc;
-  TC_LAUNCH("k_assemble", s, k_assemble<R><<<nba, kBlock, 0, s>>>(e, pa));
-  TC_LAUNCH("k_energy_total", s, k_energy_total<<<1, kBlock, 0, s>>>(e.part, nbt, e.part + nbt, nc, pa, nba, nba, e.sc, 1, pa));
-}
-
-// inertia energy only (line-search trial)
+// inertia energy at the trial point (K_VERT units)
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_inertia(const EnvView<R> e, const R* __restrict__ u, double* part) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) k_inertia(const BatchView<R> bv, PartLayout L) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const int v = l.chunk * kBlock + threadIdx.x;
   double ein = 0.0;
   if (v < e.nv && e.mass) {
     const R mh = e.mass[v] * e.inv_h2;
     for (int i = 0; i < 3; ++i) {
-      const double du = (double)u[i * e.nv + v] - (double)e.utilde[i * e.nv + v];
+      const double du = (double)e.ut[i * e.nv + v] - (double)e.utilde[i * e.nv + v];
       ein += 0.5 * (double)mh * du * du;
     }
   }
   ein = block_sum<kBlock>(ein);
-  if (threadIdx.x == 0) part[blockIdx.x] = ein;
+  if (threadIdx.x == 0) bv.part[L.inert + blockIdx.x] = ein;
 }
 
-template <class R> void launch_energy(const EnvView<R>& e, const R* u_eval, cudaStream_t s) {
-  const int nbt = (int)grid_for(e.nt), nbv = (int)grid_for(e.nv), nc = n_contact_blocks(e);
-  launch_elem<R>(e, false, u_eval, s);
-  launch_contact<R>(e, false, u_eval, s);
-  double* pa = e.part + nbt + 2 * nc;
-  TC_LAUNCH("k_inertia", s, k_inertia<R><<<nbv, kBlock, 0, s>>>(e, u_eval, pa));
-  TC_LAUNCH("k_energy_total", s, k_energy_total<<<1, kBlock, 0, s>>>(e.part, nbt, e.part + nbt, nc, pa, nbv, 0, e.sc, 0, nullptr));
+// per env: total energy (elastic + contact + inertia), min pair distance and
+// (after assembly) |g|^2 -> the env's Scalars
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_finalize_energy(const BatchView<R> bv, PartLayout L, int assembly) {
+  const int env = blockIdx.x;
+  const EnvView<R>& e = bv.views[env];
+  double E = env_unit_sum(bv, K_TET, env, bv.part + L.elem);
+  double dm = 1e300;
+  for (int k = 0; k < 3; ++k) {
+    E += env_unit_sum(bv, K_CV + k, env, bv.part + L.cont[k], 2, 0);
+    dm = fmin(dm, env_unit_min(bv, K_CV + k, env, bv.part + L.cont[k], 2, 1));
+  }
+  double gn2 = 0.0;
+  if (assembly) {
+    E += env_unit_sum(bv, K_VGRP, env, bv.part + L.asmb, 2, 1);
+    gn2 = env_unit_sum(bv, K_VGRP, env, bv.part + L.asmb, 2, 0);
+  } else {
+    E += env_unit_sum(bv, K_VERT, env, bv.part + L.inert);
+  }
+  if (threadIdx.x == 0) {
+    e.sc->energy = E;
+    if (assembly) e.sc->gnorm2 = gn2;
+    e.sc->reduce_tmp[1] = dm;  // min squared pair distance seen by the contact pass
+    if (!isfinite(E)) e.sc->status |= ST_NONFINITE;
+  }
 }
 
-// --------------------------------------------------------------------- PCG
-// Layout of e.part during PCG: [0, nbv) p.q; [nbv, 2 nbv) r.z; [2 nbv, 3 nbv) r.r
+template <class R> void b_assemble(const BatchHost<R>& b, cudaStream_t s) {
+  if (b.units[K_VGRP] > 0) TC_LAUNCH("k_assemble", s, k_assemble<R><<<b.units[K_VGRP], kBlock, 0, s>>>(b.bv, b.L));
+  TC_LAUNCH("k_finalize_energy", s, k_finalize_energy<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L, 1));
+}
+
+// energy at the trial displacement ut (elastic + contact + inertia)
+template <class R> void b_trial_energy(const BatchHost<R>& b, cudaStream_t s) {
+  b_elem<R>(b, false, true, s);
+  b_contact<R>(b, false, true, s);
+  if (b.units[K_VERT] > 0) TC_LAUNCH("k_inertia", s, k_inertia<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
+  TC_LAUNCH("k_finalize_energy", s, k_finalize_energy<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L, 0));
+}
+
+// ------------------------------------------------------------------ PCG
 
 template <class R> TC_D void apply_minv(const EnvView<R>& e, int v, const R r[3], R z[3]) {
   const int nv = e.nv;
@@ -244,9 +239,12 @@ template <class R> TC_D void apply_minv(const EnvView<R>& e, int v, const R r[3]
   z[2] = m5 * r[0] + m4 * r[1] + m2 * r[2];
 }
 
+// r = -g, z = M^-1 r, p = z, dx = 0; partials r.z, r.r per K_VERT unit
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_init(const EnvView<R> e) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, PartLayout L) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const int v = l.chunk * kBlock + threadIdx.x;
   const int nv = e.nv;
   double rz = 0.0, rr = 0.0;
   if (v < nv) {
@@ -264,24 +262,33 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(const EnvView<R> e) {
   }
   rz = block_sum<kBlock>(rz);
   rr = block_sum<kBlock>(rr);
-  const int nbv = gridDim.x;
   if (threadIdx.x == 0) {
-    e.part[nbv + blockIdx.x] = rz;
-    e.part[2 * nbv + blockIdx.x] = rr;
+    bv.part[L.rz + blockIdx.x] = rz;
+    bv.part[L.rr + blockIdx.x] = rr;
   }
 }
 
-__global__ void k_pcg_init_scalars(const double* part, int nbv, Scalars* sc, double eta, int max_iter) {
-  const double rz = sum_partials(part + nbv, nbv);
-  const double rr = sum_partials(part + 2 * nbv, nbv);
+// per env: r.z, r.r and the squared stopping tolerance (param[env]) ->
+// published scalars
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, PartLayout L) {
+  const int env = blockIdx.x;
+  const EnvView<R>& e = bv.views[env];
+  const double rz = env_unit_sum(bv, K_VERT, env, bv.part + L.rz);
+  const double rr = env_unit_sum(bv, K_VERT, env, bv.part + L.rr);
   if (threadIdx.x == 0) {
+    Scalars* sc = e.sc;
     if (!isfinite(rz) || !isfinite(rr)) sc->status |= ST_NONFINITE;
-    sc->rz = rz;
-    sc->rz_next = rz;
-    sc->rr = rr;
-    sc->pcg_tol2 = eta * eta * sc->gnorm2;
-    sc->pcg_done = (rr <= sc->pcg_tol2 || max_iter <= 0) ? 1 : 0;
-    sc->pcg_iters = 0;
+    const double tol2 = bv.param[env];
+    double* es = bv.part + L.env_s + 8 * env;
+    es[0] = 0.0;
+    es[1] = 0.0;
+    es[2] = rz;
+    es[3] = rr;
+    es[4] = 0.0;
+    es[5] = (rr <= tol2) ? 1.0 : 0.0;
+    es[6] = 0.0;
+    es[7] = tol2;
   }
 }
 
@@ -325,14 +332,6 @@ template <class R> TC_D void spmv_elem_one(const EnvView<R>& e, int el) {
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kBlock) k_spmv_elem(const EnvView<R> e) {
-  if (e.sc->pcg_done) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) e.sc->rz = e.sc->rz_next;
-  const int el = blockIdx.x * blockDim.x + threadIdx.x;
-  if (el < e.nt) spmv_elem_one<R>(e, el);
-}
-
 // contact share of A p per primitive: y = H_prim p_prim
 template <class R, int NGP>
 TC_D void contact_spmv_prim(const EnvView<R>& e, const R* slot, int n, int prim, const int* verts, R* yout) {
@@ -352,30 +351,24 @@ TC_D void contact_spmv_prim(const EnvView<R>& e, const R* slot, int n, int prim,
   for (int a = 0; a < NG; ++a) yout[(int64_t)a * n + prim] = y[a];
 }
 
-template <class R> TC_D void spmv_contact_one(const EnvView<R>& e, int i) {
-  if (i < e.nvc) {
+template <class R> TC_D void spmv_contact_one(const EnvView<R>& e, int kind, int i) {
+  if (kind == K_CV) {
+    if (i >= e.nvc) return;
     const int v[1] = {e.cverts[i]};
     contact_spmv_prim<R, 1>(e, e.cv_slot, e.nvc, i, v, e.cv_y);
-  } else if (i < e.nvc + e.nec) {
-    const int p = i - e.nvc;
-    const int v[2] = {e.cedges[p], e.cedges[e.nec + p]};
-    contact_spmv_prim<R, 2>(e, e.ce_slot, e.nec, p, v, e.ce_y);
-  } else if (i < e.nvc + e.nec + e.nfc) {
-    const int p = i - e.nvc - e.nec;
-    const int v[3] = {e.cfaces[p], e.cfaces[e.nfc + p], e.cfaces[2 * e.nfc + p]};
-    contact_spmv_prim<R, 3>(e, e.cf_slot, e.nfc, p, v, e.cf_y);
+  } else if (kind == K_CE) {
+    if (i >= e.nec) return;
+    const int v[2] = {e.cedges[i], e.cedges[e.nec + i]};
+    contact_spmv_prim<R, 2>(e, e.ce_slot, e.nec, i, v, e.ce_y);
+  } else {
+    if (i >= e.nfc) return;
+    const int v[3] = {e.cfaces[i], e.cfaces[e.nfc + i], e.cfaces[2 * e.nfc + i]};
+    contact_spmv_prim<R, 3>(e, e.cf_slot, e.nfc, i, v, e.cf_y);
   }
 }
 
-template <class R>
-__global__ void __launch_bounds__(kBlock) k_spmv_contact(const EnvView<R> e) {
-  if (e.sc->pcg_done) return;
-  spmv_contact_one<R>(e, blockIdx.x * blockDim.x + threadIdx.x);
-}
-
 // q = A p at vertex v gathered by a lane group; returns p.q on the group's
-// lane 0 (0 elsewhere).  Every lane of the warp calls it (valid may differ
-// per group).
+// lane 0 (0 elsewhere).  Every lane of the warp calls it.
 template <class R> TC_D double pcg_q_group(const EnvView<R>& e, int v, bool valid) {
   const int lane = threadIdx.x & (kLanes - 1);
   const int nv = e.nv, nt = e.nt;
@@ -416,156 +409,143 @@ template <class R> TC_D double pcg_q_group(const EnvView<R>& e, int v, bool vali
   return pq;
 }
 
-// Per-iteration kernels (used when a cooperative launch is unavailable).
-// Partials: part[0, nbq) p.q, part[nbq, nbq + nbv) r.z, then r.r.
-template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_q(const EnvView<R> e) {
-  if (e.sc->pcg_done) return;
-  const int v = (blockIdx.x * blockDim.x + threadIdx.x) / kLanes;
-  double pq = pcg_q_group<R>(e, v, v < e.nv);
-  pq = block_sum<kBlock>(pq);
-  if (threadIdx.x == 0) e.part[blockIdx.x] = pq;
-}
-
-// dx += alpha p, r -= alpha q, z = M^-1 r; partials r.z, r.r
-template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_update(const EnvView<R> e, int nbq) {
-  if (e.sc->pcg_done) return;
-  const int nbv = gridDim.x;
-  const double pq = bcast(sum_partials(e.part, nbq));
-  const double alpha = pq > 0.0 ? e.sc->rz / pq : 0.0;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nv = e.nv;
-  double rz = 0.0, rr = 0.0;
-  if (v < nv) {
-    R r[3], z[3];
-    for (int i = 0; i < 3; ++i) {
-      e.dx[i * nv + v] += (R)alpha * e.p[i * nv + v];
-      r[i] = e.r[i * nv + v] - (R)alpha * e.q[i * nv + v];
-      e.r[i * nv + v] = r[i];
-    }
-    apply_minv<R>(e, v, r, z);
-    for (int i = 0; i < 3; ++i) {
-      e.z[i * nv + v] = z[i];
-      rz += (double)r[i] * (double)z[i];
-      rr += (double)r[i] * (double)r[i];
-    }
-  }
-  rz = block_sum<kBlock>(rz);
-  rr = block_sum<kBlock>(rr);
-  if (threadIdx.x == 0) {
-    e.part[nbq + blockIdx.x] = rz;
-    e.part[nbq + nbv + blockIdx.x] = rr;
-    if (blockIdx.x == 0) e.sc->pq = pq;
-  }
-}
-
-// beta = rz_new / rz; p = z + beta p; convergence flag (block 0 writes)
-template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_p(const EnvView<R> e, int max_iter, int nbq) {
-  if (e.sc->pcg_done) return;
-  const int nbv = gridDim.x;
-  const double rz_new = bcast(sum_partials(e.part + nbq, nbv));
-  const double rr = bcast(sum_partials(e.part + nbq + nbv, nbv));
-  const double rz_old = e.sc->rz;
-  const double beta = rz_old > 0.0 ? rz_new / rz_old : 0.0;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nv = e.nv;
-  if (v < nv)
-    for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + (R)beta * e.p[i * nv + v];
-  // sc->rz is read by every block above, so the new value goes to rz_next;
-  // k_spmv_elem (next iteration, where nobody reads rz) moves it into rz.
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    Scalars* sc = e.sc;
-    sc->rz_next = rz_new;
-    sc->rr = rr;
-    sc->pcg_iters += 1;
-    if (rr <= sc->pcg_tol2 || sc->pcg_iters >= max_iter || !(sc->pq > 0.0) || !isfinite(rr)) sc->pcg_done = 1;
-  }
-}
-
 // ------------------------------------------------------ persistent PCG
-// All iterations in one cooperative launch: grid-stride element / contact
-// SpMV, per-vertex gather, then the vector updates, separated by grid-wide
-// barriers (four per iteration).  Each block sums the per-block partials in
-// the same fixed order, so alpha, beta and the stopping test are identical in
-// every block and no scalar is shared through global memory mid-iteration.
-// Partials: part[0, G) p.q, part[G, 2G) r.z, part[2G, 3G) r.r (G = gridDim.x).
-
-TC_D double sum_part_all(const double* part, int n) {
-  // every thread of the block gets the same value
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
-  s = block_sum<kBlock>(s);
-  return bcast(s);
-}
+// All CG iterations of all envs of the batch in one cooperative launch.  Per
+// iteration: element + contact SpMV | gather q = A p (p.q partials) | per-env
+// alpha | vector update (r.z, r.r partials) | per-env beta and stop test |
+// direction update, with grid-wide syncs between the phases.  Per-env scalars
+// are folded by one block per env and published through global memory before
+// the next sync, so every block reads the same values; converged envs skip
+// their work while the others continue.  Published scalars, 8 per env at
+// part + env_s: alpha, beta, r.z, r.r, p.q, done (0 running, 1 stopped before
+// the iteration, 2 stopped in it), iterations, tolerance^2.
 
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_persistent(const EnvView<R> e, int max_iter) {
+__global__ void __launch_bounds__(kBlock) k_pcg_batched(const BatchView<R> bv, PartLayout L, int max_iter) {
   cg::grid_group grid = cg::this_grid();
   const int G = gridDim.x;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nth = G * blockDim.x;
-  const int nv = e.nv, nc = e.nvc + e.nec + e.nfc;
-  const int nv_pad = round_up(nv, kWarp / kLanes);
-  double rz = e.sc->rz;
-  const double tol2 = e.sc->pcg_tol2;
-  int it = 0;
-  bool done = e.sc->pcg_done != 0;
-  double rr = e.sc->rr, pq = 0.0;
-  while (!done && it < max_iter) {
-    for (int el = tid; el < e.nt; el += nth) spmv_elem_one<R>(e, el);
-    for (int i = tid; i < nc; i += nth) spmv_contact_one<R>(e, i);
-    grid.sync();
-    double lpq = 0.0;
-    for (int v = tid / kLanes; v < nv_pad; v += nth / kLanes) lpq += pcg_q_group<R>(e, v, v < nv);
-    lpq = block_sum<kBlock>(lpq);
-    if (threadIdx.x == 0) e.part[blockIdx.x] = lpq;
-    grid.sync();
-    pq = sum_part_all(e.part, G);
-    const double alpha = pq > 0.0 ? rz / pq : 0.0;
-    double lrz = 0.0, lrr = 0.0;
-    for (int v = tid; v < nv; v += nth) {
-      R r[3], z[3];
-      for (int i = 0; i < 3; ++i) {
-        e.dx[i * nv + v] += (R)alpha * e.p[i * nv + v];
-        r[i] = e.r[i * nv + v] - (R)alpha * e.q[i * nv + v];
-        e.r[i * nv + v] = r[i];
+  const int nenv = bv.nenv;
+  double* es = bv.part + L.env_s;
+  const int* pre = bv.prefix;
+  const int nT = pre[K_TET * (nenv + 1) + nenv];
+  const int nC[3] = {pre[K_CV * (nenv + 1) + nenv], pre[K_CE * (nenv + 1) + nenv], pre[K_CF * (nenv + 1) + nenv]};
+  const int nG = pre[K_VGRP * (nenv + 1) + nenv];
+  const int nV = pre[K_VERT * (nenv + 1) + nenv];
+  for (int it = 0; it < max_iter; ++it) {
+    int all_done = 1;
+    for (int env = 0; env < nenv; ++env) all_done &= es[8 * env + 5] != 0.0;
+    if (all_done) break;
+    // 1. SpMV
+    for (int u = blockIdx.x; u < nT; u += G) {
+      const Loc l = locate(pre, nenv, K_TET, u);
+      if (es[8 * l.env + 5] != 0.0) continue;
+      const EnvView<R>& e = bv.views[l.env];
+      const int el = l.chunk * kBlock + threadIdx.x;
+      if (el < e.nt) spmv_elem_one<R>(e, el);
+    }
+    for (int k = 0; k < 3; ++k)
+      for (int u = blockIdx.x; u < nC[k]; u += G) {
+        const Loc l = locate(pre, nenv, K_CV + k, u);
+        if (es[8 * l.env + 5] != 0.0) continue;
+        if (threadIdx.x < unit_items(K_CV + k))
+          spmv_contact_one<R>(bv.views[l.env], K_CV + k, l.chunk * unit_items(K_CV + k) + threadIdx.x);
       }
-      apply_minv<R>(e, v, r, z);
-      for (int i = 0; i < 3; ++i) {
-        e.z[i * nv + v] = z[i];
-        lrz += (double)r[i] * (double)z[i];
-        lrr += (double)r[i] * (double)r[i];
+    grid.sync();
+    // 2. gather q = A p; partial p.q per unit
+    for (int u = blockIdx.x; u < nG; u += G) {
+      const Loc l = locate(pre, nenv, K_VGRP, u);
+      double pq = 0.0;
+      if (es[8 * l.env + 5] == 0.0) {
+        const EnvView<R>& e = bv.views[l.env];
+        const int v = l.chunk * 32 + threadIdx.x / kLanes;
+        pq = pcg_q_group<R>(e, v, v < e.nv);
+      }
+      pq = block_sum<kBlock>(pq);
+      if (threadIdx.x == 0) bv.part[L.pq + u] = pq;
+    }
+    grid.sync();
+    // 3. per-env alpha = r.z / p.q
+    for (int env = blockIdx.x; env < nenv; env += G) {
+      const double pq = env_unit_sum(bv, K_VGRP, env, bv.part + L.pq);
+      if (threadIdx.x == 0 && es[8 * env + 5] == 0.0) {
+        es[8 * env + 4] = pq;
+        es[8 * env + 0] = pq > 0.0 ? es[8 * env + 2] / pq : 0.0;
       }
     }
-    lrz = block_sum<kBlock>(lrz);
-    lrr = block_sum<kBlock>(lrr);
+    grid.sync();
+    // 4. dx += alpha p, r -= alpha q, z = M^-1 r; partials r.z, r.r
+    for (int u = blockIdx.x; u < nV; u += G) {
+      const Loc l = locate(pre, nenv, K_VERT, u);
+      double rz = 0.0, rr = 0.0;
+      if (es[8 * l.env + 5] == 0.0) {
+        const EnvView<R>& e = bv.views[l.env];
+        const int nv = e.nv;
+        const int v = l.chunk * kBlock + threadIdx.x;
+        const R alpha = (R)es[8 * l.env + 0];
+        if (v < nv) {
+          R r[3], z[3];
+          for (int i = 0; i < 3; ++i) {
+            e.dx[i * nv + v] += alpha * e.p[i * nv + v];
+            r[i] = e.r[i * nv + v] - alpha * e.q[i * nv + v];
+            e.r[i * nv + v] = r[i];
+          }
+          apply_minv<R>(e, v, r, z);
+          for (int i = 0; i < 3; ++i) {
+            e.z[i * nv + v] = z[i];
+            rz += (double)r[i] * (double)z[i];
+            rr += (double)r[i] * (double)r[i];
+          }
+        }
+      }
+      rz = block_sum<kBlock>(rz);
+      rr = block_sum<kBlock>(rr);
+      if (threadIdx.x == 0) {
+        bv.part[L.rz + u] = rz;
+        bv.part[L.rr + u] = rr;
+      }
+    }
+    grid.sync();
+    // 5. per-env beta and stop test
+    for (int env = blockIdx.x; env < nenv; env += G) {
+      const double rz_new = env_unit_sum(bv, K_VERT, env, bv.part + L.rz);
+      const double rr = env_unit_sum(bv, K_VERT, env, bv.part + L.rr);
+      if (threadIdx.x == 0 && es[8 * env + 5] == 0.0) {
+        const double rz_old = es[8 * env + 2];
+        es[8 * env + 1] = rz_old > 0.0 ? rz_new / rz_old : 0.0;
+        es[8 * env + 2] = rz_new;
+        es[8 * env + 3] = rr;
+        es[8 * env + 6] += 1.0;
+        const double pq = es[8 * env + 4];
+        const bool done = rr <= es[8 * env + 7] || !(pq > 0.0) || !isfinite(rr) || es[8 * env + 6] >= max_iter;
+        es[8 * env + 5] = done ? 2.0 : 0.0;
+      }
+    }
+    grid.sync();
+    // 6. p = z + beta p for envs still running
+    for (int u = blockIdx.x; u < nV; u += G) {
+      const Loc l = locate(pre, nenv, K_VERT, u);
+      if (es[8 * l.env + 5] != 0.0) continue;
+      const EnvView<R>& e = bv.views[l.env];
+      const int nv = e.nv;
+      const int v = l.chunk * kBlock + threadIdx.x;
+      const R beta = (R)es[8 * l.env + 1];
+      if (v < nv)
+        for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + beta * e.p[i * nv + v];
+    }
+    grid.sync();
+  }
+  // publish per-env results
+  for (int env = blockIdx.x; env < nenv; env += G)
     if (threadIdx.x == 0) {
-      e.part[G + blockIdx.x] = lrz;
-      e.part[2 * G + blockIdx.x] = lrr;
+      Scalars* sc = bv.views[env].sc;
+      sc->pcg_iters = (int)es[8 * env + 6];
+      sc->rz = es[8 * env + 2];
+      sc->rr = es[8 * env + 3];
+      sc->pq = es[8 * env + 4];
+      sc->pcg_tol2 = es[8 * env + 7];
+      sc->pcg_done = 1;
+      if (!isfinite(sc->rr) || !isfinite(sc->pq)) sc->status |= ST_NONFINITE;
     }
-    grid.sync();
-    const double rz_new = sum_part_all(e.part + G, G);
-    rr = sum_part_all(e.part + 2 * G, G);
-    const double beta = rz > 0.0 ? rz_new / rz : 0.0;
-    rz = rz_new;
-    ++it;
-    done = rr <= tol2 || !(pq > 0.0) || !isfinite(rr);
-    if (!done && it < max_iter) {
-      for (int v = tid; v < nv; v += nth)
-        for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + (R)beta * e.p[i * nv + v];
-      grid.sync();
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (!isfinite(rr) || !isfinite(pq)) e.sc->status |= ST_NONFINITE;
-    e.sc->pcg_iters = it;
-    e.sc->rz = rz;
-    e.sc->rr = rr;
-    e.sc->pq = pq;
-    e.sc->pcg_done = 1;
-  }
 }
 
 template <class R> struct CoopInfo {
@@ -576,53 +556,37 @@ template <class R> struct CoopInfo {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<R>, kBlock, 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched<R>, kBlock, 0);
       cached = coop ? sms * per_sm : 0;
     }
     return cached;
   }
 };
 
-// Runs the whole PCG solve; returns false if a cooperative launch is not
-// available (the caller then uses the per-iteration kernels).
-template <class R> bool launch_pcg_persistent(const EnvView<R>& e, int max_iter, cudaStream_t s) {
+template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s) {
+  if (b.units[K_VERT] > 0) TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
+  TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
   const int cap = CoopInfo<R>::max_blocks();
-  if (cap <= 0) return false;
-  const int64_t work = std::max<int64_t>(e.nt, std::max<int64_t>(e.nv, e.nvc + e.nec + e.nfc));
-  int G = (int)std::min<int64_t>((work + kBlock - 1) / kBlock, cap);
-  G = std::max(G, 1);
-  // 3 G partials must fit: part holds at least 3 * grid_for(nv) + the element blocks
-  G = std::min(G, (int)(grid_for(e.nt) + grid_for(e.nv)));
-  EnvView<R> ev = e;
+  if (cap <= 0) return TC_ERR_CUDA;
+  int work = std::max(b.units[K_TET], std::max(b.units[K_VGRP], b.units[K_VERT]));
+  work = std::max(work, std::max(b.nenv, b.units[K_CV] + b.units[K_CE] + b.units[K_CF]));
+  const int G = std::max(1, std::min(work, cap));
+  BatchView<R> bv = b.bv;
+  PartLayout L = b.L;
   int mi = max_iter;
-  void* args[] = {(void*)&ev, (void*)&mi};
-  cudaError_t err;
-  TC_LAUNCH("k_pcg_persistent", s,
-            err = cudaLaunchCooperativeKernel((void*)k_pcg_persistent<R>, dim3(G), dim3(kBlock), args, 0, s));
-  return err == cudaSuccess;
+  void* args[] = {(void*)&bv, (void*)&L, (void*)&mi};
+  cudaError_t err = cudaSuccess;
+  TC_LAUNCH("k_pcg_batched", s,
+            err = cudaLaunchCooperativeKernel((void*)k_pcg_batched<R>, dim3(G), dim3(kBlock), args, 0, s));
+  return err == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
-template <class R> void launch_pcg_init(const EnvView<R>& e, double eta, cudaStream_t s) {
-  const int nbv = (int)grid_for(e.nv);
-  TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<nbv, kBlock, 0, s>>>(e));
-  TC_LAUNCH("k_pcg_init_scalars", s, k_pcg_init_scalars<<<1, kBlock, 0, s>>>(e.part, nbv, e.sc, eta, 1 << 30));
-}
+// ------------------------------------------------------ per-env reductions
 
-template <class R> void launch_pcg_iter(const EnvView<R>& e, int max_iter, cudaStream_t s) {
-  const int nbv = (int)grid_for(e.nv);
-  TC_LAUNCH("k_spmv_elem", s, k_spmv_elem<R><<<grid_for(e.nt), kBlock, 0, s>>>(e));
-  const int nc = e.nvc + e.nec + e.nfc;
-  if (nc > 0) TC_LAUNCH("k_spmv_contact", s, k_spmv_contact<R><<<grid_for(nc), kBlock, 0, s>>>(e));
-  const int nbq = (int)grid_for((int64_t)round_up(e.nv, kWarp / kLanes) * kLanes);
-  TC_LAUNCH("k_pcg_q", s, k_pcg_q<R><<<nbq, kBlock, 0, s>>>(e));
-  TC_LAUNCH("k_pcg_update", s, k_pcg_update<R><<<nbv, kBlock, 0, s>>>(e, nbq));
-  TC_LAUNCH("k_pcg_p", s, k_pcg_p<R><<<nbv, kBlock, 0, s>>>(e, max_iter, nbq));
-}
-
-// max-norm of dx -> sc->pmax, and g.dx (minus the Newton decrement)
-// -> sc->reduce_tmp[3]
+// max-norm of dx -> pmax, and g.dx (minus twice the Newton decrement)
 template <class R>
-__global__ void k_pmax(const EnvView<R> e) {
+__global__ void __launch_bounds__(kBlock) k_pmax(const BatchView<R> bv) {
+  const EnvView<R>& e = bv.views[blockIdx.x];
   double m = 0.0, gd = 0.0;
   for (int v = threadIdx.x; v < e.nv; v += blockDim.x)
     for (int i = 0; i < 3; ++i) {
@@ -639,39 +603,58 @@ __global__ void k_pmax(const EnvView<R> e) {
   }
 }
 
-template <class R> void launch_pmax(const EnvView<R>& e, cudaStream_t s) { k_pmax<R><<<1, kBlock, 0, s>>>(e); }
+template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s) {
+  TC_LAUNCH("k_pmax", s, k_pmax<R><<<b.nenv, kBlock, 0, s>>>(b.bv));
+}
 
+// trial point ut = u + alpha dx; alpha = min(1, TOI) when param < 0 (or no
+// param), else param
 template <class R>
-__global__ void k_axpy(int n3, R* out, const R* u, R alpha, const R* d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n3) out[i] = u[i] + alpha * d[i];
+__global__ void __launch_bounds__(kBlock) k_trial(const BatchView<R> bv) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const double a = bv.param ? bv.param[l.env] : -1.0;
+  const R alpha = (R)(a < 0.0 ? fmin(1.0, e.sc->ccd_t) : a);
+  const int v = l.chunk * kBlock + threadIdx.x;
+  if (v < e.nv)
+    for (int i = 0; i < 3; ++i) e.ut[i * e.nv + v] = e.u[i * e.nv + v] + alpha * e.dx[i * e.nv + v];
 }
 
-template <class R> void launch_axpy_u(const EnvView<R>& e, R* out, const R* u, R alpha, const R* d, cudaStream_t s) {
-  TC_LAUNCH("k_axpy", s, k_axpy<R><<<grid_for(3 * (int64_t)e.nv), kBlock, 0, s>>>(3 * e.nv, out, u, alpha, d));
+template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s) {
+  if (b.units[K_VERT] > 0) TC_LAUNCH("k_trial", s, k_trial<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv));
 }
 
-// first line-search trial: alpha = min(1, TOI) read on the device
+// mode 0 (step start): u0 = u and, when dynamic, utilde = u + dt vel;
+// mode 1 (step end, dynamic): vel = (u - u0) / dt
 template <class R>
-__global__ void k_trial(int n3, R* out, const R* u, const R* d, const Scalars* sc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const R alpha = (R)fmin(1.0, sc->ccd_t);
-  if (i < n3) out[i] = u[i] + alpha * d[i];
+__global__ void __launch_bounds__(kBlock) k_step_vectors(const BatchView<R> bv, int mode) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const int v = l.chunk * kBlock + threadIdx.x;
+  if (v >= e.nv) return;
+  for (int i = 0; i < 3; ++i) {
+    const int k = i * e.nv + v;
+    if (mode == 0) {
+      e.u0[k] = e.u[k];
+      if (e.dt > 0.0) e.utilde[k] = e.u[k] + (R)e.dt * e.vel[k];
+    } else if (e.dt > 0.0) {
+      e.vel[k] = (R)((double)(e.u[k] - e.u0[k]) / e.dt);
+    }
+  }
 }
 
-template <class R> void launch_trial(const EnvView<R>& e, R* out, cudaStream_t s) {
-  TC_LAUNCH("k_trial", s, k_trial<R><<<grid_for(3 * (int64_t)e.nv), kBlock, 0, s>>>(3 * e.nv, out, e.u, e.dx, e.sc));
+template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStream_t s) {
+  if (b.units[K_VERT] > 0)
+    TC_LAUNCH("k_step_vectors", s, k_step_vectors<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, mode));
 }
 
-#define TC_INST(R)                                                                              \
-  template void launch_assemble<R>(const EnvView<R>&, cudaStream_t);                            \
-  template void launch_energy<R>(const EnvView<R>&, const R*, cudaStream_t);                    \
-  template void launch_pcg_init<R>(const EnvView<R>&, double, cudaStream_t);                    \
-  template void launch_pcg_iter<R>(const EnvView<R>&, int, cudaStream_t);                       \
-  template bool launch_pcg_persistent<R>(const EnvView<R>&, int, cudaStream_t);                 \
-  template void launch_trial<R>(const EnvView<R>&, R*, cudaStream_t);                           \
-  template void launch_pmax<R>(const EnvView<R>&, cudaStream_t);                                \
-  template void launch_axpy_u<R>(const EnvView<R>&, R*, const R*, R, const R*, cudaStream_t);
+#define TC_INST(R)                                                            \
+  template void b_assemble<R>(const BatchHost<R>&, cudaStream_t);             \
+  template void b_trial_energy<R>(const BatchHost<R>&, cudaStream_t);         \
+  template tc_status b_pcg<R>(const BatchHost<R>&, int, cudaStream_t);        \
+  template void b_pmax<R>(const BatchHost<R>&, cudaStream_t);                 \
+  template void b_trial<R>(const BatchHost<R>&, cudaStream_t);                \
+  template void b_step_vectors<R>(const BatchHost<R>&, int, cudaStream_t);
 TC_INST(float)
 TC_INST(double)
 #undef TC_INST

@@ -1,0 +1,39 @@
+// Host-side description of one batched launch and the launcher entry points.
+#pragma once
+#include "env.cuh"
+
+namespace tc {
+
+// Offsets (in doubles) of the per-unit partial regions of a batch.
+struct PartLayout {
+  int64_t elem;      // K_TET units: element energy
+  int64_t cont[3];   // K_CV / K_CE / K_CF units: (energy, min d^2)
+  int64_t asmb;      // K_VGRP units: (|g|^2, inertia energy)
+  int64_t inert;     // K_VERT units: trial inertia energy
+  int64_t ccd[3];    // contact units: min TOI
+  int64_t pq;        // K_VGRP units: p.q
+  int64_t rz, rr;    // K_VERT units
+  int64_t env_s;     // 8 per env: PCG scalars published between phases
+  int64_t total;
+};
+
+template <class R> struct BatchHost {
+  int nenv = 0;
+  int units[K_NKIND] = {0, 0, 0, 0, 0, 0};
+  BatchView<R> bv{};
+  PartLayout L{};
+};
+
+template <class R> void b_elem(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s);
+template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s);
+template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s);
+template <class R> void b_force(const BatchHost<R>& b, cudaStream_t s);
+template <class R> void b_assemble(const BatchHost<R>& b, cudaStream_t s);
+template <class R> void b_trial_energy(const BatchHost<R>& b, cudaStream_t s);
+template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s);
+template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s);
+template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s);
+// mode 0: u0 = u and (dynamic) utilde = u + dt vel; mode 1: vel = (u - u0) / dt
+template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStream_t s);
+
+}  // namespace tc

@@ -21,7 +21,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "initial penetra
           10: "admission", 11: "timeout", 12: "capacity"}
 
 # every symbol include/tacauchy.h declares
-EXPORTS = ["tc_create_scene", "tc_step", "tc_stress", "tc_traction", "tc_pressure_map", "tc_contact_force",
+EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_traction", "tc_pressure_map", "tc_contact_force",
            "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
            "tc_profile_read", "tc_pressure_map_noalloc"]
@@ -98,6 +98,7 @@ def load():
                             ctypes.POINTER(TriMesh), ctypes.POINTER(Pose), ctypes.POINTER(SceneOpts),
                             ctypes.POINTER(Grid), ctypes.POINTER(Allocator), P, ctypes.POINTER(P)],
         "tc_step": [P, ctypes.POINTER(Pose)],
+        "tc_step_batch": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(Pose), ctypes.POINTER(ctypes.c_int32)],
         "tc_stress": [P, P],
         "tc_traction": [P, P, P, P],
         "tc_pressure_map": [P, P, P],
@@ -307,6 +308,28 @@ class Env:
             self.close()
         except Exception:
             pass
+
+
+def step_batch(envs, poses, raise_on_error=False):
+    """One step of each env in `envs` toward the matching pose, all Newton
+    phases launched once over the whole batch (tc_step_batch).  Returns the
+    list of per-env status codes; with raise_on_error the first non-zero one
+    raises TcError."""
+    envs = list(envs)
+    poses = list(poses)
+    if len(envs) != len(poses):
+        raise ValueError("one pose per env")
+    n = len(envs)
+    lib = load()
+    handles = (ctypes.c_void_p * max(n, 1))(*[e.h for e in envs])
+    targets = (Pose * max(n, 1))(*[make_pose(p) for p in poses])
+    statuses = (ctypes.c_int32 * max(n, 1))()
+    _check(lib.tc_step_batch(handles, n, targets, statuses), "tc_step_batch")
+    out = [int(statuses[i]) for i in range(n)]
+    if raise_on_error:
+        for code in out:
+            _check(code, "tc_step_batch")
+    return out
 
 
 def stress_from_F(F, E, nu, out=None, stream=None):
