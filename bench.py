@@ -44,21 +44,16 @@ def peaks():
 
 
 def pcg_iteration_bytes(info):
-    """Algorithmic bytes of one PCG iteration of one env (FP32): element SpMV
-    (tet ids 16, Dm^-1 36, volume 4, H9 180 read, 12 slot values 48 written, p
-    read once per vertex), contact SpMV (per primitive: ids, packed block,
-    result), per-vertex gather of the slots (CSR offset, incidence id and 3
-    values per incidence; q written), the update (dx, r read+write; p, q,
-    M^-1 read; z written) and the direction update (z, p read; p written)."""
-    nt, nv = info["nt"], info["nv"]
-    nvc, nec, nfc = info["nvc"], info["nec"], info["nfc"]
-    deg = 4.0 * nt / nv
-    spmv = nt * (16 + 36 + 4 + 180 + 48) + 12 * nv
-    contact = nvc * (4 + 24 + 12 + 12) + nec * (8 + 84 + 24 + 24) + nfc * (12 + 180 + 36 + 36)
-    gather = nv * (4 + deg * (4 + 12) + 12 + 12 + 1)
-    update = nv * (24 + 24 + 12 + 12 + 24 + 12)
-    pupdate = nv * (12 + 24)
-    return spmv + contact + gather + update + pupdate
+    """Algorithmic bytes of one PCG iteration of one env (FP32): the BSR
+    product q = A p (per 3x3 block 36 B of values + 4 B column id; row offsets
+    4 B and p 12 B read, q 12 B written per vertex), the vector update (dx, r
+    read + write 48 B; p, q 24 B and M^-1 24 B read; z 12 B written) and the
+    direction update (z, p read 24 B; p written 12 B)."""
+    nv, nnzb = info["nv"], info["nnzb"]
+    spmv = nnzb * 40 + nv * (4 + 12 + 12)
+    update = nv * (48 + 24 + 24 + 12)
+    pupdate = nv * 36
+    return spmv + update + pupdate
 
 
 # algorithmic bytes per launch of the per-env kernels (FP32 mixed mode)

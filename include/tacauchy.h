@@ -124,6 +124,7 @@ typedef struct {
   int64_t newton_iters, pcg_iters, substeps, steps, line_search_halvings;
   double kappa;              /* barrier stiffness in use (N/m)              */
   size_t device_bytes;       /* device memory held by the env               */
+  int64_t nnzb;              /* 3x3 blocks of the Newton matrix (free rows)  */
 } tc_info;
 
 /* Scene setup (row a0): rest shape Dm^-1 and volumes, lumped masses, boundary
@@ -252,6 +253,75 @@ tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const float* sigma
                                   const int32_t* cv_face_off, const int32_t* cv_face_idx, int32_t nvc,
                                   const int32_t* pix_face, const float* pix_w, int32_t npix,
                                   float* out, uint8_t* mask, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Step server: continuous batching of step requests from many envs.
+ *
+ * Not in the paper, which steps one env per call.  A server owns one worker
+ * thread and one CUDA stream on the device current at creation.  tc_submit
+ * queues a request (env, target pose, optional output buffers) and returns a
+ * ticket at once.  Before every scheduling round the worker admits queued
+ * requests in FIFO order while fewer than max_slots are in flight and the
+ * device footprint of their envs (the memory each env holds) stays within
+ * hbm_budget_bytes; a request waits while an earlier request of the same env
+ * is in flight, and a lone request is always admitted.  Each round advances
+ * every admitted request by one phase group of the implicit step (Algorithm 2,
+ * physics line) with one launch set per phase over all of them, so requests
+ * that arrive while others are on the GPU join at the next round boundary.
+ * A request's result equals tc_step on the same env and pose (bit for bit).
+ * When it finishes, its stress (as tc_stress) and pressure map (as
+ * tc_pressure_map) are written to the buffers given at submit, and the
+ * ticket completes.  While a request is queued or in flight its env belongs
+ * to the server: tc_step, tc_step_batch and tc_set_positions on it return
+ * TC_ERR_INVALID_ARG, and no other call may use it.  All calls are
+ * thread-safe; tc_server_destroy must not overlap any other call on the
+ * same server.
+ * ---------------------------------------------------------------------- */
+typedef struct tc_server tc_server;
+
+typedef struct {
+  tc_status status;   /* the step's status (TC_ERR_ADMISSION: the env never
+                         fits the budget, or the server shut down first) */
+  double queue_us;    /* submit -> admitted into the running batch          */
+  double latency_us;  /* submit -> step done and outputs written            */
+  int32_t rounds;     /* scheduling rounds the request took part in         */
+} tc_result;
+
+typedef struct {
+  int64_t submitted, completed, rounds;
+  int32_t queued, inflight, peak_inflight, max_slots;
+  size_t inflight_bytes, budget_bytes;
+  void* stream;       /* cudaStream_t all of the server's work runs on      */
+} tc_server_stats;
+
+/* hbm_budget_bytes > 0: bound on the summed footprint of the envs in flight;
+ * max_slots > 0: bound on the number of requests in flight. */
+tc_status tc_server_create(size_t hbm_budget_bytes, int32_t max_slots, tc_server** out);
+
+/* Queue one step of env toward *target (host pose; non-finite:
+ * TC_ERR_NONFINITE).  sigma_out (device float 6 x nt), map_out (device float
+ * H x W) and mask_out (device uint8 H x W) may each be NULL; mask_out needs
+ * map_out, and map_out needs an env created with a grid.  *ticket receives
+ * the request's id.  Never blocks on the GPU. */
+tc_status tc_submit(tc_server* server, tc_env* env, const tc_pose* target,
+                    float* sigma_out, float* map_out, uint8_t* mask_out,
+                    uint64_t* ticket);
+
+/* *done = 1 once the request has finished; then *result (nullable) is
+ * filled and the ticket is released (a later call with it returns
+ * TC_ERR_INVALID_ARG).  Unknown ticket: TC_ERR_INVALID_ARG. */
+tc_status tc_poll(tc_server* server, uint64_t ticket, int32_t* done, tc_result* result);
+
+/* Block up to timeout_us (>= 0) microseconds for the request to finish.
+ * Finished: TC_OK, *result (nullable) filled, ticket released.  Not finished
+ * in time: TC_ERR_TIMEOUT (the request keeps running; wait or poll again). */
+tc_status tc_wait(tc_server* server, uint64_t ticket, int64_t timeout_us, tc_result* result);
+
+tc_status tc_server_info(tc_server* server, tc_server_stats* out);
+
+/* Cancel queued requests (their status becomes TC_ERR_ADMISSION), finish the
+ * ones in flight, stop the worker and free the server. */
+void tc_server_destroy(tc_server* server);
 
 #ifdef __cplusplus
 }

@@ -8,4 +8,4 @@ The compute lives in libtacauchy.so (CUDA, C ABI in include/tacauchy.h);
 ``python -m paper_2606_20426_gb300.build``.
 """
 from . import tacauchy  # noqa: F401
-from .tacauchy import Env, TcError, load, step_batch, stress_from_F  # noqa: F401
+from .tacauchy import Env, Server, TcError, load, step_batch, stress_from_F  # noqa: F401

@@ -14,10 +14,6 @@
 #include "batch.cuh"
 #include "env.cuh"
 
-struct tc_env {
-  tc::Env impl;
-};
-
 namespace tc {
 
 thread_local Profiler* g_prof = nullptr;
@@ -69,12 +65,12 @@ template <class R> static tc_status alloc_state(Env& env) {
     *p = a.alloc<R>(n);
     return *p != nullptr;
   };
-  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.utrial, 3 * nv) && A(&env.H9, 45 * nt) &&
-            A(&env.eslot, 36 * nt) && A(&env.yslot, 12 * nt) && A(&env.g, 3 * nv) && A(&env.Minv, 6 * nv) &&
+  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.utrial, 3 * nv) && A(&env.kblk, 90 * nt) &&
+            A(&env.eslot, 12 * nt) && A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) &&
+            A(&env.Minv, 6 * nv) &&
             A(&env.dx, 3 * nv) && A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) &&
             A(&env.cv_slot, 9 * (int64_t)std::max(env.nvc, 1)) && A(&env.ce_slot, 27 * (int64_t)std::max(env.nec, 1)) &&
-            A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1)) && A(&env.cv_y, 3 * (int64_t)std::max(env.nvc, 1)) &&
-            A(&env.ce_y, 6 * (int64_t)std::max(env.nec, 1)) && A(&env.cf_y, 9 * (int64_t)std::max(env.nfc, 1));
+            A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1));
   if (ok && env.dynamic) ok = A(&env.vel, 3 * nv) && A(&env.utilde, 3 * nv);
   if (!ok) return TC_ERR_OOM;
   TC_CHECK(cudaMemsetAsync(env.u, 0, sizeof(R) * 3 * nv, env.stream));
@@ -248,6 +244,7 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   if (!env.sc || cudaMallocHost(&env.sc_host, sizeof(tc::Scalars)) != cudaSuccess) st = TC_ERR_OOM;
   if (st == TC_OK && cudaMemsetAsync(env.sc, 0, sizeof(tc::Scalars), env.stream) != cudaSuccess) st = TC_ERR_CUDA;
   if (st == TC_OK) st = tc::setup_scene(env, mesh, fixed, nfixed, indenter, grid);
+  if (st == TC_OK) st = tc::build_bsr(env, mesh->tets, fixed, nfixed);
   if (st == TC_OK)
     st = env.precision == TC_FP64 ? tc::alloc_state<double>(env) : tc::alloc_state<float>(env);
   if (st == TC_OK)
@@ -265,6 +262,7 @@ tc_status tc_step(tc_env* h, const tc_pose* target) {
   if (!h || !target) return TC_ERR_INVALID_ARG;
   if (!pose_ok(target)) return TC_ERR_NONFINITE;
   Env& env = h->impl;
+  if (env.busy.load()) return TC_ERR_INVALID_ARG;  // a server holds a request of this env
   tc::ProfGuard pg(env);
   tc_status st = env.precision == TC_FP64 ? tc::do_step<double>(env, *target) : tc::do_step<float>(env, *target);
   env.last_status = st;
@@ -275,7 +273,7 @@ tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets, tc_sta
   if (n < 0 || (n > 0 && (!envs || !targets || !statuses))) return TC_ERR_INVALID_ARG;
   if (n == 0) return TC_OK;
   for (int i = 0; i < n; ++i) {
-    if (!envs[i]) return TC_ERR_INVALID_ARG;
+    if (!envs[i] || envs[i]->impl.busy.load()) return TC_ERR_INVALID_ARG;
     if (envs[i]->impl.precision != envs[0]->impl.precision || envs[i]->impl.device != envs[0]->impl.device)
       return TC_ERR_INVALID_ARG;
     for (int j = 0; j < i; ++j)
@@ -382,6 +380,7 @@ tc_status tc_get_positions(tc_env* h, double* x) {
 tc_status tc_set_positions(tc_env* h, const double* x) {
   if (!h || !x) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  if (env.busy.load()) return TC_ERR_INVALID_ARG;
   return env.precision == TC_FP64 ? tc::set_positions<double>(env, x) : tc::set_positions<float>(env, x);
 }
 
@@ -406,6 +405,7 @@ tc_status tc_env_info(tc_env* h, tc_info* info) {
   info->line_search_halvings = env.stats.halvings;
   info->kappa = env.kappa;
   info->device_bytes = env.arena.bytes;
+  info->nnzb = env.nnzb;
   return TC_OK;
 }
 

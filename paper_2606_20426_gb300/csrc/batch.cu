@@ -174,7 +174,7 @@ tc_status BatchExec<R>::build(const std::vector<Env*>& set, const double* params
   L.pq = take(tot[K_VGRP]);
   L.rz = take(tot[K_VERT]);
   L.rr = take(tot[K_VERT]);
-  L.env_s = take(8 * (int64_t)n);
+  L.env_s = take(16 * (int64_t)n);
   L.total = off;
   // the staging buffers below may still feed the previous phase's copies
   TC_CHECK(cudaStreamSynchronize(stream));
@@ -281,6 +281,8 @@ static tc_status ccd_phase(BatchExec<R>& X, const std::vector<Env*>& set, const 
         int cap = e.cand_cap;
         while (cap < sc.overflow) cap *= 2;
         if ((st = alloc_candidates(e, cap)) != TC_OK) return st;
+        // the new lists come from the env's own stream
+        if (e.stream != X.stream) TC_CHECK(cudaStreamSynchronize(e.stream));
         again.push_back(todo[j]);
       } else {
         e.cand_valid = true;

@@ -227,7 +227,8 @@ TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R H[45]
   }
 }
 
-// K1: energy (per-block partial), gradient slots, H9, diagonal-block slots.
+// K1: energy (per-unit partial), gradient slots and the element's stiffness
+// blocks (10 upper 3x3 corner blocks of V D^T H D, D = dF/dx).
 template <class R, bool HESS>
 __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayout L, int trial) {
   const Loc l = locate(bv.prefix, bv.nenv, K_TET, blockIdx.x);
@@ -266,8 +267,8 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
         for (int i = 0; i < 3; ++i) e.eslot[(int64_t)(3 * a + i) * nt + el] = gs[a][i];
       R H[45];
       psd_tangent<R>(G, k, e.mu, e.lam_hat, H);
-      for (int q = 0; q < 45; ++q) e.H9[(int64_t)q * nt + el] = H[q];
-      // diagonal blocks K_aa = V n_a^T H_(ik) n_a
+      // stiffness blocks K_ab[i][k] = V sum_jl H[(i,j),(k,l)] n_a[j] n_b[l]
+      // for corners a <= b (n_a: gradient of corner a's shape function)
       R n[4][3];
       for (int j = 0; j < 3; ++j) {
         n[1][j] = Bm[0][j];
@@ -275,14 +276,26 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
         n[3][j] = Bm[2][j];
         n[0][j] = -(Bm[0][j] + Bm[1][j] + Bm[2][j]);
       }
-      const int bi[6] = {0, 1, 2, 0, 1, 2}, bk[6] = {0, 1, 2, 1, 2, 0};
-      for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 6; ++c) {
-          const int i = bi[c], kk = bk[c];
-          R acc = 0;
+      R* K = e.kblk + (int64_t)el * 90;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          R T[3][4];  // T[j][b] = sum_l H[(i,j),(kk,l)] n_b[l]
+#pragma unroll
           for (int j = 0; j < 3; ++j)
-            for (int l = 0; l < 3; ++l) acc += H[sym_index(3 * i + j, 3 * kk + l, 9)] * n[a][j] * n[a][l];
-          e.eslot[(int64_t)(12 + 6 * a + c) * nt + el] = V * acc;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              T[j][b] = H[sym_index(3 * i + j, 3 * kk + 0, 9)] * n[b][0] + H[sym_index(3 * i + j, 3 * kk + 1, 9)] * n[b][1] +
+                        H[sym_index(3 * i + j, 3 * kk + 2, 9)] * n[b][2];
+          int pidx = 0;
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = a; b < 4; ++b) {
+              K[pidx * 9 + 3 * i + kk] = V * (n[a][0] * T[0][b] + n[a][1] * T[1][b] + n[a][2] * T[2][b]);
+              ++pidx;
+            }
         }
     }
   }

@@ -13,6 +13,7 @@
 //   indenter  : body-frame vertices (double), faces, edges, uniform grid
 //   pixels    : covering face + barycentric weights per pixel
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -58,9 +59,9 @@ template <class R> struct EnvView {
   // per tet
   const R* Dminv;             // 9 x nt (row-major entry k at k*nt + e)
   const R* vol;
-  R* H9;                      // 45 x nt packed upper triangle of PSD dP/dF
-  R* eslot;                   // 36 x nt
-  R* yslot;                   // 12 x nt
+  R* eslot;                   // 12 x nt element gradient per (corner, component)
+  R* kblk;                    // nt x 10 x 9: the element's PSD 12x12 stiffness as its 10
+                              // upper 3x3 corner blocks (a <= b, row-major), tet-major
   // per vertex
   const R* mass;              // nv (dynamic) or null
   R* u;                       // 3 x nv displacement
@@ -85,9 +86,16 @@ template <class R> struct EnvView {
   R* cv_slot;                 // 9 x nvc  (3 g + 6 H)
   R* ce_slot;                 // 27 x nec (6 g + 21 H)
   R* cf_slot;                 // 54 x nfc (9 g + 45 H)
-  R* cv_y;                    // 3 x nvc contact share of H p
-  R* ce_y;                    // 6 x nec
-  R* cf_y;                    // 9 x nfc
+  // block-sparse (BSR, 3x3 blocks) Newton matrix over the free vertices
+  int nnzb;
+  const int32_t* bsr_rp;      // nv + 1 row offsets (fixed rows are empty)
+  const int32_t* bsr_ci;      // nnzb column vertex ids, ascending per row
+  const int32_t* bsr_diag;    // nv: position of the diagonal block, -1 if fixed
+  const int32_t* be_off;      // nnzb + 1: element contributions of each block
+  const int32_t* be_idx;      //   tet*16 + a*4 + b (corner a's row, corner b's column)
+  const int32_t* bc_off;      // nnzb + 1: contact contributions of each block
+  const int32_t* bc_idx;      //   kind<<30 | a<<28 | b<<26 | primitive
+  R* bsr_val;                 // 9 x nnzb block entries (entry r*3+c of block k at (r*3+c)*nnzb + k)
   // indenter (body frame)
   const double* IV;           // 3 x ind_nv SoA
   const float* IVhi;          // IV as FP32 hi + lo pairs (hi = fl(IV), lo = fl(IV - hi))
@@ -211,9 +219,12 @@ struct Env {
   void* vol = nullptr;
   void* mass = nullptr;
   void *u = nullptr, *ut = nullptr, *vel = nullptr, *utilde = nullptr;
-  void *H9 = nullptr, *eslot = nullptr, *yslot = nullptr;
+  void *eslot = nullptr, *kblk = nullptr, *bsr_val = nullptr;
+  int nnzb = 0;
+  int32_t *bsr_rp = nullptr, *bsr_ci = nullptr, *bsr_diag = nullptr;
+  int32_t *be_off = nullptr, *be_idx = nullptr, *bc_off = nullptr, *bc_idx = nullptr;
   void *g = nullptr, *Minv = nullptr, *dx = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
-  void *cv_slot = nullptr, *ce_slot = nullptr, *cf_slot = nullptr, *cv_y = nullptr, *ce_y = nullptr, *cf_y = nullptr;
+  void *cv_slot = nullptr, *ce_slot = nullptr, *cf_slot = nullptr;
   void* utrial = nullptr;
   // extraction scratch (float)
   float *sigma = nullptr, *face_p = nullptr, *face_A = nullptr, *vert_p = nullptr;
@@ -225,6 +236,8 @@ struct Env {
   int last_status = TC_OK;
   Profiler* prof = nullptr;  // per-kernel timing, null unless enabled
   void* exec = nullptr;      // BatchExec<R> of this env (batches of one)
+  std::atomic<int> busy{0};      // step requests of this env queued or in flight on a server
+  std::atomic<int> in_flight{0}; // 1 while one of them is admitted
 
   template <class R> EnvView<R> view() const;
 };
@@ -237,7 +250,9 @@ template <class R> EnvView<R> Env::view() const {
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
   e.dhat = dhat; e.kappa = kappa;
   e.tets = tets; e.X0 = X0; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
-  e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.H9 = (R*)H9; e.eslot = (R*)eslot; e.yslot = (R*)yslot;
+  e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.eslot = (R*)eslot; e.kblk = (R*)kblk;
+  e.nnzb = nnzb; e.bsr_rp = bsr_rp; e.bsr_ci = bsr_ci; e.bsr_diag = bsr_diag; e.bsr_val = (R*)bsr_val;
+  e.be_off = be_off; e.be_idx = be_idx; e.bc_off = bc_off; e.bc_idx = bc_idx;
   e.mass = (const R*)mass; e.u = (R*)u; e.ut = (R*)utrial; e.utilde = (R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
   e.u0 = (R*)ut; e.vel = (R*)vel; e.dt = dynamic ? dt : 0.0;
   e.dx = (R*)dx; e.r = (R*)r; e.z = (R*)z; e.p = (R*)p; e.q = (R*)q;
@@ -245,7 +260,6 @@ template <class R> EnvView<R> Env::view() const {
   e.cv_face_off = cv_face_off; e.cv_face_idx = cv_face_idx; e.cv_edge_off = cv_edge_off; e.cv_edge_idx = cv_edge_idx;
   e.gel_elen2 = gel_elen2;
   e.cv_slot = (R*)cv_slot; e.ce_slot = (R*)ce_slot; e.cf_slot = (R*)cf_slot;
-  e.cv_y = (R*)cv_y; e.ce_y = (R*)ce_y; e.cf_y = (R*)cf_y;
   e.IV = IV; e.IVhi = IVhi; e.IVlo = IVlo; e.IF = IF; e.IE = IE; e.ind_elen2 = ind_elen2;
   for (int k = 0; k < 3; ++k) { e.cand[k] = cand[k]; e.cand_n[k] = cand_n[k]; }
   e.cand_cap = cand_cap;
@@ -269,6 +283,9 @@ template <class R> EnvView<R> Env::view() const {
 tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32_t nfixed,
                       const tc_trimesh* ind, const tc_grid* grid);
 tc_status check_initial(Env& env);
+// BSR pattern and fixed-order contribution lists of the Newton matrix
+// (host build from the host tets, after setup_scene)
+tc_status build_bsr(Env& env, const int32_t* tets, const int32_t* fixed_ids, int32_t nfixed);
 
 // Extraction.
 template <class R> void launch_stress(const EnvView<R>& e, float* sigma, cudaStream_t s);
@@ -283,3 +300,8 @@ void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, fl
                           cudaStream_t s);
 
 }  // namespace tc
+
+// The opaque handle of the C ABI.
+struct tc_env {
+  tc::Env impl;
+};

@@ -2,9 +2,11 @@
 // matrix-free block-Jacobi PCG (K5), energies for the line search (K7) and
 // step updates.
 //
-// Assembly and SpMV are atomic-free: element and contact passes write their
+// Assembly is atomic-free: element and contact passes write their
 // per-element / per-primitive contributions to slots, and one lane group per
-// vertex sums its incident slots through fixed incidence lists.  Every block
+// vertex sums its incident slots through fixed incidence lists into the
+// gradient and into its row of the block-sparse (3x3 BSR) Newton matrix,
+// which the PCG then multiplies row by row.  Every block
 // reduction writes one partial per work unit; per-env finalize blocks fold an
 // env's partials in unit order.  Dot products and energies accumulate in
 // double.  Results do not depend on the batch composition or the schedule.
@@ -31,20 +33,6 @@ template <class T> TC_D T group_sum(T v) {
   return v;
 }
 
-template <class R> struct Sym3 {
-  R xx, yy, zz, xy, yz, zx;
-};
-
-template <class R> TC_D void add_packed_block(Sym3<R>& D, const R* slot, int64_t stride, int64_t prim, int l, int N) {
-  const int b = 3 * l;
-  D.xx += slot[(int64_t)sym_index(b + 0, b + 0, N) * stride + prim];
-  D.yy += slot[(int64_t)sym_index(b + 1, b + 1, N) * stride + prim];
-  D.zz += slot[(int64_t)sym_index(b + 2, b + 2, N) * stride + prim];
-  D.xy += slot[(int64_t)sym_index(b + 0, b + 1, N) * stride + prim];
-  D.yz += slot[(int64_t)sym_index(b + 1, b + 2, N) * stride + prim];
-  D.zx += slot[(int64_t)sym_index(b + 2, b + 0, N) * stride + prim];
-}
-
 // An env's per-unit partials part[u * stride + offset], u over its units of
 // `kind`, folded in unit order by one block.
 template <class R>
@@ -65,9 +53,36 @@ TC_D double env_unit_min(const BatchView<R>& bv, int kind, int env, const double
 }
 
 // ---------------------------------------------------------------- assembly
-// g_v = sum of element and contact gradient slots (+ inertia), 3x3 diagonal
-// block -> inverse for block-Jacobi.  Partials per K_VGRP unit: |g|^2 and the
-// inertia energy 1/(2h^2)|u - u_tilde|_M^2.
+// One lane group per vertex (row) gathers, through fixed-order lists:
+//   g_v     = element gradient slots + contact gradient slots (+ inertia)
+//   row v   = every 3x3 block (v, j) of the Newton matrix: element stiffness
+//             blocks + contact Hessian blocks (+ M/h^2 on the diagonal)
+//   M^-1_v  = inverse of the diagonal block (block-Jacobi preconditioner).
+// Partials per K_VGRP unit: |g|^2 and the inertia energy 1/(2h^2)|u - u~|_M^2.
+TC_D int pair_index(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }  // corners a <= b
+
+template <class R> TC_D void add_contact_block(const EnvView<R>& e, uint32_t code, R B[9]) {
+  const int kind = (int)(code >> 30), a = (int)((code >> 28) & 3u), b = (int)((code >> 26) & 3u);
+  const int prim = (int)(code & ((1u << 26) - 1u));
+  const R* slot;
+  int n, N;
+  if (kind == 0) {
+    slot = e.cv_slot;
+    n = e.nvc;
+    N = 3;
+  } else if (kind == 1) {
+    slot = e.ce_slot;
+    n = e.nec;
+    N = 6;
+  } else {
+    slot = e.cf_slot;
+    n = e.nfc;
+    N = 9;
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) B[3 * r + c] += slot[(int64_t)(N + sym_index(3 * a + r, 3 * b + c, N)) * n + prim];
+}
+
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, PartLayout L) {
   const Loc l = locate(bv.prefix, bv.nenv, K_VGRP, blockIdx.x);
@@ -78,45 +93,80 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, Part
   const bool valid = v < nv;
   double gn2 = 0.0, ein = 0.0;
   R g[3] = {0, 0, 0};
-  Sym3<R> D{0, 0, 0, 0, 0, 0};
+  bool finite = true;
   if (valid) {
     for (int k = e.vt_off[v] + lane; k < e.vt_off[v + 1]; k += kLanes) {
       const int code = e.vt_idx[k];
       const int el = code >> 2, c = code & 3;
       for (int i = 0; i < 3; ++i) g[i] += e.eslot[(int64_t)(3 * c + i) * nt + el];
-      const R* ds = e.eslot + (int64_t)(12 + 6 * c) * nt + el;
-      D.xx += ds[0];
-      D.yy += ds[(int64_t)nt];
-      D.zz += ds[2 * (int64_t)nt];
-      D.xy += ds[3 * (int64_t)nt];
-      D.yz += ds[4 * (int64_t)nt];
-      D.zx += ds[5 * (int64_t)nt];
     }
     const int s = e.vslot[v];
     if (s >= 0) {
-      if (lane == 0) {
+      if (lane == 0)
         for (int i = 0; i < 3; ++i) g[i] += e.cv_slot[(int64_t)i * e.nvc + s];
-        add_packed_block<R>(D, e.cv_slot + 3 * (int64_t)e.nvc, e.nvc, s, 0, 3);
-      }
       for (int k = e.cv_edge_off[s] + lane; k < e.cv_edge_off[s + 1]; k += kLanes) {
         const int code = e.cv_edge_idx[k], p = code >> 2, q = code & 3;
         for (int i = 0; i < 3; ++i) g[i] += e.ce_slot[(int64_t)(3 * q + i) * e.nec + p];
-        add_packed_block<R>(D, e.ce_slot + 6 * (int64_t)e.nec, e.nec, p, q, 6);
       }
       for (int k = e.cv_face_off[s] + lane; k < e.cv_face_off[s + 1]; k += kLanes) {
         const int code = e.cv_face_idx[k], p = code >> 2, q = code & 3;
         for (int i = 0; i < 3; ++i) g[i] += e.cf_slot[(int64_t)(3 * q + i) * e.nfc + p];
-        add_packed_block<R>(D, e.cf_slot + 9 * (int64_t)e.nfc, e.nfc, p, q, 9);
+      }
+    }
+    // the matrix row (empty for a fixed vertex)
+    const R mh = e.mass ? e.mass[v] * e.inv_h2 : R(0);
+    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
+      R B[9];
+      for (int q = 0; q < 9; ++q) B[q] = R(0);
+      for (int c = e.be_off[k]; c < e.be_off[k + 1]; ++c) {
+        const int code = e.be_idx[c];
+        const int t = code >> 4, a = (code >> 2) & 3, b = code & 3;
+        const R* K = e.kblk + (int64_t)t * 90;
+        if (a <= b) {
+          const R* Kb = K + 9 * pair_index(a, b);
+          for (int q = 0; q < 9; ++q) B[q] += Kb[q];
+        } else {
+          const R* Kb = K + 9 * pair_index(b, a);
+          for (int r = 0; r < 3; ++r)
+            for (int cc = 0; cc < 3; ++cc) B[3 * r + cc] += Kb[3 * cc + r];
+        }
+      }
+      for (int c = e.bc_off[k]; c < e.bc_off[k + 1]; ++c) add_contact_block<R>(e, (uint32_t)e.bc_idx[c], B);
+      if (k == e.bsr_diag[v]) {
+        B[0] += mh;
+        B[4] += mh;
+        B[8] += mh;
+        // inverse of the (symmetric) diagonal block: adjugate / det
+        const R xx = B[0], yy = B[4], zz = B[8], xy = B[1], yz = B[5], zx = B[2];
+        const R c00 = yy * zz - yz * yz, c01 = yz * zx - xy * zz, c02 = xy * yz - yy * zx;
+        const R det = xx * c00 + xy * c01 + zx * c02;
+        R M[6];
+        if (det > R(0) && isfinite((double)det)) {
+          const R id = R(1) / det;
+          M[0] = c00 * id;
+          M[1] = (xx * zz - zx * zx) * id;
+          M[2] = (xx * yy - xy * xy) * id;
+          M[3] = c01 * id;
+          M[4] = (xy * zx - xx * yz) * id;
+          M[5] = c02 * id;
+        } else {
+          const R tr = xx + yy + zz;
+          const R d = tr > R(0) ? R(3) / tr : R(1);
+          M[0] = M[1] = M[2] = d;
+          M[3] = M[4] = M[5] = R(0);
+        }
+        for (int i = 0; i < 6; ++i) {
+          e.Minv[(int64_t)i * nv + v] = M[i];
+          finite = finite && isfinite((double)M[i]);
+        }
+      }
+      for (int q = 0; q < 9; ++q) {
+        e.bsr_val[(int64_t)q * e.nnzb + k] = B[q];
+        finite = finite && isfinite((double)B[q]);
       }
     }
   }
   for (int i = 0; i < 3; ++i) g[i] = group_sum(g[i]);
-  D.xx = group_sum(D.xx);
-  D.yy = group_sum(D.yy);
-  D.zz = group_sum(D.zz);
-  D.xy = group_sum(D.xy);
-  D.yz = group_sum(D.yz);
-  D.zx = group_sum(D.zx);
   if (valid && lane == 0) {
     if (e.mass) {
       const R mh = e.mass[v] * e.inv_h2;
@@ -125,43 +175,18 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, Part
         g[i] += mh * du;
         ein += 0.5 * (double)mh * (double)du * (double)du;
       }
-      D.xx += mh;
-      D.yy += mh;
-      D.zz += mh;
     }
-    R M[6] = {0, 0, 0, 0, 0, 0};
     if (e.fixed[v]) {
       g[0] = g[1] = g[2] = R(0);
-    } else {
-      // inverse of the symmetric 3x3 block (adjugate / det)
-      const R c00 = D.yy * D.zz - D.yz * D.yz, c01 = D.yz * D.zx - D.xy * D.zz, c02 = D.xy * D.yz - D.yy * D.zx;
-      const R det = D.xx * c00 + D.xy * c01 + D.zx * c02;
-      if (det > R(0) && isfinite((double)det)) {
-        const R id = R(1) / det;
-        M[0] = c00 * id;
-        M[1] = (D.xx * D.zz - D.zx * D.zx) * id;
-        M[2] = (D.xx * D.yy - D.xy * D.xy) * id;
-        M[3] = c01 * id;
-        M[4] = (D.xy * D.zx - D.xx * D.yz) * id;
-        M[5] = c02 * id;
-      } else {
-        const R tr = D.xx + D.yy + D.zz;
-        const R d = tr > R(0) ? R(3) / tr : R(1);
-        M[0] = M[1] = M[2] = d;
-      }
+      for (int i = 0; i < 6; ++i) e.Minv[(int64_t)i * nv + v] = R(0);
     }
-    bool finite = true;
     for (int i = 0; i < 3; ++i) {
       e.g[i * nv + v] = g[i];
       gn2 += (double)g[i] * (double)g[i];
       finite = finite && isfinite((double)g[i]);
     }
-    for (int i = 0; i < 6; ++i) {
-      e.Minv[(int64_t)i * nv + v] = M[i];
-      finite = finite && isfinite((double)M[i]);
-    }
-    if (!finite) atomicOr(&e.sc->status, ST_NONFINITE);
   }
+  if (!finite) atomicOr(&e.sc->status, ST_NONFINITE);
   gn2 = block_sum<kBlock>(gn2);
   ein = block_sum<kBlock>(ein);
   if (threadIdx.x == 0) {
@@ -268,8 +293,14 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, Part
   }
 }
 
-// per env: r.z, r.r and the squared stopping tolerance (param[env]) ->
-// published scalars
+// Per-env PCG scalars, double-buffered by iteration parity: iteration `it`
+// reads buffer it & 1 and the env's designated block writes buffer
+// (it + 1) & 1, so no block reads a value while it is being replaced.
+// Fields: 0 r.z, 1 r.r, 2 done (0 running, 1 stopped), 3 iterations,
+// 4 squared tolerance, 5 p.q of the last iteration.
+constexpr int kEnvScalars = 8;
+
+// per env: r.z, r.r and the squared stopping tolerance (param[env]) -> buffer 0
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, PartLayout L) {
   const int env = blockIdx.x;
@@ -280,269 +311,203 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
     Scalars* sc = e.sc;
     if (!isfinite(rz) || !isfinite(rr)) sc->status |= ST_NONFINITE;
     const double tol2 = bv.param[env];
-    double* es = bv.part + L.env_s + 8 * env;
-    es[0] = 0.0;
-    es[1] = 0.0;
-    es[2] = rz;
-    es[3] = rr;
-    es[4] = 0.0;
-    es[5] = (rr <= tol2) ? 1.0 : 0.0;
-    es[6] = 0.0;
-    es[7] = tol2;
+    double* es = bv.part + L.env_s + kEnvScalars * env;
+    es[0] = rz;
+    es[1] = rr;
+    es[2] = (rr <= tol2) ? 1.0 : 0.0;
+    es[3] = 0.0;
+    es[4] = tol2;
+    es[5] = 0.0;
   }
 }
 
-// element share of A p: y_e = V D^T H9 D p_e  (12 per tet)
-template <class R> TC_D void spmv_elem_one(const EnvView<R>& e, int el) {
-  const int nt = e.nt, nv = e.nv;
-  const int4 t = e.tets[el];
-  const int v[4] = {t.x, t.y, t.z, t.w};
-  R Bm[3][3];
-  for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < 3; ++j) Bm[a][j] = e.Dminv[(int64_t)(a * 3 + j) * nt + el];
-  R Dp[3][3];
-  for (int i = 0; i < 3; ++i) {
-    const R p0 = e.p[i * nv + v[0]];
-    for (int a = 0; a < 3; ++a) Dp[i][a] = e.p[i * nv + v[a + 1]] - p0;
-  }
-  R f[9];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) f[3 * i + j] = Dp[i][0] * Bm[0][j] + Dp[i][1] * Bm[1][j] + Dp[i][2] * Bm[2][j];
-  R y[9];
-  for (int a = 0; a < 9; ++a) y[a] = R(0);
-  int idx = 0;
-#pragma unroll
-  for (int a = 0; a < 9; ++a) {
-#pragma unroll
-    for (int b = a; b < 9; ++b) {
-      const R h = e.H9[(int64_t)(idx++) * nt + el];
-      y[a] += h * f[b];
-      if (b != a) y[b] += h * f[a];
-    }
-  }
-  const R V = e.vol[el];
-  for (int i = 0; i < 3; ++i) {
-    R s0 = 0;
-    for (int a = 0; a < 3; ++a) {
-      const R ya = V * (y[3 * i + 0] * Bm[a][0] + y[3 * i + 1] * Bm[a][1] + y[3 * i + 2] * Bm[a][2]);
-      e.yslot[(int64_t)(3 * (a + 1) + i) * nt + el] = ya;
-      s0 += ya;
-    }
-    e.yslot[(int64_t)i * nt + el] = -s0;
-  }
-}
-
-// contact share of A p per primitive: y = H_prim p_prim
-template <class R, int NGP>
-TC_D void contact_spmv_prim(const EnvView<R>& e, const R* slot, int n, int prim, const int* verts, R* yout) {
-  constexpr int NG = 3 * NGP;
-  R x[NG];
-  for (int l = 0; l < NGP; ++l)
-    for (int i = 0; i < 3; ++i) x[3 * l + i] = e.p[i * e.nv + verts[l]];
-  R y[NG];
-  for (int a = 0; a < NG; ++a) y[a] = R(0);
-  int idx = NG;
-  for (int a = 0; a < NG; ++a)
-    for (int b = a; b < NG; ++b) {
-      const R h = slot[(int64_t)(idx++) * n + prim];
-      y[a] += h * x[b];
-      if (b != a) y[b] += h * x[a];
-    }
-  for (int a = 0; a < NG; ++a) yout[(int64_t)a * n + prim] = y[a];
-}
-
-template <class R> TC_D void spmv_contact_one(const EnvView<R>& e, int kind, int i) {
-  if (kind == K_CV) {
-    if (i >= e.nvc) return;
-    const int v[1] = {e.cverts[i]};
-    contact_spmv_prim<R, 1>(e, e.cv_slot, e.nvc, i, v, e.cv_y);
-  } else if (kind == K_CE) {
-    if (i >= e.nec) return;
-    const int v[2] = {e.cedges[i], e.cedges[e.nec + i]};
-    contact_spmv_prim<R, 2>(e, e.ce_slot, e.nec, i, v, e.ce_y);
-  } else {
-    if (i >= e.nfc) return;
-    const int v[3] = {e.cfaces[i], e.cfaces[e.nfc + i], e.cfaces[2 * e.nfc + i]};
-    contact_spmv_prim<R, 3>(e, e.cf_slot, e.nfc, i, v, e.cf_y);
-  }
-}
-
-// q = A p at vertex v gathered by a lane group; returns p.q on the group's
-// lane 0 (0 elsewhere).  Every lane of the warp calls it.
-template <class R> TC_D double pcg_q_group(const EnvView<R>& e, int v, bool valid) {
+// q = A p for row v (BSR, one lane group per row); returns p.q on the
+// group's lane 0 (0 elsewhere).  Every lane of the warp calls it.
+template <class R> TC_D double bsr_q_group(const EnvView<R>& e, int v, bool valid) {
   const int lane = threadIdx.x & (kLanes - 1);
-  const int nv = e.nv, nt = e.nt;
-  R q[3] = {0, 0, 0};
-  const bool act = valid && !e.fixed[v];
-  if (act) {
-    for (int k = e.vt_off[v] + lane; k < e.vt_off[v + 1]; k += kLanes) {
-      const int code = e.vt_idx[k];
-      const int el = code >> 2, c = code & 3;
-      for (int i = 0; i < 3; ++i) q[i] += e.yslot[(int64_t)(3 * c + i) * nt + el];
-    }
-    const int s = e.vslot[v];
-    if (s >= 0) {
-      if (lane == 0)
-        for (int i = 0; i < 3; ++i) q[i] += e.cv_y[(int64_t)i * e.nvc + s];
-      for (int k = e.cv_edge_off[s] + lane; k < e.cv_edge_off[s + 1]; k += kLanes) {
-        const int code = e.cv_edge_idx[k], p = code >> 2, l = code & 3;
-        for (int i = 0; i < 3; ++i) q[i] += e.ce_y[(int64_t)(3 * l + i) * e.nec + p];
-      }
-      for (int k = e.cv_face_off[s] + lane; k < e.cv_face_off[s + 1]; k += kLanes) {
-        const int code = e.cv_face_idx[k], p = code >> 2, l = code & 3;
-        for (int i = 0; i < 3; ++i) q[i] += e.cf_y[(int64_t)(3 * l + i) * e.nfc + p];
-      }
+  const int nv = e.nv;
+  R q0 = 0, q1 = 0, q2 = 0;
+  if (valid) {
+    const int64_t nb = e.nnzb;
+    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
+      const int j = e.bsr_ci[k];
+      const R p0 = e.p[j], p1 = e.p[nv + j], p2 = e.p[2 * nv + j];
+      const R* B = e.bsr_val + k;
+      q0 += B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
+      q1 += B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
+      q2 += B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
     }
   }
-  for (int i = 0; i < 3; ++i) q[i] = group_sum(q[i]);
+  q0 = group_sum(q0);
+  q1 = group_sum(q1);
+  q2 = group_sum(q2);
   double pq = 0.0;
   if (valid && lane == 0) {
-    if (act && e.mass) {
-      const R mh = e.mass[v] * e.inv_h2;
-      for (int i = 0; i < 3; ++i) q[i] += mh * e.p[i * nv + v];
-    }
-    for (int i = 0; i < 3; ++i) {
-      e.q[i * nv + v] = q[i];
-      pq += (double)e.p[i * nv + v] * (double)q[i];
-    }
+    e.q[v] = q0;
+    e.q[nv + v] = q1;
+    e.q[2 * nv + v] = q2;
+    pq = (double)e.p[v] * (double)q0 + (double)e.p[nv + v] * (double)q1 + (double)e.p[2 * nv + v] * (double)q2;
   }
   return pq;
 }
 
-// ------------------------------------------------------ persistent PCG
-// All CG iterations of all envs of the batch in one cooperative launch.  Per
-// iteration: element + contact SpMV | gather q = A p (p.q partials) | per-env
-// alpha | vector update (r.z, r.r partials) | per-env beta and stop test |
-// direction update, with grid-wide syncs between the phases.  Per-env scalars
-// are folded by one block per env and published through global memory before
-// the next sync, so every block reads the same values; converged envs skip
-// their work while the others continue.  Published scalars, 8 per env at
-// part + env_s: alpha, beta, r.z, r.r, p.q, done (0 running, 1 stopped before
-// the iteration, 2 stopped in it), iterations, tolerance^2.
+// block-wide sum broadcast to every thread
+TC_D double block_sum_all(double v) {
+  __shared__ double s_tot;
+  const double t = block_sum<kBlock>(v);
+  if (threadIdx.x == 0) s_tot = t;
+  __syncthreads();
+  const double r = s_tot;
+  __syncthreads();
+  return r;
+}
 
+template <class R> TC_D double env_sum_all(const BatchView<R>& bv, int kind, int env, const double* part) {
+  const int* p = bv.prefix + kind * (bv.nenv + 1);
+  double s = 0.0;
+  for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) s += part[u];
+  return block_sum_all(s);
+}
+
+// ------------------------------------------------------ persistent PCG
+// All CG iterations of all envs of the batch in one cooperative launch, over
+// contiguous ranges of work units per block.  Per iteration:
+//   A  q = A p (BSR rows), p.q partials                           | sync
+//   B  alpha = r.z / p.q per env, dx += alpha p, r -= alpha q,
+//      z = M^-1 r; r.z, r.r partials                              | sync
+//   C  beta = r.z_new / r.z per env, stop test, p = z + beta p;
+//      each env's designated block publishes its new scalars      | sync
+// Every block folds the partials of the envs it touches itself, in unit
+// order with the same reduction tree, so all blocks hold bit-identical
+// per-env scalars without waiting for one writer; converged envs skip their
+// work while the others continue.  Results do not depend on the grid size or
+// on which other envs are in the batch.
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_pcg_batched(const BatchView<R> bv, PartLayout L, int max_iter) {
   cg::grid_group grid = cg::this_grid();
   const int G = gridDim.x;
   const int nenv = bv.nenv;
-  double* es = bv.part + L.env_s;
   const int* pre = bv.prefix;
-  const int nT = pre[K_TET * (nenv + 1) + nenv];
-  const int nC[3] = {pre[K_CV * (nenv + 1) + nenv], pre[K_CE * (nenv + 1) + nenv], pre[K_CF * (nenv + 1) + nenv]};
   const int nG = pre[K_VGRP * (nenv + 1) + nenv];
   const int nV = pre[K_VERT * (nenv + 1) + nenv];
-  for (int it = 0; it < max_iter; ++it) {
+  const int g0 = (int)((int64_t)nG * blockIdx.x / G), g1 = (int)((int64_t)nG * (blockIdx.x + 1) / G);
+  const int w0 = (int)((int64_t)nV * blockIdx.x / G), w1 = (int)((int64_t)nV * (blockIdx.x + 1) / G);
+  double* es0 = bv.part + L.env_s;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    const double* cur = es0 + (int64_t)(it & 1) * kEnvScalars * nenv;
+    double* nxt = es0 + (int64_t)((it + 1) & 1) * kEnvScalars * nenv;
     int all_done = 1;
-    for (int env = 0; env < nenv; ++env) all_done &= es[8 * env + 5] != 0.0;
+    for (int env = 0; env < nenv; ++env) all_done &= cur[kEnvScalars * env + 2] != 0.0;
     if (all_done) break;
-    // 1. SpMV
-    for (int u = blockIdx.x; u < nT; u += G) {
-      const Loc l = locate(pre, nenv, K_TET, u);
-      if (es[8 * l.env + 5] != 0.0) continue;
-      const EnvView<R>& e = bv.views[l.env];
-      const int el = l.chunk * kBlock + threadIdx.x;
-      if (el < e.nt) spmv_elem_one<R>(e, el);
-    }
-    for (int k = 0; k < 3; ++k)
-      for (int u = blockIdx.x; u < nC[k]; u += G) {
-        const Loc l = locate(pre, nenv, K_CV + k, u);
-        if (es[8 * l.env + 5] != 0.0) continue;
-        if (threadIdx.x < unit_items(K_CV + k))
-          spmv_contact_one<R>(bv.views[l.env], K_CV + k, l.chunk * unit_items(K_CV + k) + threadIdx.x);
-      }
-    grid.sync();
-    // 2. gather q = A p; partial p.q per unit
-    for (int u = blockIdx.x; u < nG; u += G) {
+    // A. q = A p
+    for (int u = g0; u < g1; ++u) {
       const Loc l = locate(pre, nenv, K_VGRP, u);
       double pq = 0.0;
-      if (es[8 * l.env + 5] == 0.0) {
+      if (cur[kEnvScalars * l.env + 2] == 0.0) {
         const EnvView<R>& e = bv.views[l.env];
         const int v = l.chunk * 32 + threadIdx.x / kLanes;
-        pq = pcg_q_group<R>(e, v, v < e.nv);
+        pq = bsr_q_group<R>(e, v, v < e.nv && !e.fixed[v]);
       }
       pq = block_sum<kBlock>(pq);
       if (threadIdx.x == 0) bv.part[L.pq + u] = pq;
     }
     grid.sync();
-    // 3. per-env alpha = r.z / p.q
-    for (int env = blockIdx.x; env < nenv; env += G) {
-      const double pq = env_unit_sum(bv, K_VGRP, env, bv.part + L.pq);
-      if (threadIdx.x == 0 && es[8 * env + 5] == 0.0) {
-        es[8 * env + 4] = pq;
-        es[8 * env + 0] = pq > 0.0 ? es[8 * env + 2] / pq : 0.0;
+    // B. vector update
+    {
+      int cenv = -1;
+      R alpha = 0;
+      for (int u = w0; u < w1; ++u) {
+        const Loc l = locate(pre, nenv, K_VERT, u);
+        double rz = 0.0, rr = 0.0;
+        if (cur[kEnvScalars * l.env + 2] == 0.0) {
+          if (l.env != cenv) {
+            cenv = l.env;
+            const double pq = env_sum_all(bv, K_VGRP, cenv, bv.part + L.pq);
+            alpha = (R)(pq > 0.0 ? cur[kEnvScalars * cenv + 0] / pq : 0.0);
+          }
+          const EnvView<R>& e = bv.views[l.env];
+          const int nv = e.nv;
+          const int v = l.chunk * kBlock + threadIdx.x;
+          if (v < nv) {
+            R r[3], z[3];
+            for (int i = 0; i < 3; ++i) {
+              e.dx[i * nv + v] += alpha * e.p[i * nv + v];
+              r[i] = e.r[i * nv + v] - alpha * e.q[i * nv + v];
+              e.r[i * nv + v] = r[i];
+            }
+            apply_minv<R>(e, v, r, z);
+            for (int i = 0; i < 3; ++i) {
+              e.z[i * nv + v] = z[i];
+              rz += (double)r[i] * (double)z[i];
+              rr += (double)r[i] * (double)r[i];
+            }
+          }
+        }
+        rz = block_sum<kBlock>(rz);
+        rr = block_sum<kBlock>(rr);
+        if (threadIdx.x == 0) {
+          bv.part[L.rz + u] = rz;
+          bv.part[L.rr + u] = rr;
+        }
       }
     }
     grid.sync();
-    // 4. dx += alpha p, r -= alpha q, z = M^-1 r; partials r.z, r.r
-    for (int u = blockIdx.x; u < nV; u += G) {
-      const Loc l = locate(pre, nenv, K_VERT, u);
-      double rz = 0.0, rr = 0.0;
-      if (es[8 * l.env + 5] == 0.0) {
+    // C. direction update and the published scalars
+    {
+      int cenv = -1;
+      R beta = 0;
+      for (int u = w0; u < w1; ++u) {
+        const Loc l = locate(pre, nenv, K_VERT, u);
+        if (cur[kEnvScalars * l.env + 2] != 0.0) continue;
+        if (l.env != cenv) {
+          cenv = l.env;
+          const double rz_new = env_sum_all(bv, K_VERT, cenv, bv.part + L.rz);
+          const double rz_old = cur[kEnvScalars * cenv + 0];
+          beta = (R)(rz_old > 0.0 ? rz_new / rz_old : 0.0);
+        }
         const EnvView<R>& e = bv.views[l.env];
         const int nv = e.nv;
         const int v = l.chunk * kBlock + threadIdx.x;
-        const R alpha = (R)es[8 * l.env + 0];
-        if (v < nv) {
-          R r[3], z[3];
-          for (int i = 0; i < 3; ++i) {
-            e.dx[i * nv + v] += alpha * e.p[i * nv + v];
-            r[i] = e.r[i * nv + v] - alpha * e.q[i * nv + v];
-            e.r[i * nv + v] = r[i];
-          }
-          apply_minv<R>(e, v, r, z);
-          for (int i = 0; i < 3; ++i) {
-            e.z[i * nv + v] = z[i];
-            rz += (double)r[i] * (double)z[i];
-            rr += (double)r[i] * (double)r[i];
-          }
+        if (v < nv)
+          for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + beta * e.p[i * nv + v];
+      }
+      for (int env = blockIdx.x; env < nenv; env += G) {
+        const double* c = cur + kEnvScalars * env;
+        double* n = nxt + kEnvScalars * env;
+        if (c[2] != 0.0) {
+          if (threadIdx.x == 0)
+            for (int f = 0; f < kEnvScalars; ++f) n[f] = c[f];
+          continue;
+        }
+        const double rz_new = env_sum_all(bv, K_VERT, env, bv.part + L.rz);
+        const double rr = env_sum_all(bv, K_VERT, env, bv.part + L.rr);
+        const double pq = env_sum_all(bv, K_VGRP, env, bv.part + L.pq);
+        if (threadIdx.x == 0) {
+          const double iters = c[3] + 1.0;
+          const bool done = rr <= c[4] || !(pq > 0.0) || !isfinite(rr) || iters >= max_iter;
+          n[0] = rz_new;
+          n[1] = rr;
+          n[2] = done ? 1.0 : 0.0;
+          n[3] = iters;
+          n[4] = c[4];
+          n[5] = pq;
         }
       }
-      rz = block_sum<kBlock>(rz);
-      rr = block_sum<kBlock>(rr);
-      if (threadIdx.x == 0) {
-        bv.part[L.rz + u] = rz;
-        bv.part[L.rr + u] = rr;
-      }
-    }
-    grid.sync();
-    // 5. per-env beta and stop test
-    for (int env = blockIdx.x; env < nenv; env += G) {
-      const double rz_new = env_unit_sum(bv, K_VERT, env, bv.part + L.rz);
-      const double rr = env_unit_sum(bv, K_VERT, env, bv.part + L.rr);
-      if (threadIdx.x == 0 && es[8 * env + 5] == 0.0) {
-        const double rz_old = es[8 * env + 2];
-        es[8 * env + 1] = rz_old > 0.0 ? rz_new / rz_old : 0.0;
-        es[8 * env + 2] = rz_new;
-        es[8 * env + 3] = rr;
-        es[8 * env + 6] += 1.0;
-        const double pq = es[8 * env + 4];
-        const bool done = rr <= es[8 * env + 7] || !(pq > 0.0) || !isfinite(rr) || es[8 * env + 6] >= max_iter;
-        es[8 * env + 5] = done ? 2.0 : 0.0;
-      }
-    }
-    grid.sync();
-    // 6. p = z + beta p for envs still running
-    for (int u = blockIdx.x; u < nV; u += G) {
-      const Loc l = locate(pre, nenv, K_VERT, u);
-      if (es[8 * l.env + 5] != 0.0) continue;
-      const EnvView<R>& e = bv.views[l.env];
-      const int nv = e.nv;
-      const int v = l.chunk * kBlock + threadIdx.x;
-      const R beta = (R)es[8 * l.env + 1];
-      if (v < nv)
-        for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + beta * e.p[i * nv + v];
     }
     grid.sync();
   }
-  // publish per-env results
+  // publish per-env results (the buffer the last iteration wrote)
+  const double* fin = es0 + (int64_t)(it & 1) * kEnvScalars * nenv;
   for (int env = blockIdx.x; env < nenv; env += G)
     if (threadIdx.x == 0) {
+      const double* c = fin + kEnvScalars * env;
       Scalars* sc = bv.views[env].sc;
-      sc->pcg_iters = (int)es[8 * env + 6];
-      sc->rz = es[8 * env + 2];
-      sc->rr = es[8 * env + 3];
-      sc->pq = es[8 * env + 4];
-      sc->pcg_tol2 = es[8 * env + 7];
+      sc->pcg_iters = (int)c[3];
+      sc->rz = c[0];
+      sc->rr = c[1];
+      sc->pq = c[5];
+      sc->pcg_tol2 = c[4];
       sc->pcg_done = 1;
       if (!isfinite(sc->rr) || !isfinite(sc->pq)) sc->status |= ST_NONFINITE;
     }
@@ -568,8 +533,7 @@ template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStre
   TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
   const int cap = CoopInfo<R>::max_blocks();
   if (cap <= 0) return TC_ERR_CUDA;
-  int work = std::max(b.units[K_TET], std::max(b.units[K_VGRP], b.units[K_VERT]));
-  work = std::max(work, std::max(b.nenv, b.units[K_CV] + b.units[K_CE] + b.units[K_CF]));
+  const int work = std::max(b.nenv, std::max(b.units[K_VGRP], b.units[K_VERT]));
   const int G = std::max(1, std::min(work, cap));
   BatchView<R> bv = b.bv;
   PartLayout L = b.L;

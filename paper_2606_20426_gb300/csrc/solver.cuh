@@ -13,7 +13,7 @@ struct PartLayout {
   int64_t ccd[3];    // contact units: min TOI
   int64_t pq;        // K_VGRP units: p.q
   int64_t rz, rr;    // K_VERT units
-  int64_t env_s;     // 8 per env: PCG scalars published between phases
+  int64_t env_s;     // 2 x 8 per env: PCG scalars, double-buffered by iteration parity
   int64_t total;
 };
 

@@ -24,7 +24,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "invalid mesh", 3: "initial penetra
 EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_traction", "tc_pressure_map", "tc_contact_force",
            "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
-           "tc_profile_read", "tc_pressure_map_noalloc"]
+           "tc_profile_read", "tc_pressure_map_noalloc", "tc_server_create", "tc_submit", "tc_poll", "tc_wait",
+           "tc_server_info", "tc_server_destroy"]
 
 
 class TcError(RuntimeError):
@@ -72,13 +73,25 @@ class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("ms", ctypes.c_double), ("launches", ctypes.c_int64)]
 
 
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("rounds", ctypes.c_int32)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("inflight_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("nf", ctypes.c_int32), ("nfc", ctypes.c_int32),
                 ("nec", ctypes.c_int32), ("nvc", ctypes.c_int32), ("ind_nv", ctypes.c_int32),
                 ("ind_nf", ctypes.c_int32), ("ind_ne", ctypes.c_int32), ("H", ctypes.c_int32),
                 ("W", ctypes.c_int32), ("newton_iters", ctypes.c_int64), ("pcg_iters", ctypes.c_int64),
                 ("substeps", ctypes.c_int64), ("steps", ctypes.c_int64), ("line_search_halvings", ctypes.c_int64),
-                ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("nnzb", ctypes.c_int64)]
 
 
 _lib = None
@@ -114,6 +127,11 @@ def load():
         "tc_profile_read": [P, ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
         "tc_pressure_map_noalloc": [P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P,
                                     ctypes.c_int32, P, P, ctypes.c_int32, P, P, P],
+        "tc_server_create": [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(P)],
+        "tc_submit": [P, P, ctypes.POINTER(Pose), P, P, P, ctypes.POINTER(ctypes.c_uint64)],
+        "tc_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Result)],
+        "tc_wait": [P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)],
+        "tc_server_info": [P, ctypes.POINTER(ServerStats)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -121,6 +139,8 @@ def load():
         f.restype = ctypes.c_int32
     lib.tc_destroy.argtypes = [P]
     lib.tc_destroy.restype = None
+    lib.tc_server_destroy.argtypes = [P]
+    lib.tc_server_destroy.restype = None
     lib.tc_status_str.argtypes = [ctypes.c_int32]
     lib.tc_status_str.restype = ctypes.c_char_p
     _lib = lib
@@ -301,6 +321,73 @@ class Env:
     def close(self):
         if getattr(self, "h", None):
             self.lib.tc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _result(r):
+    return {"status": int(r.status), "queue_us": r.queue_us, "latency_us": r.latency_us, "rounds": int(r.rounds)}
+
+
+class Server:
+    """Continuous-batching step server (tc_server_*): submit() queues one step
+    of an env and returns a ticket; wait()/poll() collect the result."""
+
+    TIMEOUT = 11
+
+    def __init__(self, hbm_budget_bytes, max_slots):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        _check(self.lib.tc_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
+               "tc_server_create")
+        self.h = h
+
+    def submit(self, env, pose, sigma=None, map=None, mask=None):
+        """Queue a step of `env` toward `pose`; sigma (6, nt), map (H, W) and
+        mask (H, W) are optional CUDA tensors written when the step is done."""
+        p = make_pose(pose)
+        t = ctypes.c_uint64()
+        _check(self.lib.tc_submit(self.h, env.h, ctypes.byref(p), _ptr(sigma), _ptr(map), _ptr(mask),
+                                  ctypes.byref(t)), "tc_submit")
+        return t.value
+
+    def poll(self, ticket):
+        done = ctypes.c_int32()
+        r = Result()
+        _check(self.lib.tc_poll(self.h, ticket, ctypes.byref(done), ctypes.byref(r)), "tc_poll")
+        return _result(r) if done.value else None
+
+    def wait(self, ticket, timeout_s=60.0):
+        """The request's result dict, or None if it is not done in time."""
+        r = Result()
+        code = self.lib.tc_wait(self.h, ticket, int(timeout_s * 1e6), ctypes.byref(r))
+        if code == self.TIMEOUT:
+            return None
+        _check(code, "tc_wait")
+        return _result(r)
+
+    def info(self):
+        st = ServerStats()
+        _check(self.lib.tc_server_info(self.h, ctypes.byref(st)), "tc_server_info")
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def stream(self):
+        """The server's CUDA stream as a torch stream (for events)."""
+        torch = _torch()
+        return torch.cuda.ExternalStream(self.info()["stream"])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.tc_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
