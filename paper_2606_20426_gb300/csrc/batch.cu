@@ -171,10 +171,9 @@ tc_status BatchExec<R>::build(const std::vector<Env*>& set, const double* params
   L.asmb = take(2 * tot[K_VGRP]);
   L.inert = take(tot[K_VERT]);
   for (int k = 0; k < 3; ++k) L.ccd[k] = take(tot[K_CV + k]);
-  L.pq = take(tot[K_VGRP]);
   L.rz = take(tot[K_VERT]);
   L.rr = take(tot[K_VERT]);
-  L.env_s = take(16 * (int64_t)n);
+  L.env_s = take(8 * (int64_t)n);
   L.total = off;
   // the staging buffers below may still feed the previous phase's copies
   TC_CHECK(cudaStreamSynchronize(stream));

@@ -244,99 +244,152 @@ TC_D void pair_points(const EnvView<R>& e, const Vec3<T>* xg, int ip, const Orig
   }
 }
 
+// Body-frame points of gel primitive `prim` at displacement u, relative to the
+// origin o of its first point.
+template <class R, int GK>
+TC_D void contact_prim_points(const EnvView<R>& e, const R* u, int prim, double bw[3][3], Origin* o) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  for (int l = 0; l < NGP; ++l) {
+    double w[3];
+    gel_world(e, u, gel_vertex(e, GK, prim, l), w);
+    to_body(e.Rm, e.tr, w, bw[l]);
+  }
+  *o = make_origin(bw[0]);
+}
+
 // One contact primitive pass over the candidate lists built by the last CCD
-// pass.  MODE 0: energy only; 1: energy + slots.
+// pass.  MODE 0: energy only; 1: energy + slots.  One unit = 128 gel
+// primitives; the unit's (primitive, candidate) pairs are flattened and
+// spread over all threads of the block, in chunks.  With MODE 1 each pair
+// writes its gradient and Hessian to shared memory, and the thread owning a
+// primitive then adds its pairs in candidate order (fixed-order sums, no
+// atomics) before rotating the sums to the world frame into the slots.
 template <class R, int GK, int MODE>
 __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int NG = 3 * NGP;
   constexpr int NH = NG * (NG + 1) / 2;
+  constexpr int CH = MODE == 1 ? 512 / (int)sizeof(R) : 128;  // pairs per chunk
+  __shared__ int s_off[129];
+  __shared__ R s_gh[MODE == 1 ? CH : 1][MODE == 1 ? NG + NH : 1];
   const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
   const EnvView<R>& e = bv.views[lc.env];
   const R* __restrict__ u = trial ? e.ut : e.u;
   double* part_out = bv.part + L.cont[GK];
-  const int prim = lc.chunk * 128 + threadIdx.x;
+  const int base = lc.chunk * 128;
   const int n = prim_count(e, GK);
+  const int32_t* cl = e.cand[GK];
+  const int mine = base + (int)threadIdx.x;
+  const int kept = mine < n ? min(e.cand_n[GK][mine], e.cand_cap) : 0;
+  if (threadIdx.x == 0) s_off[0] = 0;
+  s_off[threadIdx.x + 1] = kept;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
+  __syncthreads();
+  const int total = s_off[128];
   double energy = 0.0;
   double dmin2 = 1e300;
-  if (prim < n) {
-    double bw[3][3];
-    for (int l = 0; l < NGP; ++l) {
-      double w[3];
-      gel_world(e, u, gel_vertex(e, GK, prim, l), w);
-      to_body(e.Rm, e.tr, w, bw[l]);
-    }
-    const Origin o = make_origin(bw[0]);
-    Vec3<R> xg[NGP];
-    for (int l = 0; l < NGP; ++l) xg[l] = rel<R>(bw[l], o.d);
-    R gacc[NG];
-    R hacc[NH];
+  R gacc[MODE == 1 ? NG : 1];
+  R hacc[MODE == 1 ? NH : 1];
+  if (MODE == 1) {
 #pragma unroll
     for (int a = 0; a < NG; ++a) gacc[a] = R(0);
 #pragma unroll
     for (int a = 0; a < NH; ++a) hacc[a] = R(0);
-    const int kind = GK == GE ? 1 : 0;
-    int gs[3];
-    if (GK == GV) { gs[0] = 0; gs[1] = 0; gs[2] = 0; }
-    else if (GK == GE) { gs[0] = 0; gs[1] = 1; gs[2] = 0; }
-    else { gs[0] = 1; gs[1] = 2; gs[2] = 3; }
-    const double eps_base = GK == GE ? 1e-3 * e.gel_elen2[prim] : 0.0;
-    const R dhat2 = (R)(e.dhat * e.dhat);
-    const int32_t* cl = e.cand[GK];
-    const int nc = min(e.cand_n[GK][prim], e.cand_cap);
-    for (int j = 0; j < nc; ++j) {
+  }
+  const int kind = GK == GE ? 1 : 0;
+  int gs[3];
+  if (GK == GV) { gs[0] = 0; gs[1] = 0; gs[2] = 0; }
+  else if (GK == GE) { gs[0] = 0; gs[1] = 1; gs[2] = 0; }
+  else { gs[0] = 1; gs[1] = 2; gs[2] = 3; }
+  const R dhat2 = (R)(e.dhat * e.dhat);
+  for (int c0 = 0; c0 < total; c0 += CH) {
+    for (int q = c0 + (int)threadIdx.x; q < total && q < c0 + CH; q += 128) {
+      int lo_i = 0, hi_i = 127;  // last i with s_off[i] <= q
+      while (lo_i < hi_i) {
+        const int mid = (lo_i + hi_i + 1) >> 1;
+        if (s_off[mid] <= q) lo_i = mid;
+        else hi_i = mid - 1;
+      }
+      const int prim = base + lo_i, j = q - s_off[lo_i];
+      R* gp = MODE == 1 ? &s_gh[q - c0][0] : nullptr;
+      R* hp = MODE == 1 ? &s_gh[q - c0][NG] : nullptr;
+      if (MODE == 1)
+        for (int a = 0; a < NG + NH; ++a) s_gh[q - c0][a] = R(0);
+      double bw[3][3];
+      Origin o;
+      contact_prim_points<R, GK>(e, u, prim, bw, &o);
+      Vec3<R> xg[NGP];
+      for (int l = 0; l < NGP; ++l) xg[l] = rel<R>(bw[l], o.d);
       const int ip = cl[(int64_t)j * n + prim];
       Vec3<R> x[4];
       pair_points<R, R, GK>(e, xg, ip, o, x);
       const R d2 = pair_dist2<R>(kind, x, nullptr);
       dmin2 = fmin(dmin2, (double)d2);
       if (!(d2 < dhat2)) continue;
-      const double eps_x = GK == GE ? eps_base * e.ind_elen2[ip] : 0.0;
+      const double eps_x = GK == GE ? 1e-3 * e.gel_elen2[prim] * e.ind_elen2[ip] : 0.0;
       if (sizeof(R) == 4 && d2 < (R)(1e-4 * e.dhat * e.dhat)) {  // FP64 island for very close pairs
         Vec3<double> xgd[NGP];
         for (int l = 0; l < NGP; ++l) xgd[l] = rel<double>(bw[l], o.d);
         Vec3<double> xd[4];
         pair_points<double, R, GK>(e, xgd, ip, o, xd);
-        double gp[NG], hp[NH];
-        for (int a = 0; a < NG; ++a) gp[a] = 0.0;
-        for (int a = 0; a < NH; ++a) hp[a] = 0.0;
-        energy += pair_gn<double, NG>(kind, xd, gs, e.dhat, e.kappa, GK == GE, eps_x, MODE == 1, gp, hp);
+        double gd[MODE == 1 ? NG : 1], hd[MODE == 1 ? NH : 1];
         if (MODE == 1) {
-          for (int a = 0; a < NG; ++a) gacc[a] += (R)gp[a];
-          for (int a = 0; a < NH; ++a) hacc[a] += (R)hp[a];
+          for (int a = 0; a < NG; ++a) gd[a] = 0.0;
+          for (int a = 0; a < NH; ++a) hd[a] = 0.0;
+        }
+        energy += pair_gn<double, NG>(kind, xd, gs, e.dhat, e.kappa, GK == GE, eps_x, MODE == 1, gd, hd);
+        if (MODE == 1) {
+          for (int a = 0; a < NG; ++a) gp[a] = (R)gd[a];
+          for (int a = 0; a < NH; ++a) hp[a] = (R)hd[a];
         }
       } else {
-        energy += (double)pair_gn<R, NG>(kind, x, gs, (R)e.dhat, (R)e.kappa, GK == GE, (R)eps_x, MODE == 1, gacc, hacc);
+        energy += (double)pair_gn<R, NG>(kind, x, gs, (R)e.dhat, (R)e.kappa, GK == GE, (R)eps_x, MODE == 1, gp, hp);
       }
     }
     if (MODE == 1) {
-      // body -> world: g_w = R g_b per point, H_w = R H_b R^T per 3x3 block
-      R Rm[9];
-      for (int k = 0; k < 9; ++k) Rm[k] = (R)e.Rm[k];
-      R* slot = GK == GV ? e.cv_slot : (GK == GE ? e.ce_slot : e.cf_slot);
-      for (int l = 0; l < NGP; ++l)
-        for (int i = 0; i < 3; ++i) {
-          R s = 0;
-          for (int k = 0; k < 3; ++k) s += Rm[3 * i + k] * gacc[3 * l + k];
-          slot[(int64_t)(3 * l + i) * n + prim] = s;
+      __syncthreads();
+      if (kept > 0) {
+        const int a0 = max(s_off[threadIdx.x], c0), a1 = min(s_off[threadIdx.x + 1], c0 + CH);
+        for (int q = a0; q < a1; ++q) {
+#pragma unroll
+          for (int a = 0; a < NG; ++a) gacc[a] += s_gh[q - c0][a];
+#pragma unroll
+          for (int a = 0; a < NH; ++a) hacc[a] += s_gh[q - c0][NG + a];
         }
-      for (int la = 0; la < NGP; ++la)
-        for (int lb = la; lb < NGP; ++lb) {
-          R B[3][3];
-          for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) B[i][j] = hacc[sym_index(3 * la + i, 3 * lb + j, NG)];
-          R T1[3][3];
-          for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) T1[i][j] = Rm[3 * i + 0] * B[0][j] + Rm[3 * i + 1] * B[1][j] + Rm[3 * i + 2] * B[2][j];
-          for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-              const int ra = 3 * la + i, cb = 3 * lb + j;
-              if (ra > cb) continue;  // packed upper triangle
-              const R v = T1[i][0] * Rm[3 * j + 0] + T1[i][1] * Rm[3 * j + 1] + T1[i][2] * Rm[3 * j + 2];
-              slot[(int64_t)(NG + sym_index(ra, cb, NG)) * n + prim] = v;
-            }
-        }
+      }
+      __syncthreads();
     }
+  }
+  if (MODE == 1 && mine < n) {
+    const int prim = mine;
+    // body -> world: g_w = R g_b per point, H_w = R H_b R^T per 3x3 block
+    R Rm[9];
+    for (int k = 0; k < 9; ++k) Rm[k] = (R)e.Rm[k];
+    R* slot = GK == GV ? e.cv_slot : (GK == GE ? e.ce_slot : e.cf_slot);
+    for (int l = 0; l < NGP; ++l)
+      for (int i = 0; i < 3; ++i) {
+        R s = 0;
+        for (int k = 0; k < 3; ++k) s += Rm[3 * i + k] * gacc[3 * l + k];
+        slot[(int64_t)(3 * l + i) * n + prim] = s;
+      }
+    for (int la = 0; la < NGP; ++la)
+      for (int lb = la; lb < NGP; ++lb) {
+        R B[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) B[i][j] = hacc[sym_index(3 * la + i, 3 * lb + j, NG)];
+        R T1[3][3];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) T1[i][j] = Rm[3 * i + 0] * B[0][j] + Rm[3 * i + 1] * B[1][j] + Rm[3 * i + 2] * B[2][j];
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) {
+            const int ra = 3 * la + i, cb = 3 * lb + j;
+            if (ra > cb) continue;  // packed upper triangle
+            const R v = T1[i][0] * Rm[3 * j + 0] + T1[i][1] * Rm[3 * j + 1] + T1[i][2] * Rm[3 * j + 2];
+            slot[(int64_t)(NG + sym_index(ra, cb, NG)) * n + prim] = v;
+          }
+      }
   }
   energy = block_sum<128>(energy);
   dmin2 = block_min<128>(dmin2);
@@ -370,67 +423,109 @@ template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, 
 // indenter is static there); additive CCD per candidate pair in type R on
 // coordinates relative to the primitive's first gel point.
 
+// Swept geometry of one gel primitive in the indenter's body frame: start
+// points b0, end points b1 and the FP32 box (outward-rounded, grown by dhat).
+template <class R, int GK>
+TC_D void ccd_prim_geom(const EnvView<R>& e, const Motion& mo, const R* dir, int prim, double b0[3][3],
+                        double b1[3][3], float lo[3], float hi[3]) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = 3e38f;
+    hi[d] = -3e38f;
+  }
+  for (int l = 0; l < NGP; ++l) {
+    const int v = gel_vertex(e, GK, prim, l);
+    double w[3];
+    gel_world(e, e.u, v, w);
+    to_body(mo.Ra, mo.ta, w, b0[l]);
+    if (dir)
+      for (int d = 0; d < 3; ++d) w[d] += (double)dir[d * e.nv + v];
+    to_body(mo.Rb, mo.tb, w, b1[l]);
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = fminf(lo[d], __double2float_rd(fmin(b0[l][d], b1[l][d]) - e.dhat));
+      hi[d] = fmaxf(hi[d], __double2float_ru(fmax(b0[l][d], b1[l][d]) + e.dhat));
+    }
+  }
+}
+
+// One unit = 128 gel primitives.  Broad phase, one thread per primitive:
+// visit the grid cells of the swept box and write every indenter primitive
+// found to the candidate list (these lists feed the contact and energy passes
+// until the next CCD pass).  Narrow phase, all threads of the block over the
+// unit's flattened (primitive, candidate) pairs: additive CCD per pair, so
+// the few primitives near the indenter do not serialise the block.
 template <class R, int GK>
 __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
+  __shared__ int s_off[129];
   const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
   const EnvView<R>& e = bv.views[lc.env];
   const Motion& mo = bv.motion[lc.env];
   const R* __restrict__ dir = mo.use_dir ? e.dx : nullptr;
   double* part_out = bv.part + L.ccd[GK];
-  const int prim = lc.chunk * 128 + threadIdx.x;
+  const int base = lc.chunk * 128;
   const int n = prim_count(e, GK);
-  double tmin = 1.0;
-  if (prim < n) {
+  int32_t* cl = e.cand[GK];
+  int kept = 0;
+  if (base + (int)threadIdx.x < n) {
+    const int prim = base + threadIdx.x;
     double b0[3][3], b1[3][3];
-    float lo[3] = {3e38f, 3e38f, 3e38f}, hi[3] = {-3e38f, -3e38f, -3e38f};
-    for (int l = 0; l < NGP; ++l) {
-      const int v = gel_vertex(e, GK, prim, l);
-      double w[3];
-      gel_world(e, e.u, v, w);
-      to_body(mo.Ra, mo.ta, w, b0[l]);
-      if (dir)
-        for (int d = 0; d < 3; ++d) w[d] += (double)dir[d * e.nv + v];
-      to_body(mo.Rb, mo.tb, w, b1[l]);
-      for (int d = 0; d < 3; ++d) {
-        lo[d] = fminf(lo[d], __double2float_rd(fmin(b0[l][d], b1[l][d]) - e.dhat));
-        hi[d] = fmaxf(hi[d], __double2float_ru(fmax(b0[l][d], b1[l][d]) + e.dhat));
-      }
+    float lo[3], hi[3];
+    ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, lo, hi);
+    int cnt = 0;
+    grid_visit<R>(e, ik, lo, hi, [&](int ip) {
+      if (cnt < e.cand_cap) cl[(int64_t)cnt * n + prim] = ip;
+      ++cnt;
+    });
+    e.cand_n[GK][prim] = cnt;
+    if (cnt > e.cand_cap) atomicMax(&e.sc->overflow, cnt);
+    kept = cnt < e.cand_cap ? cnt : e.cand_cap;
+  }
+  // exclusive prefix of the kept counts (128 threads, fixed order)
+  if (threadIdx.x == 0) s_off[0] = 0;
+  s_off[threadIdx.x + 1] = kept;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
+  __syncthreads();
+  const int total = s_off[128];
+  double tmin = 1.0;
+  const int kind = GK == GE ? 1 : 0;
+  for (int q = threadIdx.x; q < total; q += 128) {
+    int lo_i = 0, hi_i = 127;  // last i with s_off[i] <= q
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (s_off[mid] <= q) lo_i = mid;
+      else hi_i = mid - 1;
     }
+    const int prim = base + lo_i, j = q - s_off[lo_i];
+    double b0[3][3], b1[3][3];
+    float blo[3], bhi[3];
+    ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, blo, bhi);
     const Origin o = make_origin(b0[0]);
     Vec3<R> xg[NGP], pg[NGP];
     for (int l = 0; l < NGP; ++l) {
       xg[l] = rel<R>(b0[l], o.d);
       pg[l] = rel<R>(b1[l], b0[l]);
     }
-    const int kind = GK == GE ? 1 : 0;
-    int32_t* cl = e.cand[GK];
-    int cnt = 0;
-    grid_visit<R>(e, ik, lo, hi, [&](int ip) {
-      // every pair the swept boxes admit is a candidate for the contact and
-      // energy passes until the next CCD pass
-      if (cnt < e.cand_cap) cl[(int64_t)cnt * n + prim] = ip;
-      ++cnt;
-      Vec3<R> x0[4], p[4];
-      pair_points<R, R, GK>(e, xg, ip, o, x0);
-      const Vec3<R> zero = v3<R>(0, 0, 0);
-      if (GK == GV) {
-        p[0] = pg[0];
-        p[1] = p[2] = p[3] = zero;
-      } else if (GK == GF) {
-        p[0] = zero;
-        for (int l = 0; l < 3; ++l) p[1 + l] = pg[l];
-      } else {
-        p[0] = pg[0];
-        p[1] = pg[1];
-        p[2] = p[3] = zero;
-      }
-      const R t = accd<R>(kind, x0, p, (R)1.0, 4096);
-      tmin = fmin(tmin, (double)t);
-    });
-    e.cand_n[GK][prim] = cnt;
-    if (cnt > e.cand_cap) atomicMax(&e.sc->overflow, cnt);
+    const int ip = cl[(int64_t)j * n + prim];
+    Vec3<R> x0[4], p[4];
+    pair_points<R, R, GK>(e, xg, ip, o, x0);
+    const Vec3<R> zero = v3<R>(0, 0, 0);
+    if (GK == GV) {
+      p[0] = pg[0];
+      p[1] = p[2] = p[3] = zero;
+    } else if (GK == GF) {
+      p[0] = zero;
+      for (int l = 0; l < 3; ++l) p[1 + l] = pg[l];
+    } else {
+      p[0] = pg[0];
+      p[1] = pg[1];
+      p[2] = p[3] = zero;
+    }
+    const R t = accd<R>(kind, x0, p, (R)1.0, 4096);
+    tmin = fmin(tmin, (double)t);
   }
   tmin = block_min<128>(tmin);
   if (threadIdx.x == 0) part_out[blockIdx.x] = tmin;

@@ -12,6 +12,9 @@
 // double.  Results do not depend on the batch composition or the schedule.
 #include <cooperative_groups.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "env.cuh"
 #include "prof.cuh"
 #include "solver.cuh"
@@ -293,11 +296,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, Part
   }
 }
 
-// Per-env PCG scalars, double-buffered by iteration parity: iteration `it`
-// reads buffer it & 1 and the env's designated block writes buffer
-// (it + 1) & 1, so no block reads a value while it is being replaced.
-// Fields: 0 r.z, 1 r.r, 2 done (0 running, 1 stopped), 3 iterations,
-// 4 squared tolerance, 5 p.q of the last iteration.
+// Per-env PCG start values written by k_pcg_init_env: 0 r.z, 1 r.r,
+// 2 done (1 when the start residual already meets the tolerance),
+// 3 iterations, 4 squared tolerance, 5 p.q.
 constexpr int kEnvScalars = 8;
 
 // per env: r.z, r.r and the squared stopping tolerance (param[env]) -> buffer 0
@@ -351,197 +352,240 @@ template <class R> TC_D double bsr_q_group(const EnvView<R>& e, int v, bool vali
   return pq;
 }
 
-// block-wide sum broadcast to every thread
-TC_D double block_sum_all(double v) {
-  __shared__ double s_tot;
-  const double t = block_sum<kBlock>(v);
-  if (threadIdx.x == 0) s_tot = t;
+// ------------------------------------------------- PCG, one cluster per env
+// Every env of the batch runs all of its CG iterations in one thread-block
+// cluster (16 CTAs where the GPU can co-schedule them, else 8; 1024 threads
+// each) over a contiguous share of the env's rows, so envs iterate
+// independently: an env that converges frees its SMs at once, and no grid-wide
+// barrier ties envs together.  Per iteration:
+//   A  q = A p (BSR rows, one 8-lane group per row), p.q          | cluster barrier
+//   B  alpha = r.z / p.q, dx += alpha p, r -= alpha q, z = M^-1 r;
+//      r.z, r.r                                                    | cluster barrier
+//   C  beta = r.z_new / r.z, stop test, p = z + beta p             | cluster barrier
+// Each CTA reduces its rows in a fixed tree and posts the result in its
+// shared memory; after the barrier every CTA adds the CS posts in rank order
+// through distributed shared memory, so all CTAs hold bit-identical scalars
+// and take the same branch.  Results do not depend on the other envs.
+constexpr int kPcgThreads = 1024;
+
+// Sum of `nval` posted values over the CS ranks of the cluster, in a fixed
+// shuffle tree on warp 0 (the same tree in every CTA), broadcast to the block.
+template <int NVAL>
+TC_D void cluster_gather(cg::cluster_group& cluster, int CS, double* s_post, double* s_bcast, double out[NVAL]) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    const double* remote = lane < CS ? cluster.map_shared_rank(s_post, lane) : nullptr;
+#pragma unroll
+    for (int k = 0; k < NVAL; ++k) {
+      double v = lane < CS ? remote[k] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) s_bcast[k] = v;
+    }
+  }
   __syncthreads();
-  const double r = s_tot;
-  __syncthreads();
-  return r;
+#pragma unroll
+  for (int k = 0; k < NVAL; ++k) out[k] = s_bcast[k];
 }
 
-template <class R> TC_D double env_sum_all(const BatchView<R>& bv, int kind, int env, const double* part) {
-  const int* p = bv.prefix + kind * (bv.nenv + 1);
-  double s = 0.0;
-  for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) s += part[u];
-  return block_sum_all(s);
-}
-
-// ------------------------------------------------------ persistent PCG
-// All CG iterations of all envs of the batch in one cooperative launch, over
-// contiguous ranges of work units per block.  Per iteration:
-//   A  q = A p (BSR rows), p.q partials                           | sync
-//   B  alpha = r.z / p.q per env, dx += alpha p, r -= alpha q,
-//      z = M^-1 r; r.z, r.r partials                              | sync
-//   C  beta = r.z_new / r.z per env, stop test, p = z + beta p;
-//      each env's designated block publishes its new scalars      | sync
-// Every block folds the partials of the envs it touches itself, in unit
-// order with the same reduction tree, so all blocks hold bit-identical
-// per-env scalars without waiting for one writer; converged envs skip their
-// work while the others continue.  Results do not depend on the grid size or
-// on which other envs are in the batch.
+// q = A p for two rows per lane group at once (independent loads in flight)
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_batched(const BatchView<R> bv, PartLayout L, int max_iter) {
-  cg::grid_group grid = cg::this_grid();
-  const int G = gridDim.x;
-  const int nenv = bv.nenv;
-  const int* pre = bv.prefix;
-  const int nG = pre[K_VGRP * (nenv + 1) + nenv];
-  const int nV = pre[K_VERT * (nenv + 1) + nenv];
-  const int g0 = (int)((int64_t)nG * blockIdx.x / G), g1 = (int)((int64_t)nG * (blockIdx.x + 1) / G);
-  const int w0 = (int)((int64_t)nV * blockIdx.x / G), w1 = (int)((int64_t)nV * (blockIdx.x + 1) / G);
-  double* es0 = bv.part + L.env_s;
-  int it = 0;
-  for (; it < max_iter; ++it) {
-    const double* cur = es0 + (int64_t)(it & 1) * kEnvScalars * nenv;
-    double* nxt = es0 + (int64_t)((it + 1) & 1) * kEnvScalars * nenv;
-    int all_done = 1;
-    for (int env = 0; env < nenv; ++env) all_done &= cur[kEnvScalars * env + 2] != 0.0;
-    if (all_done) break;
-    // A. q = A p
-    for (int u = g0; u < g1; ++u) {
-      const Loc l = locate(pre, nenv, K_VGRP, u);
-      double pq = 0.0;
-      if (cur[kEnvScalars * l.env + 2] == 0.0) {
-        const EnvView<R>& e = bv.views[l.env];
-        const int v = l.chunk * 32 + threadIdx.x / kLanes;
-        pq = bsr_q_group<R>(e, v, v < e.nv && !e.fixed[v]);
-      }
-      pq = block_sum<kBlock>(pq);
-      if (threadIdx.x == 0) bv.part[L.pq + u] = pq;
+TC_D void bsr_rows2(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const R* __restrict__ val,
+                    int64_t nb, const R* p, R* q, int nv, int v0, int v1, int r1, double& pq) {
+  const int lane = threadIdx.x & (kLanes - 1);
+  const bool ok0 = v0 < r1, ok1 = v1 < r1;
+  R a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
+  const int k0s = ok0 ? __ldg(rp + v0) : 0, k0e = ok0 ? __ldg(rp + v0 + 1) : 0;
+  const int k1s = ok1 ? __ldg(rp + v1) : 0, k1e = ok1 ? __ldg(rp + v1 + 1) : 0;
+  int k0 = k0s + lane, k1 = k1s + lane;
+  while (k0 < k0e || k1 < k1e) {
+    if (k0 < k0e) {
+      const int j = __ldg(ci + k0);
+      const R p0 = p[j], p1 = p[nv + j], p2 = p[2 * nv + j];
+      const R* B = val + k0;
+      a0 += __ldg(B) * p0 + __ldg(B + nb) * p1 + __ldg(B + 2 * nb) * p2;
+      a1 += __ldg(B + 3 * nb) * p0 + __ldg(B + 4 * nb) * p1 + __ldg(B + 5 * nb) * p2;
+      a2 += __ldg(B + 6 * nb) * p0 + __ldg(B + 7 * nb) * p1 + __ldg(B + 8 * nb) * p2;
+      k0 += kLanes;
     }
-    grid.sync();
-    // B. vector update
-    {
-      int cenv = -1;
-      R alpha = 0;
-      for (int u = w0; u < w1; ++u) {
-        const Loc l = locate(pre, nenv, K_VERT, u);
-        double rz = 0.0, rr = 0.0;
-        if (cur[kEnvScalars * l.env + 2] == 0.0) {
-          if (l.env != cenv) {
-            cenv = l.env;
-            const double pq = env_sum_all(bv, K_VGRP, cenv, bv.part + L.pq);
-            alpha = (R)(pq > 0.0 ? cur[kEnvScalars * cenv + 0] / pq : 0.0);
-          }
-          const EnvView<R>& e = bv.views[l.env];
-          const int nv = e.nv;
-          const int v = l.chunk * kBlock + threadIdx.x;
-          if (v < nv) {
-            R r[3], z[3];
-            for (int i = 0; i < 3; ++i) {
-              e.dx[i * nv + v] += alpha * e.p[i * nv + v];
-              r[i] = e.r[i * nv + v] - alpha * e.q[i * nv + v];
-              e.r[i * nv + v] = r[i];
-            }
-            apply_minv<R>(e, v, r, z);
-            for (int i = 0; i < 3; ++i) {
-              e.z[i * nv + v] = z[i];
-              rz += (double)r[i] * (double)z[i];
-              rr += (double)r[i] * (double)r[i];
-            }
-          }
-        }
-        rz = block_sum<kBlock>(rz);
-        rr = block_sum<kBlock>(rr);
-        if (threadIdx.x == 0) {
-          bv.part[L.rz + u] = rz;
-          bv.part[L.rr + u] = rr;
-        }
-      }
+    if (k1 < k1e) {
+      const int j = __ldg(ci + k1);
+      const R p0 = p[j], p1 = p[nv + j], p2 = p[2 * nv + j];
+      const R* B = val + k1;
+      b0 += __ldg(B) * p0 + __ldg(B + nb) * p1 + __ldg(B + 2 * nb) * p2;
+      b1 += __ldg(B + 3 * nb) * p0 + __ldg(B + 4 * nb) * p1 + __ldg(B + 5 * nb) * p2;
+      b2 += __ldg(B + 6 * nb) * p0 + __ldg(B + 7 * nb) * p1 + __ldg(B + 8 * nb) * p2;
+      k1 += kLanes;
     }
-    grid.sync();
-    // C. direction update and the published scalars
-    {
-      int cenv = -1;
-      R beta = 0;
-      for (int u = w0; u < w1; ++u) {
-        const Loc l = locate(pre, nenv, K_VERT, u);
-        if (cur[kEnvScalars * l.env + 2] != 0.0) continue;
-        if (l.env != cenv) {
-          cenv = l.env;
-          const double rz_new = env_sum_all(bv, K_VERT, cenv, bv.part + L.rz);
-          const double rz_old = cur[kEnvScalars * cenv + 0];
-          beta = (R)(rz_old > 0.0 ? rz_new / rz_old : 0.0);
-        }
-        const EnvView<R>& e = bv.views[l.env];
-        const int nv = e.nv;
-        const int v = l.chunk * kBlock + threadIdx.x;
-        if (v < nv)
-          for (int i = 0; i < 3; ++i) e.p[i * nv + v] = e.z[i * nv + v] + beta * e.p[i * nv + v];
-      }
-      for (int env = blockIdx.x; env < nenv; env += G) {
-        const double* c = cur + kEnvScalars * env;
-        double* n = nxt + kEnvScalars * env;
-        if (c[2] != 0.0) {
-          if (threadIdx.x == 0)
-            for (int f = 0; f < kEnvScalars; ++f) n[f] = c[f];
-          continue;
-        }
-        const double rz_new = env_sum_all(bv, K_VERT, env, bv.part + L.rz);
-        const double rr = env_sum_all(bv, K_VERT, env, bv.part + L.rr);
-        const double pq = env_sum_all(bv, K_VGRP, env, bv.part + L.pq);
-        if (threadIdx.x == 0) {
-          const double iters = c[3] + 1.0;
-          const bool done = rr <= c[4] || !(pq > 0.0) || !isfinite(rr) || iters >= max_iter;
-          n[0] = rz_new;
-          n[1] = rr;
-          n[2] = done ? 1.0 : 0.0;
-          n[3] = iters;
-          n[4] = c[4];
-          n[5] = pq;
-        }
-      }
-    }
-    grid.sync();
   }
-  // publish per-env results (the buffer the last iteration wrote)
-  const double* fin = es0 + (int64_t)(it & 1) * kEnvScalars * nenv;
-  for (int env = blockIdx.x; env < nenv; env += G)
-    if (threadIdx.x == 0) {
-      const double* c = fin + kEnvScalars * env;
-      Scalars* sc = bv.views[env].sc;
-      sc->pcg_iters = (int)c[3];
-      sc->rz = c[0];
-      sc->rr = c[1];
-      sc->pq = c[5];
-      sc->pcg_tol2 = c[4];
-      sc->pcg_done = 1;
-      if (!isfinite(sc->rr) || !isfinite(sc->pq)) sc->status |= ST_NONFINITE;
+  a0 = group_sum(a0);
+  a1 = group_sum(a1);
+  a2 = group_sum(a2);
+  b0 = group_sum(b0);
+  b1 = group_sum(b1);
+  b2 = group_sum(b2);
+  if (lane == 0) {
+    if (ok0) {
+      q[v0] = a0;
+      q[nv + v0] = a1;
+      q[2 * nv + v0] = a2;
+      pq += (double)p[v0] * (double)a0 + (double)p[nv + v0] * (double)a1 + (double)p[2 * nv + v0] * (double)a2;
     }
+    if (ok1) {
+      q[v1] = b0;
+      q[nv + v1] = b1;
+      q[2 * nv + v1] = b2;
+      pq += (double)p[v1] * (double)b0 + (double)p[nv + v1] * (double)b1 + (double)p[2 * nv + v1] * (double)b2;
+    }
+  }
 }
 
-template <class R> struct CoopInfo {
-  static int max_blocks() {
-    static int cached = -1;
-    if (cached < 0) {
-      int dev = 0, sms = 0, per_sm = 0, coop = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched<R>, kBlock, 0);
-      cached = coop ? sms * per_sm : 0;
+template <class R>
+__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cluster(const BatchView<R> bv, PartLayout L, int max_iter) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int env = blockIdx.x / CS;
+  __shared__ double s_post[3];
+  __shared__ double s_bcast[3];
+  const EnvView<R>& ev = bv.views[env];
+  const int nv = ev.nv;
+  const int64_t nb = ev.nnzb;
+  const int32_t* __restrict__ rp = ev.bsr_rp;
+  const int32_t* __restrict__ ci = ev.bsr_ci;
+  const R* __restrict__ val = ev.bsr_val;
+  const R* __restrict__ Minv = ev.Minv;
+  R* p = ev.p;
+  R* q = ev.q;
+  R* r = ev.r;
+  R* z = ev.z;
+  R* dx = ev.dx;
+  const int r0 = (int)((int64_t)nv * rank / CS), r1 = (int)((int64_t)nv * (rank + 1) / CS);
+  const double* es = bv.part + L.env_s + kEnvScalars * env;
+  double rz = es[0], rr = es[1], pq = 0.0;
+  const double tol2 = es[4];
+  bool done = es[2] != 0.0;
+  int it = 0;
+  constexpr int kGroups = kPcgThreads / kLanes;
+  while (!done && it < max_iter) {
+    // A. q = A p
+    double loc = 0.0;
+    const int g = (int)threadIdx.x / kLanes;
+    for (int base = r0; base < r1; base += 2 * kGroups)  // block-uniform trip count
+      bsr_rows2<R>(rp, ci, val, nb, p, q, nv, base + g, base + g + kGroups, r1, loc);
+    loc = block_sum<kPcgThreads>(loc);
+    if (threadIdx.x == 0) s_post[0] = loc;
+    cluster.sync();
+    double g1[1];
+    cluster_gather<1>(cluster, CS, s_post, s_bcast, g1);
+    pq = g1[0];
+    const R alpha = (R)(pq > 0.0 ? rz / pq : 0.0);
+    // B. vector update
+    double lrz = 0.0, lrr = 0.0;
+    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
+      R rv[3], zv[3];
+      for (int i = 0; i < 3; ++i) {
+        dx[i * nv + v] += alpha * p[i * nv + v];
+        rv[i] = r[i * nv + v] - alpha * q[i * nv + v];
+        r[i * nv + v] = rv[i];
+      }
+      const R m0 = __ldg(Minv + v), m1 = __ldg(Minv + nv + v), m2 = __ldg(Minv + 2 * nv + v);
+      const R m3 = __ldg(Minv + 3 * nv + v), m4 = __ldg(Minv + 4 * nv + v), m5 = __ldg(Minv + 5 * nv + v);
+      zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
+      zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
+      zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
+      for (int i = 0; i < 3; ++i) {
+        z[i * nv + v] = zv[i];
+        lrz += (double)rv[i] * (double)zv[i];
+        lrr += (double)rv[i] * (double)rv[i];
+      }
     }
-    return cached;
+    lrz = block_sum<kPcgThreads>(lrz);
+    lrr = block_sum<kPcgThreads>(lrr);
+    if (threadIdx.x == 0) {
+      s_post[1] = lrz;
+      s_post[2] = lrr;
+    }
+    cluster.sync();
+    double g3[3];
+    cluster_gather<3>(cluster, CS, s_post, s_bcast, g3);
+    const double rz_new = g3[1];
+    rr = g3[2];
+    ++it;
+    done = rr <= tol2 || !(pq > 0.0) || !isfinite(rr) || it >= max_iter;
+    const R beta = (R)(rz > 0.0 ? rz_new / rz : 0.0);
+    rz = rz_new;
+    if (done) break;
+    // C. direction update
+    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads)
+      for (int i = 0; i < 3; ++i) p[i * nv + v] = z[i * nv + v] + beta * p[i * nv + v];
+    cluster.sync();
   }
-};
+  if (rank == 0 && threadIdx.x == 0) {
+    Scalars* sc = ev.sc;
+    sc->pcg_iters = it;
+    sc->rz = rz;
+    sc->rr = rr;
+    sc->pq = pq;
+    sc->pcg_tol2 = tol2;
+    sc->pcg_done = 1;
+    if (!isfinite(rr) || !isfinite(pq)) sc->status |= ST_NONFINITE;
+  }
+  // no CTA may leave while another can still read its shared memory
+  cluster.sync();
+}
+
+// Largest cluster the GPU co-schedules for the PCG kernel: 16 (non-portable)
+// if possible, else the portable 8.
+template <class R> static int pcg_cluster_size() {
+  static int cached = -1;
+  if (cached < 0) {
+    cached = 8;
+    if (cudaFuncSetAttribute(k_pcg_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kPcgThreads);
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<R>, &cfg) == cudaSuccess && n > 0) cached = 16;
+      const char* tr = std::getenv("TACAUCHY_TRACE");
+      if (tr && tr[0] && tr[0] != '0') {
+        int n8 = 0;
+        attr[0].val.clusterDim.x = 8;
+        cfg.gridDim = dim3(8);
+        cudaOccupancyMaxActiveClusters(&n8, k_pcg_cluster<R>, &cfg);
+        std::fprintf(stderr, "[tc] pcg cluster size %d (co-resident clusters: %d of 16 CTAs, %d of 8)\n", cached, n, n8);
+      }
+    }
+    cudaGetLastError();
+  }
+  return cached;
+}
 
 template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s) {
   if (b.units[K_VERT] > 0) TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
   TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
-  const int cap = CoopInfo<R>::max_blocks();
-  if (cap <= 0) return TC_ERR_CUDA;
-  const int work = std::max(b.nenv, std::max(b.units[K_VGRP], b.units[K_VERT]));
-  const int G = std::max(1, std::min(work, cap));
-  BatchView<R> bv = b.bv;
-  PartLayout L = b.L;
-  int mi = max_iter;
-  void* args[] = {(void*)&bv, (void*)&L, (void*)&mi};
+  const int CS = pcg_cluster_size<R>();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(b.nenv * CS));
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cudaError_t err = cudaSuccess;
-  TC_LAUNCH("k_pcg_batched", s,
-            err = cudaLaunchCooperativeKernel((void*)k_pcg_batched<R>, dim3(G), dim3(kBlock), args, 0, s));
+  TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R>, b.bv, b.L, max_iter));
   return err == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 

@@ -11,9 +11,8 @@ struct PartLayout {
   int64_t asmb;      // K_VGRP units: (|g|^2, inertia energy)
   int64_t inert;     // K_VERT units: trial inertia energy
   int64_t ccd[3];    // contact units: min TOI
-  int64_t pq;        // K_VGRP units: p.q
   int64_t rz, rr;    // K_VERT units
-  int64_t env_s;     // 2 x 8 per env: PCG scalars, double-buffered by iteration parity
+  int64_t env_s;     // 8 per env: PCG start values
   int64_t total;
 };
 
