@@ -29,9 +29,12 @@ namespace tc {
   } while (0)
 
 // TACAUCHY_TRACE=1 prints one line per env and Newton iteration to stderr.
-static bool trace_on() {
-  const char* v = std::getenv("TACAUCHY_TRACE");
-  return v && v[0] && v[0] != '0';
+bool trace_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("TACAUCHY_TRACE");
+    return v && v[0] && v[0] != '0';
+  }();
+  return on;
 }
 
 void pose_interp(const tc_pose& a, const tc_pose& b, double s, tc_pose* out) {

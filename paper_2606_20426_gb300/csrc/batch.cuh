@@ -65,6 +65,8 @@ template <class R> struct StepScheduler {
   bool empty() const { return tasks.empty(); }
 };
 
+// TACAUCHY_TRACE set (and not 0): per-iteration trace lines on stderr
+bool trace_on();
 void pose_interp(const tc_pose& a, const tc_pose& b, double s, tc_pose* out);
 tc_status alloc_candidates(Env& env, int cap);
 template <class R> tc_status ensure_candidates(BatchExec<R>& X, const std::vector<Env*>& envs);

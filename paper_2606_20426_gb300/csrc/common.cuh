@@ -80,6 +80,77 @@ TC_D double warp_min(double v) {
   return v;
 }
 
+// ---------------------------------------------------------- double-float
+// On this part FP64 instructions issue at a small fraction of the FP32 rate,
+// so accumulators that must carry more than 24 bits use an unevaluated pair
+// of floats (hi + lo, Dekker / Knuth error-free transformations): products of
+// two floats are exact (FMA residual), sums keep ~48 bits.
+struct DF {
+  float hi, lo;
+};
+TC_D DF df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+TC_D DF df_add(DF x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  const float e = s.lo + x.lo + y.lo;
+  const float h = s.hi + e;
+  return {h, e - (h - s.hi)};
+}
+TC_D DF df_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+TC_D DF df_shfl_xor(DF v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// Accumulator of a precision: double-float for FP32 work, double for FP64.
+template <class R> struct Acc;
+template <> struct Acc<float> {
+  using T = DF;
+  static TC_D T zero() { return {0.f, 0.f}; }
+  static TC_D T prod(float a, float b) { return df_prod(a, b); }
+  static TC_D T add(T a, T b) { return df_add(a, b); }
+  static TC_D T shfl_xor(T v, int o) { return df_shfl_xor(v, o); }
+  static TC_D double to_double(T v) { return (double)v.hi + (double)v.lo; }
+};
+template <> struct Acc<double> {
+  using T = double;
+  static TC_D T zero() { return 0.0; }
+  static TC_D T prod(double a, double b) { return a * b; }
+  static TC_D T add(T a, T b) { return a + b; }
+  static TC_D T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  static TC_D double to_double(T v) { return v; }
+};
+
+// Block sums of NV accumulators per thread (fixed tree); totals in s[k][0]
+// after the call, visible to every thread.
+template <class R, int NV> TC_D void block_acc_sum(typename Acc<R>::T* v, typename Acc<R>::T (*s)[32]) {
+  using A = Acc<R>;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    typename A::T x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+    if (lane == 0) s[k][w] = x;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      typename A::T x = lane < (int)(blockDim.x >> 5) ? s[k][lane] : A::zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+      if (lane == 0) s[k][0] = x;
+    }
+  }
+  __syncthreads();
+}
+
 // Block sum of one double per thread; result valid in thread 0.
 // Fixed combination order -> deterministic.
 template <int NT> TC_D double block_sum(double v) {

@@ -16,6 +16,7 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
 #include <deque>
 #include <mutex>
 #include <new>
@@ -142,8 +143,13 @@ void Server::run() {
     }
     fin.clear();
     tc_status st = TC_OK;
+    const Clock::time_point t_round = Clock::now();
     if (!s32.empty()) st = s32.round(fin);
     if (st == TC_OK && !s64.empty()) st = s64.round(fin);
+    if (trace_on())
+      std::fprintf(stderr, "[tc] server round %lld: %zu in flight, %zu admitted, %zu finished, %.3f ms\n",
+                   (long long)rounds.load(), live.size(), admitted.size(), fin.size(),
+                   std::chrono::duration<double, std::milli>(Clock::now() - t_round).count());
     for (Req* r : live) r->rounds++;
     rounds++;
     std::vector<std::pair<Req*, tc_status>> done;

@@ -17,6 +17,7 @@
 
 #include "env.cuh"
 #include "prof.cuh"
+#include "batch.cuh"
 #include "solver.cuh"
 
 namespace cg = cooperative_groups;
@@ -354,100 +355,45 @@ template <class R> TC_D double bsr_q_group(const EnvView<R>& e, int v, bool vali
 
 // ------------------------------------------------- PCG, one cluster per env
 // Every env of the batch runs all of its CG iterations in one thread-block
-// cluster (16 CTAs where the GPU can co-schedule them, else 8; 1024 threads
+// cluster (16 CTAs where the GPU co-schedules them, else 8; 1024 threads
 // each) over a contiguous share of the env's rows, so envs iterate
-// independently: an env that converges frees its SMs at once, and no grid-wide
-// barrier ties envs together.  Per iteration:
-//   A  q = A p (BSR rows, one 8-lane group per row), p.q          | cluster barrier
+// independently: an env that converges frees its SMs at once, and no
+// grid-wide barrier ties envs together.  Per iteration, two cluster barriers:
+//   S  p = z + beta p over the CTA's halo (the columns its rows touch),
+//      staged in shared memory; the CTA's own rows also go to the next p
+//      buffer in HBM (two buffers alternate, so no CTA overwrites values
+//      another may still read)
+//   A  q = A p, one thread per 3x3 block into a shared buffer, then one
+//      thread per row adds its blocks in order; p.q                 | barrier
 //   B  alpha = r.z / p.q, dx += alpha p, r -= alpha q, z = M^-1 r;
-//      r.z, r.r                                                    | cluster barrier
-//   C  beta = r.z_new / r.z, stop test, p = z + beta p             | cluster barrier
-// Each CTA reduces its rows in a fixed tree and posts the result in its
-// shared memory; after the barrier every CTA adds the CS posts in rank order
-// through distributed shared memory, so all CTAs hold bit-identical scalars
-// and take the same branch.  Results do not depend on the other envs.
+//      r.z, r.r                                                     | barrier
+// Dot products accumulate in double-float pairs (FP64 issues at a small
+// fraction of the FP32 rate on this part) with fixed reduction trees; each
+// CTA posts its partials in shared memory and thread 0 of every CTA adds the
+// posts of all ranks in the same order through distributed shared memory, so
+// every CTA derives bit-identical alpha, beta and stop decisions.  When the
+// halo does not fit the shared-memory budget the SpMV forms p = z + beta p of
+// the neighbours from HBM instead.  Results do not depend on the other envs.
 constexpr int kPcgThreads = 1024;
-
-// Sum of `nval` posted values over the CS ranks of the cluster, in a fixed
-// shuffle tree on warp 0 (the same tree in every CTA), broadcast to the block.
-template <int NVAL>
-TC_D void cluster_gather(cg::cluster_group& cluster, int CS, double* s_post, double* s_bcast, double out[NVAL]) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const double* remote = lane < CS ? cluster.map_shared_rank(s_post, lane) : nullptr;
-#pragma unroll
-    for (int k = 0; k < NVAL; ++k) {
-      double v = lane < CS ? remote[k] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) s_bcast[k] = v;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < NVAL; ++k) out[k] = s_bcast[k];
-}
-
-// q = A p for two rows per lane group at once (independent loads in flight)
-template <class R>
-TC_D void bsr_rows2(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci, const R* __restrict__ val,
-                    int64_t nb, const R* p, R* q, int nv, int v0, int v1, int r1, double& pq) {
-  const int lane = threadIdx.x & (kLanes - 1);
-  const bool ok0 = v0 < r1, ok1 = v1 < r1;
-  R a0 = 0, a1 = 0, a2 = 0, b0 = 0, b1 = 0, b2 = 0;
-  const int k0s = ok0 ? __ldg(rp + v0) : 0, k0e = ok0 ? __ldg(rp + v0 + 1) : 0;
-  const int k1s = ok1 ? __ldg(rp + v1) : 0, k1e = ok1 ? __ldg(rp + v1 + 1) : 0;
-  int k0 = k0s + lane, k1 = k1s + lane;
-  while (k0 < k0e || k1 < k1e) {
-    if (k0 < k0e) {
-      const int j = __ldg(ci + k0);
-      const R p0 = p[j], p1 = p[nv + j], p2 = p[2 * nv + j];
-      const R* B = val + k0;
-      a0 += __ldg(B) * p0 + __ldg(B + nb) * p1 + __ldg(B + 2 * nb) * p2;
-      a1 += __ldg(B + 3 * nb) * p0 + __ldg(B + 4 * nb) * p1 + __ldg(B + 5 * nb) * p2;
-      a2 += __ldg(B + 6 * nb) * p0 + __ldg(B + 7 * nb) * p1 + __ldg(B + 8 * nb) * p2;
-      k0 += kLanes;
-    }
-    if (k1 < k1e) {
-      const int j = __ldg(ci + k1);
-      const R p0 = p[j], p1 = p[nv + j], p2 = p[2 * nv + j];
-      const R* B = val + k1;
-      b0 += __ldg(B) * p0 + __ldg(B + nb) * p1 + __ldg(B + 2 * nb) * p2;
-      b1 += __ldg(B + 3 * nb) * p0 + __ldg(B + 4 * nb) * p1 + __ldg(B + 5 * nb) * p2;
-      b2 += __ldg(B + 6 * nb) * p0 + __ldg(B + 7 * nb) * p1 + __ldg(B + 8 * nb) * p2;
-      k1 += kLanes;
-    }
-  }
-  a0 = group_sum(a0);
-  a1 = group_sum(a1);
-  a2 = group_sum(a2);
-  b0 = group_sum(b0);
-  b1 = group_sum(b1);
-  b2 = group_sum(b2);
-  if (lane == 0) {
-    if (ok0) {
-      q[v0] = a0;
-      q[nv + v0] = a1;
-      q[2 * nv + v0] = a2;
-      pq += (double)p[v0] * (double)a0 + (double)p[nv + v0] * (double)a1 + (double)p[2 * nv + v0] * (double)a2;
-    }
-    if (ok1) {
-      q[v1] = b0;
-      q[nv + v1] = b1;
-      q[2 * nv + v1] = b2;
-      pq += (double)p[v1] * (double)b0 + (double)p[nv + v1] * (double)b1 + (double)p[2 * nv + v1] * (double)b2;
-    }
-  }
-}
+constexpr int kPcgMaxChunks = 256;
 
 template <class R>
-__global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cluster(const BatchView<R> bv, PartLayout L, int max_iter) {
+__global__ void __launch_bounds__(kPcgThreads, 1)
+    k_pcg_cluster(const BatchView<R> bv, PartLayout L, int max_iter, int smem_bytes) {
+  using A = Acc<R>;
+  using AT = typename A::T;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  __shared__ AT s_red[3][32];
+  __shared__ AT s_post[3];
+  __shared__ R s_coef;
+  __shared__ int s_flag;
+  __shared__ int s_chunk[kPcgMaxChunks + 1];
+  __shared__ int s_nchunk;
+  __shared__ int s_lohi[2];
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int env = blockIdx.x / CS;
-  __shared__ double s_post[3];
-  __shared__ double s_bcast[3];
   const EnvView<R>& ev = bv.views[env];
   const int nv = ev.nv;
   const int64_t nb = ev.nnzb;
@@ -455,71 +401,202 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cluster(const BatchView<
   const int32_t* __restrict__ ci = ev.bsr_ci;
   const R* __restrict__ val = ev.bsr_val;
   const R* __restrict__ Minv = ev.Minv;
-  R* p = ev.p;
   R* q = ev.q;
   R* r = ev.r;
   R* z = ev.z;
   R* dx = ev.dx;
+  R* pbuf[2] = {ev.p, ev.p2};
   const int r0 = (int)((int64_t)nv * rank / CS), r1 = (int)((int64_t)nv * (rank + 1) / CS);
+  // halo of the CTA's rows
+  if (threadIdx.x == 0) {
+    s_lohi[0] = r0;
+    s_lohi[1] = r1 - 1;
+  }
+  __syncthreads();
+  {
+    int lo = r0, hi = r1 - 1;
+    for (int k = rp[r0] + (int)threadIdx.x; k < rp[r1]; k += kPcgThreads) {
+      const int j = ci[k];
+      lo = min(lo, j);
+      hi = max(hi, j);
+    }
+    if (r1 > r0) {
+      atomicMin(&s_lohi[0], lo);
+      atomicMax(&s_lohi[1], hi);
+    }
+  }
+  __syncthreads();
+  const int cmin = s_lohi[0];
+  const int H = r1 > r0 ? s_lohi[1] - cmin + 1 : 0;
+  const size_t stage_bytes = ((size_t)3 * H * sizeof(R) + 15) & ~(size_t)15;
+  const bool staged = stage_bytes <= (size_t)smem_bytes / 2;
+  R* sp = reinterpret_cast<R*>(s_dyn);
+  R* sy = reinterpret_cast<R*>(s_dyn + (staged ? stage_bytes : 0));
+  const int ycap = (int)((smem_bytes - (staged ? stage_bytes : 0)) / (3 * sizeof(R)));
+  // row chunks of at most ycap blocks (a longer row forms a chunk of its own)
+  if (threadIdx.x == 0) {
+    int n = 0, a = r0;
+    s_chunk[0] = r0;
+    while (a < r1 && n < kPcgMaxChunks) {
+      int b = a + 1;
+      while (b < r1 && rp[b + 1] - rp[a] <= ycap) ++b;
+      if (n == kPcgMaxChunks - 1) b = r1;  // last chunk takes the rest
+      s_chunk[++n] = b;
+      a = b;
+    }
+    s_nchunk = n;
+  }
+  __syncthreads();
+  const int nchunk = s_nchunk;
   const double* es = bv.part + L.env_s + kEnvScalars * env;
-  double rz = es[0], rr = es[1], pq = 0.0;
+  double rz = es[0], rr = es[1], pq = 0.0;  // thread 0's copies are the ones used
   const double tol2 = es[4];
   bool done = es[2] != 0.0;
+  R beta = R(0);
   int it = 0;
-  constexpr int kGroups = kPcgThreads / kLanes;
-  while (!done && it < max_iter) {
+  while (!done) {
+    const R* pc = pbuf[it & 1];
+    R* pn = pbuf[(it + 1) & 1];
+    // S. direction update over the halo (or the own rows)
+    const int s0 = staged ? cmin : r0, s1 = staged ? cmin + H : r1;
+    for (int v = s0 + (int)threadIdx.x; v < s1; v += kPcgThreads) {
+      const bool own = v >= r0 && v < r1;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const R x = z[i * nv + v] + beta * pc[i * nv + v];
+        if (staged) sp[i * H + (v - cmin)] = x;
+        if (own) pn[i * nv + v] = x;
+      }
+    }
+    __syncthreads();
     // A. q = A p
-    double loc = 0.0;
-    const int g = (int)threadIdx.x / kLanes;
-    for (int base = r0; base < r1; base += 2 * kGroups)  // block-uniform trip count
-      bsr_rows2<R>(rp, ci, val, nb, p, q, nv, base + g, base + g + kGroups, r1, loc);
-    loc = block_sum<kPcgThreads>(loc);
-    if (threadIdx.x == 0) s_post[0] = loc;
+    AT pq_loc = A::zero();
+    for (int c = 0; c < nchunk; ++c) {
+      const int ra = s_chunk[c], rb = s_chunk[c + 1];
+      const int ka = rp[ra], kb = rp[rb];
+      const bool fits = kb - ka <= ycap;
+      if (fits) {
+        for (int k = ka + (int)threadIdx.x; k < kb; k += kPcgThreads) {
+          const int j = ci[k];
+          R p0, p1, p2;
+          if (staged) {
+            const int l = j - cmin;
+            p0 = sp[l];
+            p1 = sp[H + l];
+            p2 = sp[2 * H + l];
+          } else {
+            p0 = z[j] + beta * pc[j];
+            p1 = z[nv + j] + beta * pc[nv + j];
+            p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
+          }
+          const R* B = val + k;
+          const int o = k - ka;
+          sy[o] = B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
+          sy[ycap + o] = B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
+          sy[2 * ycap + o] = B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
+        }
+        __syncthreads();
+      }
+      for (int v = ra + (int)threadIdx.x; v < rb; v += kPcgThreads) {
+        R a0 = 0, a1 = 0, a2 = 0;
+        const int k0 = rp[v], k1 = rp[v + 1];
+        if (fits) {
+          for (int k = k0 - ka; k < k1 - ka; ++k) {
+            a0 += sy[k];
+            a1 += sy[ycap + k];
+            a2 += sy[2 * ycap + k];
+          }
+        } else {
+          for (int k = k0; k < k1; ++k) {  // a row longer than the buffer
+            const int j = ci[k];
+            const R p0 = z[j] + beta * pc[j], p1 = z[nv + j] + beta * pc[nv + j];
+            const R p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
+            const R* B = val + k;
+            a0 += B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
+            a1 += B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
+            a2 += B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
+          }
+        }
+        q[v] = a0;
+        q[nv + v] = a1;
+        q[2 * nv + v] = a2;
+        R pv0, pv1, pv2;
+        if (staged) {
+          const int l = v - cmin;
+          pv0 = sp[l];
+          pv1 = sp[H + l];
+          pv2 = sp[2 * H + l];
+        } else {
+          pv0 = pn[v];
+          pv1 = pn[nv + v];
+          pv2 = pn[2 * nv + v];
+        }
+        pq_loc = A::add(pq_loc, A::add(A::add(A::prod(pv0, a0), A::prod(pv1, a1)), A::prod(pv2, a2)));
+      }
+      __syncthreads();
+    }
+    block_acc_sum<R, 1>(&pq_loc, s_red);
+    if (threadIdx.x == 0) s_post[0] = s_red[0][0];
     cluster.sync();
-    double g1[1];
-    cluster_gather<1>(cluster, CS, s_post, s_bcast, g1);
-    pq = g1[0];
-    const R alpha = (R)(pq > 0.0 ? rz / pq : 0.0);
+    if (threadIdx.x < 32) {
+      AT x = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[0] : A::zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+      if (threadIdx.x == 0) {
+        pq = A::to_double(x);
+        s_coef = (R)(pq > 0.0 ? rz / pq : 0.0);
+      }
+    }
+    __syncthreads();
+    const R alpha = s_coef;
     // B. vector update
-    double lrz = 0.0, lrr = 0.0;
+    AT acc[2] = {A::zero(), A::zero()};
     for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
       R rv[3], zv[3];
       for (int i = 0; i < 3; ++i) {
-        dx[i * nv + v] += alpha * p[i * nv + v];
+        const R pv = staged ? sp[i * H + (v - cmin)] : pn[i * nv + v];
+        dx[i * nv + v] += alpha * pv;
         rv[i] = r[i * nv + v] - alpha * q[i * nv + v];
         r[i * nv + v] = rv[i];
       }
-      const R m0 = __ldg(Minv + v), m1 = __ldg(Minv + nv + v), m2 = __ldg(Minv + 2 * nv + v);
-      const R m3 = __ldg(Minv + 3 * nv + v), m4 = __ldg(Minv + 4 * nv + v), m5 = __ldg(Minv + 5 * nv + v);
+      const R m0 = Minv[v], m1 = Minv[nv + v], m2 = Minv[2 * nv + v];
+      const R m3 = Minv[3 * nv + v], m4 = Minv[4 * nv + v], m5 = Minv[5 * nv + v];
       zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
       zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
       zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
       for (int i = 0; i < 3; ++i) {
         z[i * nv + v] = zv[i];
-        lrz += (double)rv[i] * (double)zv[i];
-        lrr += (double)rv[i] * (double)rv[i];
+        acc[0] = A::add(acc[0], A::prod(rv[i], zv[i]));
+        acc[1] = A::add(acc[1], A::prod(rv[i], rv[i]));
       }
     }
-    lrz = block_sum<kPcgThreads>(lrz);
-    lrr = block_sum<kPcgThreads>(lrr);
+    block_acc_sum<R, 2>(acc, s_red);
     if (threadIdx.x == 0) {
-      s_post[1] = lrz;
-      s_post[2] = lrr;
+      s_post[1] = s_red[0][0];
+      s_post[2] = s_red[1][0];
     }
     cluster.sync();
-    double g3[3];
-    cluster_gather<3>(cluster, CS, s_post, s_bcast, g3);
-    const double rz_new = g3[1];
-    rr = g3[2];
+    if (threadIdx.x < 32) {
+      AT x = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[1] : A::zero();
+      AT y = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[2] : A::zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        x = A::add(x, A::shfl_xor(x, o));
+        y = A::add(y, A::shfl_xor(y, o));
+      }
+      if (threadIdx.x == 0) {
+        const double rz_new = A::to_double(x);
+        rr = A::to_double(y);
+        s_coef = (R)(rz > 0.0 ? rz_new / rz : 0.0);
+        rz = rz_new;
+        s_flag = (rr <= tol2 || !(pq > 0.0) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    beta = s_coef;
+    done = s_flag != 0;
     ++it;
-    done = rr <= tol2 || !(pq > 0.0) || !isfinite(rr) || it >= max_iter;
-    const R beta = (R)(rz > 0.0 ? rz_new / rz : 0.0);
-    rz = rz_new;
-    if (done) break;
-    // C. direction update
-    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads)
-      for (int i = 0; i < 3; ++i) p[i * nv + v] = z[i * nv + v] + beta * p[i * nv + v];
-    cluster.sync();
+    __syncthreads();  // s_coef / s_flag are rewritten in the next iteration
   }
   if (rank == 0 && threadIdx.x == 0) {
     Scalars* sc = ev.sc;
@@ -535,16 +612,30 @@ __global__ void __launch_bounds__(kPcgThreads, 1) k_pcg_cluster(const BatchView<
   cluster.sync();
 }
 
-// Largest cluster the GPU co-schedules for the PCG kernel: 16 (non-portable)
-// if possible, else the portable 8.
-template <class R> static int pcg_cluster_size() {
-  static int cached = -1;
-  if (cached < 0) {
-    cached = 8;
+// Launch shape of the PCG kernel: the largest cluster the GPU co-schedules
+// (16, non-portable, if possible, else the portable 8) and the dynamic shared
+// memory of one CTA (the per-block opt-in limit less the static part).
+template <class R> struct PcgShape {
+  int cs = 8;
+  int smem = 0;
+};
+template <class R> static const PcgShape<R>& pcg_shape() {
+  static PcgShape<R> shape;
+  static bool init = false;
+  if (!init) {
+    init = true;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_pcg_cluster<R>);
+    shape.smem = std::max(0, optin - (int)fa.sharedSizeBytes - 1024);
+    cudaFuncSetAttribute(k_pcg_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, shape.smem);
     if (cudaFuncSetAttribute(k_pcg_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(16);
       cfg.blockDim = dim3(kPcgThreads);
+      cfg.dynamicSmemBytes = shape.smem;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
       attr[0].val.clusterDim.x = 16;
@@ -553,39 +644,34 @@ template <class R> static int pcg_cluster_size() {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<R>, &cfg) == cudaSuccess && n > 0) cached = 16;
-      const char* tr = std::getenv("TACAUCHY_TRACE");
-      if (tr && tr[0] && tr[0] != '0') {
-        int n8 = 0;
-        attr[0].val.clusterDim.x = 8;
-        cfg.gridDim = dim3(8);
-        cudaOccupancyMaxActiveClusters(&n8, k_pcg_cluster<R>, &cfg);
-        std::fprintf(stderr, "[tc] pcg cluster size %d (co-resident clusters: %d of 16 CTAs, %d of 8)\n", cached, n, n8);
-      }
+      if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<R>, &cfg) == cudaSuccess && n > 0) shape.cs = 16;
+      if (trace_on())
+        std::fprintf(stderr, "[tc] pcg cluster size %d, %d co-resident, %d B shared per CTA\n", shape.cs, n,
+                     shape.smem);
     }
     cudaGetLastError();
   }
-  return cached;
+  return shape;
 }
 
 template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s) {
   if (b.units[K_VERT] > 0) TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
   TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
-  const int CS = pcg_cluster_size<R>();
+  const PcgShape<R>& sh = pcg_shape<R>();
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(b.nenv * CS));
+  cfg.gridDim = dim3((unsigned)(b.nenv * sh.cs));
   cfg.blockDim = dim3(kPcgThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)sh.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)CS;
+  attr[0].val.clusterDim.x = (unsigned)sh.cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t err = cudaSuccess;
-  TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R>, b.bv, b.L, max_iter));
+  TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R>, b.bv, b.L, max_iter, sh.smem));
   return err == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
