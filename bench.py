@@ -387,19 +387,23 @@ def run_ours(args):
         return max_over_ranks(x, world, dev)
 
     budget = int(sum(i["device_bytes"] for i in infos) * 1.5)
-    srv = Server(hbm_budget_bytes=budget, max_slots=B)
+    srv = Server(hbm_budget_bytes=budget, max_slots=B, workers=args.workers)
     clients = _Clients(srv, served, pose_of, outs_s)
-    sstream = srv.stream()
+    wstreams = srv.streams()
     # ------------- served form (headline): closed loop, one request in flight per env
     clients.closed_loop(args.warmup)
     barrier()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev_end = [torch.cuda.Event(enable_timing=True) for _ in wstreams]
     with ClockSampler(local) as clk:
-        ev[0].record(sstream)
+        # the device is idle here: an event on one worker stream marks the start
+        ev[0].record(wstreams[0])
         lat = clients.closed_loop(args.steps)
-        ev[1].record(sstream)
-        ev[1].synchronize()
-    total_ms = slowest(ev[0].elapsed_time(ev[1]))
+        for e_, s_ in zip(ev_end, wstreams):
+            e_.record(s_)
+        for e_ in ev_end:
+            e_.synchronize()
+    total_ms = slowest(max(ev[0].elapsed_time(e_) for e_ in ev_end))
     clocks = clk.summary()
     value = job_rate(B * args.steps, world, total_ms / 1e3)
     sinfo = srv.info()
@@ -518,7 +522,7 @@ def run_ours(args):
                    "tets_per_env": infos[0]["nt"], "verts_per_env": infos[0]["nv"]},
         "latency_ms": {"p50": round(float(np.percentile(lat, 50)) / 1e3, 3),
                        "p99": round(float(np.percentile(lat, 99)) / 1e3, 3)},
-        "server": {"rounds": sinfo["rounds"], "peak_inflight": sinfo["peak_inflight"],
+        "server": {"workers": sinfo["workers"], "rounds": sinfo["rounds"], "peak_inflight": sinfo["peak_inflight"],
                    "hbm_budget_bytes": budget},
         "batched": batched_out,
         "plain": plain_out,
@@ -630,6 +634,7 @@ def main():
     ap.add_argument("--plain", type=int, default=1, help="also time the plain one-env-per-launch form")
     ap.add_argument("--sweep", type=int, default=1, help="also run the tc_stress_from_F size sweep")
     ap.add_argument("--poisson", type=int, default=1, help="also run open-loop Poisson arrivals")
+    ap.add_argument("--workers", type=int, default=0, help="server worker threads (0: one per env)")
     ap.add_argument("--poisson-seconds", type=float, default=4.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)

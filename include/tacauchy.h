@@ -257,17 +257,18 @@ tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const float* sigma
 /* ------------------------------------------------------------------------
  * Step server: continuous batching of step requests from many envs.
  *
- * Not in the paper, which steps one env per call.  A server owns one worker
- * thread and one CUDA stream on the device current at creation.  tc_submit
- * queues a request (env, target pose, optional output buffers) and returns a
- * ticket at once.  Before every scheduling round the worker admits queued
- * requests in FIFO order while fewer than max_slots are in flight and the
- * device footprint of their envs (the memory each env holds) stays within
- * hbm_budget_bytes; a request waits while an earlier request of the same env
- * is in flight, and a lone request is always admitted.  Each round advances
- * every admitted request by one phase group of the implicit step (Algorithm 2,
- * physics line) with one launch set per phase over all of them, so requests
- * that arrive while others are on the GPU join at the next round boundary.
+ * Not in the paper, which steps one env per call.  A server owns a pool of
+ * worker threads, each with its own CUDA stream, on the device current at
+ * creation.  tc_submit queues a request (env, target pose, optional output
+ * buffers) and returns a ticket at once.  Before every scheduling round a
+ * worker admits queued requests in FIFO order while it and the server have
+ * free slots and the device footprint of the envs in flight (the memory each
+ * env holds) stays within hbm_budget_bytes; a request waits while an earlier
+ * request of the same env is in flight, and a lone request is always
+ * admitted.  Each round advances every request of the worker by one phase
+ * group of the implicit step (Algorithm 2, physics line) with one launch set
+ * per phase over all of them, so requests that arrive while others are on the
+ * GPU join at the next round boundary, and workers overlap on the device.
  * A request's result equals tc_step on the same env and pose (bit for bit).
  * When it finishes, its stress (as tc_stress) and pressure map (as
  * tc_pressure_map) are written to the buffers given at submit, and the
@@ -289,14 +290,16 @@ typedef struct {
 
 typedef struct {
   int64_t submitted, completed, rounds;
-  int32_t queued, inflight, peak_inflight, max_slots;
+  int32_t queued, inflight, peak_inflight, max_slots, workers;
   size_t inflight_bytes, budget_bytes;
-  void* stream;       /* cudaStream_t all of the server's work runs on      */
 } tc_server_stats;
 
 /* hbm_budget_bytes > 0: bound on the summed footprint of the envs in flight;
- * max_slots > 0: bound on the number of requests in flight. */
-tc_status tc_server_create(size_t hbm_budget_bytes, int32_t max_slots, tc_server** out);
+ * max_slots > 0: bound on the number of requests in flight; workers: worker
+ * threads, each with its own CUDA stream and scheduler holding up to
+ * ceil(max_slots / workers) requests (<= 0: one worker per slot, so every
+ * request iterates independently; 1: a single batch over all requests). */
+tc_status tc_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t workers, tc_server** out);
 
 /* Queue one step of env toward *target (host pose; non-finite:
  * TC_ERR_NONFINITE).  sigma_out (device float 6 x nt), map_out (device float
@@ -318,6 +321,10 @@ tc_status tc_poll(tc_server* server, uint64_t ticket, int32_t* done, tc_result* 
 tc_status tc_wait(tc_server* server, uint64_t ticket, int64_t timeout_us, tc_result* result);
 
 tc_status tc_server_info(tc_server* server, tc_server_stats* out);
+
+/* *stream = the cudaStream_t of worker `worker` (0 <= worker < workers), for
+ * callers that order their own work or events after the server's. */
+tc_status tc_server_stream(tc_server* server, int32_t worker, void** stream);
 
 /* Cancel queued requests (their status becomes TC_ERR_ADMISSION), finish the
  * ones in flight, stop the worker and free the server. */

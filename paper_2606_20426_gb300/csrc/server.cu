@@ -1,23 +1,29 @@
 // Step server: continuous batching of tc_step requests from many envs.
 //
 // Callers submit (env, target pose, optional output buffers) from any thread
-// and get a ticket back at once.  One worker thread per server owns a
-// round-based step scheduler per precision: before every round it admits
-// queued requests while a slot and HBM budget are free (an env's footprint is
-// the device memory its arena holds), then runs one round -- every admitted
-// request advances by one phase group, with one launch set per phase over all
-// of them -- and finishes the requests that converged or failed: their
-// stress and pressure map are written to the caller's buffers and their
-// tickets complete.  A request that arrives while others are on the GPU joins
-// at the next round boundary, so envs of different sizes and at different
-// Newton iterations share every launch.  Env state (positions, velocities,
-// candidate lists, PCG vectors) stays resident in the env between requests.
+// and get a ticket back at once.  A pool of worker threads, each with its
+// own CUDA stream and one round-based step scheduler per precision, drains a
+// shared FIFO queue.  Before every round a worker admits queued requests
+// while it has a free slot, the server has a free slot and the HBM budget
+// allows (an env's footprint is the device memory its arena holds); then it
+// runs one round -- every request it holds advances by one phase group, with
+// one launch set per phase over all of them -- and finishes the requests that
+// converged or failed: their stress and pressure map are written to the
+// caller's buffers and their tickets complete.  A request that arrives while
+// others are on the GPU joins at the next round boundary of a worker with
+// room.  Workers run independently, so an env that needs many Newton or CG
+// iterations delays only the requests batched with it, and the streams of
+// different workers overlap on the device.  Env state (positions,
+// velocities, candidate lists, PCG vectors) stays resident in the env
+// between requests.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -45,16 +51,27 @@ struct Req {
   size_t bytes = 0;
 };
 
-struct Server {
-  int device = 0;
+struct Server;
+
+struct Worker {
+  Server* srv = nullptr;
+  int id = 0;
   cudaStream_t stream = nullptr;
-  size_t budget = 0;
-  int max_slots = 0;
   Arena arena;
   BatchExec<float> x32;
   BatchExec<double> x64;
   StepScheduler<float> s32;
   StepScheduler<double> s64;
+  int inflight = 0;  // guarded by the server mutex
+  std::thread th;
+  void run();
+};
+
+struct Server {
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 0;
+  int slots_per_worker = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<uint64_t> queue;
@@ -62,13 +79,13 @@ struct Server {
   int inflight = 0, peak_inflight = 0;
   size_t inflight_bytes = 0;
   int64_t submitted = 0, completed = 0;
+  uint64_t gen = 0;  // bumped whenever a request arrives or capacity frees up
   std::atomic<int64_t> rounds{0};
   uint64_t next_ticket = 1;
   bool stop = false;
-  std::thread worker;
+  std::vector<std::unique_ptr<Worker>> workers;
 
-  void run();
-  void admit_locked(std::vector<Req*>& out);
+  void admit_locked(Worker& w, std::vector<Req*>& out);
   void complete_locked(Req& r, tc_status st);
 };
 
@@ -79,10 +96,11 @@ void Server::complete_locked(Req& r, tc_status st) {
   completed++;
 }
 
-// FIFO admission: a request waits while an earlier request of its env is in
-// flight; the queue head waits for a free slot and for its footprint to fit
-// the budget, except that a lone request always runs.
-void Server::admit_locked(std::vector<Req*>& out) {
+// FIFO admission into worker w: a request waits while an earlier request of
+// its env is in flight; the queue head waits for a free slot (the worker's
+// and the server's) and for its footprint to fit the budget, except that a
+// lone request always runs.
+void Server::admit_locked(Worker& w, std::vector<Req*>& out) {
   for (auto it = queue.begin(); it != queue.end();) {
     Req& r = reqs.at(*it);
     if (r.env->in_flight.load()) {
@@ -96,12 +114,14 @@ void Server::admit_locked(std::vector<Req*>& out) {
       it = queue.erase(it);
       continue;
     }
+    if (w.inflight >= slots_per_worker) break;
     const bool fits = inflight < max_slots && inflight_bytes + r.bytes <= budget;
     if (!fits && inflight > 0) break;
     r.state = 1;
     r.t_admit = Clock::now();
     r.env->in_flight.store(1);
     inflight++;
+    w.inflight++;
     inflight_bytes += r.bytes;
     peak_inflight = std::max(peak_inflight, inflight);
     out.push_back(&r);
@@ -120,21 +140,26 @@ template <class R> static tc_status extract(Env& env, Req& r, cudaStream_t s) {
   return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
-void Server::run() {
-  cudaSetDevice(device);
+void Worker::run() {
+  Server& S = *srv;
+  cudaSetDevice(S.device);
   std::vector<Req*> live;
   std::vector<StepDone> fin;
   for (;;) {
     std::vector<Req*> admitted;
     {
-      std::unique_lock<std::mutex> lk(mu);
-      cv_work.wait(lk, [&] { return stop || !queue.empty() || inflight > 0; });
-      if (stop && inflight == 0) break;
-      if (!stop) admit_locked(admitted);
+      std::unique_lock<std::mutex> lk(S.mu);
+      for (;;) {
+        if (!S.stop) S.admit_locked(*this, admitted);
+        if (inflight > 0) break;
+        if (S.stop) return;
+        const uint64_t seen = S.gen;
+        S.cv_work.wait(lk, [&] { return S.stop || S.gen != seen; });
+      }
     }
-    cv_done.notify_all();  // admission may have completed requests that can never fit
+    S.cv_done.notify_all();  // admission may have completed requests that can never fit
     // the env's earlier work (creation, extraction by the caller) is ordered
-    // before its first launch on the server stream
+    // before its first launch on this worker's stream
     for (Req* r : admitted) {
       if (r->env->stream != stream) cudaStreamSynchronize(r->env->stream);
       if (r->env->precision == TC_FP64) s64.admit(r->env, r->target, r->ticket);
@@ -147,14 +172,14 @@ void Server::run() {
     if (!s32.empty()) st = s32.round(fin);
     if (st == TC_OK && !s64.empty()) st = s64.round(fin);
     if (trace_on())
-      std::fprintf(stderr, "[tc] server round %lld: %zu in flight, %zu admitted, %zu finished, %.3f ms\n",
-                   (long long)rounds.load(), live.size(), admitted.size(), fin.size(),
+      std::fprintf(stderr, "[tc] worker %d round: %zu in flight, %zu admitted, %zu finished, %.3f ms\n", id,
+                   live.size(), admitted.size(), fin.size(),
                    std::chrono::duration<double, std::milli>(Clock::now() - t_round).count());
     for (Req* r : live) r->rounds++;
-    rounds++;
+    S.rounds++;
     std::vector<std::pair<Req*, tc_status>> done;
     if (st != TC_OK) {
-      // a launch or copy failed: every request in flight ends with that status
+      // a launch or copy failed: every request this worker holds ends with that status
       s32.tasks.clear();
       s64.tasks.clear();
       for (Req* r : live) done.push_back({r, st});
@@ -174,15 +199,17 @@ void Server::run() {
     }
     if (done.empty()) continue;
     {
-      std::lock_guard<std::mutex> lk(mu);
+      std::lock_guard<std::mutex> lk(S.mu);
       for (auto& d : done) {
         Req& r = *d.first;
-        complete_locked(r, d.second);
+        S.complete_locked(r, d.second);
         r.env->in_flight.store(0);
         r.env->busy.fetch_sub(1);
+        S.inflight--;
         inflight--;
-        inflight_bytes -= r.bytes;
+        S.inflight_bytes -= r.bytes;
       }
+      S.gen++;
     }
     std::vector<Req*> keep;
     for (Req* r : live) {
@@ -191,7 +218,8 @@ void Server::run() {
       if (!fin_r) keep.push_back(r);
     }
     live.swap(keep);
-    cv_done.notify_all();
+    S.cv_done.notify_all();
+    S.cv_work.notify_all();  // freed capacity may let an idle worker admit
   }
 }
 
@@ -213,34 +241,79 @@ static void fill_result(const tc::Req& r, tc_result* out) {
   out->rounds = r.rounds;
 }
 
+static void stop_workers(tc::Server& s) {
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    s.stop = true;
+  }
+  s.cv_work.notify_all();
+  for (auto& w : s.workers)
+    if (w->th.joinable()) w->th.join();
+  s.cv_done.notify_all();
+  for (auto& w : s.workers) {
+    if (!w->stream) continue;
+    cudaStreamSynchronize(w->stream);
+    w->x32.release();
+    w->x64.release();
+    w->arena.release_all();
+    cudaStreamSynchronize(w->stream);
+    cudaStreamDestroy(w->stream);
+    w->stream = nullptr;
+  }
+}
+
 extern "C" {
 
-tc_status tc_server_create(size_t hbm_budget_bytes, int32_t max_slots, tc_server** out) {
+tc_status tc_server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t workers, tc_server** out) {
   if (!out || hbm_budget_bytes == 0 || max_slots <= 0) return TC_ERR_INVALID_ARG;
   *out = nullptr;
   tc_server* h = new (std::nothrow) tc_server;
   if (!h) return TC_ERR_OOM;
   tc::Server& s = h->impl;
-  if (cudaGetDevice(&s.device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaGetDevice(&s.device) != cudaSuccess) {
     delete h;
     return TC_ERR_CUDA;
   }
+  const int nw = workers > 0 ? std::min(workers, max_slots) : max_slots;
   s.budget = hbm_budget_bytes;
   s.max_slots = max_slots;
-  s.arena.stream = s.stream;
-  s.x32.arena = &s.arena;
-  s.x32.stream = s.stream;
-  s.x64.arena = &s.arena;
-  s.x64.stream = s.stream;
-  s.s32.exec = &s.x32;
-  s.s64.exec = &s.x64;
-  try {
-    s.worker = std::thread([&s] { s.run(); });
-  } catch (...) {
-    cudaStreamDestroy(s.stream);
+  s.slots_per_worker = (max_slots + nw - 1) / nw;
+  tc_status st = TC_OK;
+  for (int i = 0; i < nw && st == TC_OK; ++i) {
+    std::unique_ptr<tc::Worker> w(new (std::nothrow) tc::Worker());
+    if (!w) {
+      st = TC_ERR_OOM;
+      break;
+    }
+    w->srv = &s;
+    w->id = i;
+    if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      st = TC_ERR_CUDA;
+      break;
+    }
+    w->arena.stream = w->stream;
+    w->x32.arena = &w->arena;
+    w->x32.stream = w->stream;
+    w->x64.arena = &w->arena;
+    w->x64.stream = w->stream;
+    w->s32.exec = &w->x32;
+    w->s64.exec = &w->x64;
+    s.workers.push_back(std::move(w));
+  }
+  if (st == TC_OK) {
+    try {
+      for (auto& w : s.workers) {
+        tc::Worker* wp = w.get();
+        w->th = std::thread([wp] { wp->run(); });
+      }
+    } catch (...) {
+      st = TC_ERR_OOM;
+    }
+  }
+  if (st != TC_OK) {
+    stop_workers(s);
     delete h;
-    return TC_ERR_OOM;
+    return st;
   }
   *out = h;
   return TC_OK;
@@ -270,10 +343,11 @@ tc_status tc_submit(tc_server* h, tc_env* env, const tc_pose* target, float* sig
     r.t_submit = Clock::now();
     s.queue.push_back(t);
     s.submitted++;
+    s.gen++;
     e.busy.fetch_add(1);
     *ticket = t;
   }
-  s.cv_work.notify_one();
+  s.cv_work.notify_all();
   return TC_OK;
 }
 
@@ -315,10 +389,18 @@ tc_status tc_server_info(tc_server* h, tc_server_stats* out) {
   out->queued = (int32_t)s.queue.size();
   out->inflight = s.inflight;
   out->peak_inflight = s.peak_inflight;
+  out->max_slots = s.max_slots;
+  out->workers = (int32_t)s.workers.size();
   out->inflight_bytes = s.inflight_bytes;
   out->budget_bytes = s.budget;
-  out->max_slots = s.max_slots;
-  out->stream = (void*)s.stream;
+  return TC_OK;
+}
+
+tc_status tc_server_stream(tc_server* h, int32_t worker, void** stream) {
+  if (!h || !stream) return TC_ERR_INVALID_ARG;
+  tc::Server& s = h->impl;
+  if (worker < 0 || worker >= (int32_t)s.workers.size()) return TC_ERR_INVALID_ARG;
+  *stream = (void*)s.workers[worker]->stream;
   return TC_OK;
 }
 
@@ -327,7 +409,6 @@ void tc_server_destroy(tc_server* h) {
   tc::Server& s = h->impl;
   {
     std::lock_guard<std::mutex> lk(s.mu);
-    s.stop = true;
     // requests not yet admitted are cancelled; admitted ones run to the end
     for (uint64_t t : s.queue) {
       tc::Req& r = s.reqs.at(t);
@@ -336,15 +417,7 @@ void tc_server_destroy(tc_server* h) {
     }
     s.queue.clear();
   }
-  s.cv_work.notify_all();
-  if (s.worker.joinable()) s.worker.join();
-  s.cv_done.notify_all();
-  cudaStreamSynchronize(s.stream);
-  s.x32.release();
-  s.x64.release();
-  s.arena.release_all();
-  cudaStreamSynchronize(s.stream);
-  cudaStreamDestroy(s.stream);
+  stop_workers(s);
   delete h;
 }
 

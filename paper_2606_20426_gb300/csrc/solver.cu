@@ -619,11 +619,9 @@ template <class R> struct PcgShape {
   int cs = 8;
   int smem = 0;
 };
-template <class R> static const PcgShape<R>& pcg_shape() {
-  static PcgShape<R> shape;
-  static bool init = false;
-  if (!init) {
-    init = true;
+template <class R> static PcgShape<R> pcg_shape_query() {
+  PcgShape<R> shape;
+  {
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -651,6 +649,10 @@ template <class R> static const PcgShape<R>& pcg_shape() {
     }
     cudaGetLastError();
   }
+  return shape;
+}
+template <class R> static const PcgShape<R>& pcg_shape() {
+  static const PcgShape<R> shape = pcg_shape_query<R>();  // thread-safe one-time init
   return shape;
 }
 

@@ -25,7 +25,7 @@ EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_tract
            "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
            "tc_profile_read", "tc_pressure_map_noalloc", "tc_server_create", "tc_submit", "tc_poll", "tc_wait",
-           "tc_server_info", "tc_server_destroy"]
+           "tc_server_info", "tc_server_stream", "tc_server_destroy"]
 
 
 class TcError(RuntimeError):
@@ -81,8 +81,8 @@ class Result(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32),
-                ("max_slots", ctypes.c_int32), ("inflight_bytes", ctypes.c_size_t),
-                ("budget_bytes", ctypes.c_size_t), ("stream", ctypes.c_void_p)]
+                ("max_slots", ctypes.c_int32), ("workers", ctypes.c_int32), ("inflight_bytes", ctypes.c_size_t),
+                ("budget_bytes", ctypes.c_size_t)]
 
 
 class Info(ctypes.Structure):
@@ -127,7 +127,8 @@ def load():
         "tc_profile_read": [P, ctypes.POINTER(KernelTime), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
         "tc_pressure_map_noalloc": [P, ctypes.c_int32, P, ctypes.c_int32, P, P, P, ctypes.c_int32, P, P,
                                     ctypes.c_int32, P, P, ctypes.c_int32, P, P, P],
-        "tc_server_create": [ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(P)],
+        "tc_server_create": [ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(P)],
+        "tc_server_stream": [P, ctypes.c_int32, ctypes.POINTER(P)],
         "tc_submit": [P, P, ctypes.POINTER(Pose), P, P, P, ctypes.POINTER(ctypes.c_uint64)],
         "tc_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Result)],
         "tc_wait": [P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)],
@@ -344,10 +345,10 @@ class Server:
 
     TIMEOUT = 11
 
-    def __init__(self, hbm_budget_bytes, max_slots):
+    def __init__(self, hbm_budget_bytes, max_slots, workers=0):
         self.lib = load()
         h = ctypes.c_void_p()
-        _check(self.lib.tc_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
+        _check(self.lib.tc_server_create(int(hbm_budget_bytes), int(max_slots), int(workers), ctypes.byref(h)),
                "tc_server_create")
         self.h = h
 
@@ -380,10 +381,15 @@ class Server:
         _check(self.lib.tc_server_info(self.h, ctypes.byref(st)), "tc_server_info")
         return {k: getattr(st, k) for k, _ in ServerStats._fields_}
 
-    def stream(self):
-        """The server's CUDA stream as a torch stream (for events)."""
+    def streams(self):
+        """The workers' CUDA streams as torch streams (for events)."""
         torch = _torch()
-        return torch.cuda.ExternalStream(self.info()["stream"])
+        out = []
+        for w in range(self.info()["workers"]):
+            p = ctypes.c_void_p()
+            _check(self.lib.tc_server_stream(self.h, w, ctypes.byref(p)), "tc_server_stream")
+            out.append(torch.cuda.ExternalStream(p.value))
+        return out
 
     def close(self):
         if getattr(self, "h", None):

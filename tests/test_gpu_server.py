@@ -44,7 +44,7 @@ def test_server_mix_equals_alone():
     nsteps = 2
     envs = [Env(s, precision=p) for p, s in scenes]
     outs = [_outputs(torch, g) for g in envs]
-    srv = Server(hbm_budget_bytes=1 << 40, max_slots=64)
+    srv = Server(hbm_budget_bytes=1 << 40, max_slots=64, workers=2)
     delays = np.random.default_rng(3).exponential(0.01, size=len(envs))
     results = {}
 
