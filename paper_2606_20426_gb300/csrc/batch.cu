@@ -246,6 +246,14 @@ static Motion make_motion(const tc_pose& a, const tc_pose& b, int use_dir) {
   std::memcpy(m.ta, a.t, sizeof(m.ta));
   std::memcpy(m.Rb, b.R, sizeof(m.Rb));
   std::memcpy(m.tb, b.t, sizeof(m.tb));
+  for (int k = 0; k < 9; ++k) {
+    m.Raf[k] = (float)m.Ra[k];
+    m.Rbf[k] = (float)m.Rb[k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    m.taf[k] = (float)m.ta[k];
+    m.tbf[k] = (float)m.tb[k];
+  }
   m.use_dir = use_dir;
   return m;
 }
@@ -417,8 +425,14 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         fail(c, TC_ERR_NEWTON_MAXITER);
         continue;
       }
+      // forcing term of the inexact Newton solve: min(0.5, sqrt(|g| / |g0|)),
+      // floored in the mixed mode at 1e-2.  There the solve ends on the step
+      // test (|dx|_inf <= ptol), so a step known to 1 % is enough: the error
+      // left after the last step is ~1e-2 of a step already below ptol, while
+      // a tighter floor only multiplies the CG iterations of the final Newton
+      // iterations.
       double et = std::min(0.5, std::sqrt(gn / std::max(c.g0, 1e-300)));
-      et = std::max(et, e.precision == TC_FP64 ? 1e-10 : 1e-5);
+      et = std::max(et, e.precision == TC_FP64 ? 1e-10 : 1e-2);
       P.push_back(N[j]);
       eta.push_back(et * et * sc.gnorm2);  // squared PCG stopping tolerance (eta |g|)^2
     }

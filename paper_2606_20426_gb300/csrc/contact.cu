@@ -272,6 +272,8 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
   constexpr int CH = MODE == 1 ? 512 / (int)sizeof(R) : 128;  // pairs per chunk
   __shared__ int s_off[129];
   __shared__ R s_gh[MODE == 1 ? CH : 1][MODE == 1 ? NG + NH : 1];
+  __shared__ Origin s_o[128];
+  __shared__ Vec3<R> s_xg[128][NGP];
   const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
   const EnvView<R>& e = bv.views[lc.env];
   const R* __restrict__ u = trial ? e.ut : e.u;
@@ -281,6 +283,13 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
   const int32_t* cl = e.cand[GK];
   const int mine = base + (int)threadIdx.x;
   const int kept = mine < n ? min(e.cand_n[GK][mine], e.cand_cap) : 0;
+  if (kept > 0) {  // the primitive's FP64 geometry, once, for all its pairs
+    double bw[3][3];
+    Origin o;
+    contact_prim_points<R, GK>(e, u, mine, bw, &o);
+    s_o[threadIdx.x] = o;
+    for (int l = 0; l < NGP; ++l) s_xg[threadIdx.x][l] = rel<R>(bw[l], o.d);
+  }
   if (threadIdx.x == 0) s_off[0] = 0;
   s_off[threadIdx.x + 1] = kept;
   __syncthreads();
@@ -317,11 +326,9 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
       R* hp = MODE == 1 ? &s_gh[q - c0][NG] : nullptr;
       if (MODE == 1)
         for (int a = 0; a < NG + NH; ++a) s_gh[q - c0][a] = R(0);
-      double bw[3][3];
-      Origin o;
-      contact_prim_points<R, GK>(e, u, prim, bw, &o);
+      const Origin o = s_o[lo_i];
       Vec3<R> xg[NGP];
-      for (int l = 0; l < NGP; ++l) xg[l] = rel<R>(bw[l], o.d);
+      for (int l = 0; l < NGP; ++l) xg[l] = s_xg[lo_i][l];
       const int ip = cl[(int64_t)j * n + prim];
       Vec3<R> x[4];
       pair_points<R, R, GK>(e, xg, ip, o, x);
@@ -330,6 +337,9 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
       if (!(d2 < dhat2)) continue;
       const double eps_x = GK == GE ? 1e-3 * e.gel_elen2[prim] * e.ind_elen2[ip] : 0.0;
       if (sizeof(R) == 4 && d2 < (R)(1e-4 * e.dhat * e.dhat)) {  // FP64 island for very close pairs
+        double bw[3][3];
+        Origin od;
+        contact_prim_points<R, GK>(e, u, prim, bw, &od);
         Vec3<double> xgd[NGP];
         for (int l = 0; l < NGP; ++l) xgd[l] = rel<double>(bw[l], o.d);
         Vec3<double> xd[4];
@@ -448,17 +458,58 @@ TC_D void ccd_prim_geom(const EnvView<R>& e, const Motion& mo, const R* dir, int
   }
 }
 
-// One unit = 128 gel primitives.  Broad phase, one thread per primitive:
-// visit the grid cells of the swept box and write every indenter primitive
-// found to the candidate list (these lists feed the contact and energy passes
-// until the next CCD pass).  Narrow phase, all threads of the block over the
-// unit's flattened (primitive, candidate) pairs: additive CCD per pair, so
-// the few primitives near the indenter do not serialise the block.
+// FP32 swept box of one gel primitive in the body frame for the broad phase:
+// the FP64 geometry rounds to within ~1e-8 m of these coordinates, and the
+// box is grown by dhat plus a margin of 1e-6 of the coordinate magnitude
+// (>= 1e-7 m), so it contains the FP64 box.
+template <class R, int GK>
+TC_D void ccd_prim_box32(const EnvView<R>& e, const Motion& mo, const R* dir, int prim, float lo[3], float hi[3]) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = 3e38f;
+    hi[d] = -3e38f;
+  }
+  float mag = 0.f;
+  for (int l = 0; l < NGP; ++l) {
+    const int v = gel_vertex(e, GK, prim, l);
+    float w[3], wb[3];
+    for (int d = 0; d < 3; ++d) {
+      w[d] = e.X0f[d * e.nv + v] + (float)e.u[d * e.nv + v];
+      wb[d] = w[d] + (dir ? (float)dir[d * e.nv + v] : 0.f);
+    }
+    float b0[3], b1[3];
+    const float dx0 = w[0] - mo.taf[0], dy0 = w[1] - mo.taf[1], dz0 = w[2] - mo.taf[2];
+    const float dx1 = wb[0] - mo.tbf[0], dy1 = wb[1] - mo.tbf[1], dz1 = wb[2] - mo.tbf[2];
+    for (int d = 0; d < 3; ++d) {
+      b0[d] = mo.Raf[d] * dx0 + mo.Raf[3 + d] * dy0 + mo.Raf[6 + d] * dz0;
+      b1[d] = mo.Rbf[d] * dx1 + mo.Rbf[3 + d] * dy1 + mo.Rbf[6 + d] * dz1;
+      lo[d] = fminf(lo[d], fminf(b0[d], b1[d]));
+      hi[d] = fmaxf(hi[d], fmaxf(b0[d], b1[d]));
+      mag = fmaxf(mag, fmaxf(fabsf(w[d]) + fabsf(mo.taf[d]), fabsf(wb[d]) + fabsf(mo.tbf[d])));
+    }
+  }
+  const float grow = (float)e.dhat + fmaxf(1e-7f, 1e-6f * mag);
+  for (int d = 0; d < 3; ++d) {
+    lo[d] -= grow;
+    hi[d] += grow;
+  }
+}
+
+// One unit = 128 gel primitives.  Broad phase, one thread per primitive, in
+// FP32: visit the grid cells of the swept box and write every indenter
+// primitive found to the candidate list (these lists feed the contact and
+// energy passes until the next CCD pass).  The FP64 swept geometry is then
+// formed once per primitive that has candidates and kept in shared memory,
+// and the narrow phase runs all threads of the block over the unit's
+// flattened (primitive, candidate) pairs: additive CCD per pair, so the few
+// primitives near the indenter do not serialise the block.
 template <class R, int GK>
 __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
   __shared__ int s_off[129];
+  __shared__ Origin s_o[128];
+  __shared__ Vec3<R> s_xg[128][NGP], s_pg[128][NGP];
   const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
   const EnvView<R>& e = bv.views[lc.env];
   const Motion& mo = bv.motion[lc.env];
@@ -470,9 +521,8 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
   int kept = 0;
   if (base + (int)threadIdx.x < n) {
     const int prim = base + threadIdx.x;
-    double b0[3][3], b1[3][3];
     float lo[3], hi[3];
-    ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, lo, hi);
+    ccd_prim_box32<R, GK>(e, mo, dir, prim, lo, hi);
     int cnt = 0;
     grid_visit<R>(e, ik, lo, hi, [&](int ip) {
       if (cnt < e.cand_cap) cl[(int64_t)cnt * n + prim] = ip;
@@ -481,6 +531,17 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
     e.cand_n[GK][prim] = cnt;
     if (cnt > e.cand_cap) atomicMax(&e.sc->overflow, cnt);
     kept = cnt < e.cand_cap ? cnt : e.cand_cap;
+    if (kept > 0) {
+      double b0[3][3], b1[3][3];
+      float blo[3], bhi[3];
+      ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, blo, bhi);
+      const Origin o = make_origin(b0[0]);
+      s_o[threadIdx.x] = o;
+      for (int l = 0; l < NGP; ++l) {
+        s_xg[threadIdx.x][l] = rel<R>(b0[l], o.d);
+        s_pg[threadIdx.x][l] = rel<R>(b1[l], b0[l]);
+      }
+    }
   }
   // exclusive prefix of the kept counts (128 threads, fixed order)
   if (threadIdx.x == 0) s_off[0] = 0;
@@ -500,14 +561,11 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
       else hi_i = mid - 1;
     }
     const int prim = base + lo_i, j = q - s_off[lo_i];
-    double b0[3][3], b1[3][3];
-    float blo[3], bhi[3];
-    ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, blo, bhi);
-    const Origin o = make_origin(b0[0]);
+    const Origin o = s_o[lo_i];
     Vec3<R> xg[NGP], pg[NGP];
     for (int l = 0; l < NGP; ++l) {
-      xg[l] = rel<R>(b0[l], o.d);
-      pg[l] = rel<R>(b1[l], b0[l]);
+      xg[l] = s_xg[lo_i][l];
+      pg[l] = s_pg[lo_i][l];
     }
     const int ip = cl[(int64_t)j * n + prim];
     Vec3<R> x0[4], p[4];

@@ -53,6 +53,7 @@ template <class R> struct EnvView {
   // topology
   const int4* tets;
   const double* X0;           // rest positions, SoA x|y|z, each nv
+  const float* X0f;           // X0 rounded to FP32 (broad-phase boxes only)
   const uint8_t* fixed;       // 1 = fixed vertex
   const int32_t* vt_off;      // vertex -> (tet*4+corner), CSR
   const int32_t* vt_idx;
@@ -140,6 +141,7 @@ TC_HD int unit_items(int kind) {
 // use_dir) seen from pose (Ra, ta) at the start and (Rb, tb) at the end.
 struct Motion {
   double Ra[9], ta[3], Rb[9], tb[3];
+  float Raf[9], taf[3], Rbf[9], tbf[3];  // FP32 copies for the broad phase
   int use_dir;
 };
 
@@ -193,6 +195,7 @@ struct Env {
   // device integer topology
   int4* tets = nullptr;
   double* X0 = nullptr;
+  float* X0f = nullptr;
   uint8_t* fixed = nullptr;
   int32_t *vt_off = nullptr, *vt_idx = nullptr;
   int32_t *cverts = nullptr, *cedges = nullptr, *cfaces = nullptr, *cparent = nullptr, *vslot = nullptr;
@@ -251,7 +254,7 @@ template <class R> EnvView<R> Env::view() const {
   e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
   e.dhat = dhat; e.kappa = kappa;
-  e.tets = tets; e.X0 = X0; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
+  e.tets = tets; e.X0 = X0; e.X0f = X0f; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
   e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.eslot = (R*)eslot; e.kblk = (R*)kblk;
   e.nnzb = nnzb; e.bsr_rp = bsr_rp; e.bsr_ci = bsr_ci; e.bsr_diag = bsr_diag; e.bsr_val = (R*)bsr_val;
   e.be_off = be_off; e.be_idx = be_idx; e.bc_off = bc_off; e.bc_idx = bc_idx;

@@ -572,11 +572,14 @@ tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed_ids, i
   std::vector<double> Xs(3 * (size_t)nv);
   for (int v = 0; v < nv; ++v)
     for (int d = 0; d < 3; ++d) Xs[(size_t)d * nv + v] = mesh->X[3 * (size_t)v + d];
+  std::vector<float> Xf(Xs.begin(), Xs.end());  // FP32 copy for conservative broad-phase boxes
   env.X0 = a.alloc<double>(3 * (int64_t)nv);
+  env.X0f = a.alloc<float>(3 * (int64_t)nv);
   env.tets = a.alloc<int4>(nt);
   env.fixed = a.alloc<uint8_t>(nv);
-  if (!env.X0 || !env.tets || !env.fixed) return TC_ERR_OOM;
+  if (!env.X0 || !env.X0f || !env.tets || !env.fixed) return TC_ERR_OOM;
   TC_TRY(cudaMemcpyAsync(env.X0, Xs.data(), sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s));
+  TC_TRY(cudaMemcpyAsync(env.X0f, Xf.data(), sizeof(float) * 3 * nv, cudaMemcpyHostToDevice, s));
   TC_TRY(cudaMemcpyAsync(env.tets, mesh->tets, sizeof(int4) * nt, cudaMemcpyHostToDevice, s));
   TC_TRY(cudaMemsetAsync(env.fixed, 0, nv, s));
   int32_t* dfix = a.alloc<int32_t>(std::max(nfixed, 1));

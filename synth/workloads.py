@@ -18,6 +18,9 @@ and the CUDA binding consume them.  Recipes (sizes in metres):
                      grid (0.075 mm pixels).
 * ``small_env``    - a few hundred tets, for tests that run the oracle's full
                      Newton solve in seconds.
+* ``sensor_env``   - the same kind of indentation on a pad, DIGIT-like dome or
+                     9DTact-like block of a given size; ``mixed_envs`` draws an
+                     uneven batch of the three families.
 """
 import math
 import numpy as np
@@ -126,6 +129,73 @@ def gelsight_env(seed, steps=20, target_tets=60000, dhat=0.05e-3, dt=1.0 / 60.0,
     return dict(name=f"gelsight-{kind}-seed{seed}", X=X, tets=T, material=dict(MATERIAL),
                 fixed=_fixed_bottom(X), ind_V=V, ind_F=F, start_pose=start, poses=poses,
                 grid=grid, opts=_opts(dhat, dt, precision), depth=depth, kind=kind)
+
+
+def _grid_over(Lx, Ly, pixel):
+    """Pixel grid over the x-y extent: rows along x, columns along y."""
+    H, W = max(1, int(round(Lx / pixel))), max(1, int(round(Ly / pixel)))
+    return dict(axis_u=1, axis_v=0, origin=(0.0, 0.0), pixel=(Ly / W, Lx / H), H=H, W=W)
+
+
+def sensor_mesh(sensor, target_tets):
+    """Mesh of a sensor family scaled to about target_tets tets:
+    'pad'   graded 18x24x4 mm pad (GelSight-Mini-like),
+    'dome'  20x16 mm base with a 1.5 mm slab and a spherical cap of radius
+            30 mm and height 3 mm clipped to the base (DIGIT-like),
+    'block' 30x30x5 mm block (9DTact-like), uniform hexes split 6 ways."""
+    if sensor == "pad":
+        return meshes.graded_pad(target_tets=target_tets), (18e-3, 24e-3)
+    if sensor == "dome":
+        nz = 6
+        s = math.sqrt(target_tets / (6.0 * nz * 20 * 16))
+        nx, ny = max(4, int(round(20 * s))), max(4, int(round(16 * s)))
+        return meshes.dome(nx=nx, ny=ny, nz=nz), (20e-3, 16e-3)
+    if sensor == "block":
+        nz = max(2, int(round((target_tets / 6.0 / 36.0) ** (1.0 / 3.0))))
+        n = max(4, int(round(math.sqrt(target_tets / (6.0 * nz)))))
+        return meshes.block(nx=n, ny=n, nz=nz), (30e-3, 30e-3)
+    raise ValueError(sensor)
+
+
+def sensor_env(seed, sensor="pad", target_tets=20000, steps=20, dhat=0.05e-3, dt=1.0 / 60.0,
+               precision="fp32", pixel=0.1e-3):
+    """A GelSight-style indentation (seeded sphere / cylinder / filleted box,
+    depth U[0.2, 1.0] mm, slip U[0, 0.5] mm over `steps` dynamic steps) on a
+    pad, dome or block sensor of about target_tets tets; the indenter starts
+    dhat above the highest gel point near the sensor centre."""
+    rng = SplitMix64(seed)
+    (X, T), (Lx, Ly) = sensor_mesh(sensor, target_tets)
+    kind, V, F, yaw = gelsight_indenter(rng)
+    cx = Lx / 2 + rng.uniform(-1e-3, 1e-3)
+    cy = Ly / 2 + rng.uniform(-1e-3, 1e-3)
+    depth = rng.uniform(0.2e-3, 1.0e-3)
+    slip = rng.uniform(0.0, 0.5e-3)
+    phi = rng.uniform(0.0, 2 * math.pi)
+    top = float(X[:, 2].max())
+    z0 = top + dhat - indenters.lowest_z(V)
+    start = _pose(cx, cy, z0, yaw)
+    poses = []
+    for k in range(1, steps + 1):
+        f = k / steps
+        poses.append(_pose(cx + f * slip * math.cos(phi), cy + f * slip * math.sin(phi),
+                           z0 - f * (dhat + depth), yaw))
+    return dict(name=f"{sensor}-{kind}-seed{seed}", X=X, tets=T, material=dict(MATERIAL),
+                fixed=_fixed_bottom(X), ind_V=V, ind_F=F, start_pose=start, poses=poses,
+                grid=_grid_over(Lx, Ly, pixel), opts=_opts(dhat, dt, precision), depth=depth, kind=kind,
+                sensor=sensor)
+
+
+def mixed_envs(seed, n_per_family=20, pads=(5000, 60000), domes=(8000, 40000), blocks=(10000, 80000),
+               steps=20, precision="fp32"):
+    """Uneven batch of pads, domes and blocks, sizes log-uniform in the given
+    tet ranges, each with its own seeded indenter."""
+    rng = SplitMix64(seed)
+    out = []
+    for fam, (lo, hi) in (("pad", pads), ("dome", domes), ("block", blocks)):
+        for i in range(n_per_family):
+            nt = int(math.exp(rng.uniform(math.log(lo), math.log(hi))))
+            out.append(sensor_env(seed * 1000 + len(out), fam, nt, steps=steps, precision=precision))
+    return out
 
 
 def splitmix64_array(seed, n):
