@@ -325,7 +325,7 @@ def run_ours(args):
     import numpy as np
     import torch
     import torch.distributed as dist
-    from paper_2606_20426_gb300 import Env, Server, step_batch
+    from paper_2606_20426_gb300 import Env, Server, autotune_pcg, step_batch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -392,6 +392,7 @@ def run_ours(args):
     wstreams = srv.streams()
     # ------------- served form (headline): closed loop, one request in flight per env
     clients.closed_loop(args.warmup)
+    tuned = autotune_pcg(served) if args.autotune else None
     barrier()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     ev_end = [torch.cuda.Event(enable_timing=True) for _ in wstreams]
@@ -524,6 +525,7 @@ def run_ours(args):
                        "p99": round(float(np.percentile(lat, 99)) / 1e3, 3)},
         "server": {"workers": sinfo["workers"], "rounds": sinfo["rounds"], "peak_inflight": sinfo["peak_inflight"],
                    "hbm_budget_bytes": budget},
+        "pcg_autotune": tuned,
         "batched": batched_out,
         "plain": plain_out,
         "poisson": poisson or None,
@@ -625,6 +627,34 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_pcg_probe(args):
+    """Profiling probe: B envs take `pcg_probe` batched steps, then one PCG
+    solve per launch shape runs through the autotuner.  Prints how many PCG
+    launches preceded the autotuner's first one (for ncu -s) and the CG
+    iterations of each shape's solves, so that a capture of that first launch
+    can be scaled per CG iteration of one env."""
+    import torch
+    from paper_2606_20426_gb300 import Env, autotune_pcg, step_batch
+    cfgs = make_envs(args.envs, 0)
+    envs = [Env(c, precision="fp32") for c in cfgs]
+    for e in envs:
+        e.profile(True)
+    for k in range(args.pcg_probe):
+        codes = step_batch(envs, [c["bench_poses"][k] for c in cfgs])
+        if any(codes):
+            raise RuntimeError(f"tc_step_batch statuses {codes}")
+    torch.cuda.synchronize()
+    launches = envs[0].kernel_times().get("k_pcg_cluster", (0.0, 0))[1]
+    for e in envs:
+        e.profile(False)
+    tune = autotune_pcg(envs)
+    info = envs[0].info
+    print(json.dumps({"pcg_launches_before": int(launches), "envs": args.envs, "steps": args.pcg_probe,
+                      "bytes_per_env_iter": pcg_iteration_bytes(info), "autotune": tune}), flush=True)
+    for e in envs:
+        e.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -635,14 +665,19 @@ def main():
     ap.add_argument("--sweep", type=int, default=1, help="also run the tc_stress_from_F size sweep")
     ap.add_argument("--poisson", type=int, default=1, help="also run open-loop Poisson arrivals")
     ap.add_argument("--workers", type=int, default=0, help="server worker threads (0: one per env)")
+    ap.add_argument("--autotune", type=int, default=1, help="pick the PCG launch shape on the bench envs first")
     ap.add_argument("--poisson-seconds", type=float, default=4.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-newton-per-step", type=float, default=40.0,
                     help="Newton iterations per env-step used to scale the reference arm's sample")
+    ap.add_argument("--pcg-probe", type=int, default=0,
+                    help="profiling probe: this many batched steps, then the PCG autotuner (see run_pcg_probe)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.pcg_probe:
+        run_pcg_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -161,6 +161,31 @@ tc_status tc_step(tc_env* env, const tc_pose* target);
 tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets,
                         tc_status* statuses);
 
+/* Launch shape of the PCG (one thread-block cluster per env):
+ * cluster_ctas in {8, 16} CTAs per env, threads in {512, 1024} per CTA.
+ * Process-wide for the given precision (TC_FP64 or TC_FP32_MIXED), so an
+ * env's result does not depend on the batch it runs in; changing it changes
+ * the rounding of later steps.  TC_ERR_CAPACITY if the GPU cannot co-schedule
+ * such a cluster.  Not in the paper. */
+tc_status tc_pcg_shape(int32_t precision, int32_t cluster_ctas, int32_t threads);
+
+typedef struct {
+  int32_t cluster_ctas, threads;  /* the shape tried                         */
+  int32_t coresident;             /* clusters of it the GPU holds at once    */
+  double us_per_env_iter;         /* device time per CG iteration of one env  */
+  int64_t env_iters;              /* CG iterations timed (all envs)           */
+} tc_pcg_tune;
+
+/* Autotuner: assemble the Newton systems of the n envs at their current
+ * state (positions are not changed), time their PCG solves under every
+ * co-schedulable shape, and select the shape with the least device time per
+ * CG iteration of one env.  results (host, up to max_results entries, may be
+ * NULL when max_results is 0) receives one entry per shape tried and
+ * *n_results their count.  The envs must share precision and device and have
+ * no server request pending.  Not in the paper. */
+tc_status tc_autotune_pcg(tc_env** envs, int32_t n, tc_pcg_tune* results, int32_t max_results,
+                          int32_t* n_results);
+
 /* Cauchy stress per tet (Eq. 4 with the rest-stable reading):
  * sigma_out device float 6 x nt, component-major (component k of tet e at
  * k * nt + e), components in the order (xx, yy, zz, xy, yz, zx). */
@@ -179,6 +204,13 @@ tc_status tc_traction(tc_env* env, float* t, float* p, float* t_tau);
  * create time.  out: device float H x W; mask: device uint8 H x W (1 = pixel
  * covered by a contact face) or NULL. */
 tc_status tc_pressure_map(tc_env* env, float* out, uint8_t* mask);
+
+/* Incremental potential at the current positions and indenter pose
+ * (Algorithm 2's minimisation objective: elastic energy + kappa * barrier
+ * sum, plus the inertia term in the dynamic case) and its gradient w.r.t. the
+ * gel positions with fixed vertices zeroed.  energy: host double or NULL;
+ * grad: host double nv x 3 (row-major) or NULL; not both NULL. */
+tc_status tc_energy_gradient(tc_env* env, double* energy, double* grad);
 
 /* Total contact force on the gel, sum_k f_k with f_k = -kappa dB/dx_k
  * (Algorithm 2: f_k = -g_k / dt^2).  out: host double[3]. */

@@ -8,4 +8,5 @@ The compute lives in libtacauchy.so (CUDA, C ABI in include/tacauchy.h);
 ``python -m paper_2606_20426_gb300.build``.
 """
 from . import tacauchy  # noqa: F401
-from .tacauchy import Env, Server, TcError, load, step_batch, stress_from_F  # noqa: F401
+from .tacauchy import (Env, Server, TcError, autotune_pcg, load, pcg_shape, step_batch,  # noqa: F401
+                       stress_from_F)

@@ -13,6 +13,7 @@
 
 #include "batch.cuh"
 #include "env.cuh"
+#include "solver.cuh"
 
 namespace tc {
 
@@ -310,6 +311,41 @@ tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets, tc_sta
   return TC_OK;
 }
 
+tc_status tc_pcg_shape(int32_t precision, int32_t cluster_ctas, int32_t threads) {
+  if (precision == TC_FP64) return tc::set_pcg_shape<double>(cluster_ctas, threads);
+  if (precision == TC_FP32_MIXED) return tc::set_pcg_shape<float>(cluster_ctas, threads);
+  return TC_ERR_INVALID_ARG;
+}
+
+tc_status tc_autotune_pcg(tc_env** envs, int32_t n, tc_pcg_tune* results, int32_t max_results, int32_t* n_results) {
+  if (n <= 0 || !envs || (max_results > 0 && !results)) return TC_ERR_INVALID_ARG;
+  std::vector<Env*> set;
+  for (int i = 0; i < n; ++i) {
+    if (!envs[i] || envs[i]->impl.busy.load() || envs[i]->impl.precision != envs[0]->impl.precision ||
+        envs[i]->impl.device != envs[0]->impl.device)
+      return TC_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (envs[j] == envs[i]) return TC_ERR_INVALID_ARG;
+    set.push_back(&envs[i]->impl);
+  }
+  Env& lead = *set[0];
+  for (Env* e : set)
+    if (e->stream != lead.stream) cudaStreamSynchronize(e->stream);
+  tc::ProfGuard pg(lead);
+  std::vector<tc::PcgTune> out;
+  const tc_status st = lead.precision == TC_FP64 ? tc::autotune_pcg<double>(tc::exec_of<double>(lead), set, out)
+                                                 : tc::autotune_pcg<float>(tc::exec_of<float>(lead), set, out);
+  if (n_results) *n_results = (int32_t)out.size();
+  for (int k = 0; k < (int)out.size() && k < max_results; ++k) {
+    results[k].cluster_ctas = out[k].cs;
+    results[k].threads = out[k].threads;
+    results[k].coresident = out[k].coresident;
+    results[k].us_per_env_iter = out[k].us_per_env_iter;
+    results[k].env_iters = out[k].env_iters;
+  }
+  return st;
+}
+
 tc_status tc_stress(tc_env* h, float* sigma_out) {
   if (!h || !sigma_out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
@@ -346,6 +382,18 @@ tc_status tc_contact_force(tc_env* h, double* out) {
   Env& env = h->impl;
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::contact_force<double>(env, out) : tc::contact_force<float>(env, out);
+}
+
+tc_status tc_energy_gradient(tc_env* h, double* energy, double* grad) {
+  if (!h || (!energy && !grad)) return TC_ERR_INVALID_ARG;
+  Env& env = h->impl;
+  if (env.busy.load()) return TC_ERR_INVALID_ARG;
+  tc::ProfGuard pg(env);
+  const tc_status st = env.precision == TC_FP64
+                           ? tc::energy_gradient_at_state<double>(tc::exec_of<double>(env), env, energy, grad)
+                           : tc::energy_gradient_at_state<float>(tc::exec_of<float>(env), env, energy, grad);
+  if (env.prof) env.prof->collect();
+  return st;
 }
 
 tc_status tc_surface_faces(tc_env* h, int32_t* faces, int32_t* parent) {

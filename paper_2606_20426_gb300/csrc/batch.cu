@@ -587,6 +587,28 @@ template <class R> tc_status energy_at_state(BatchExec<R>& X, Env& env, Scalars*
   return TC_OK;
 }
 
+template <class R> tc_status energy_gradient_at_state(BatchExec<R>& X, Env& env, double* E, double* grad) {
+  std::vector<Env*> one{&env};
+  tc_status st = ensure_candidates<R>(X, one);
+  if (st != TC_OK) return st;
+  if ((st = X.build(one, nullptr, nullptr)) != TC_OK) return st;
+  b_elem<R>(X.host, true, false, X.stream);
+  b_contact<R>(X.host, true, false, X.stream);
+  b_assemble<R>(X.host, X.stream);
+  if ((st = X.read()) != TC_OK) return st;
+  if (X.h_sc[0].status & ST_NONFINITE) return TC_ERR_NONFINITE;
+  if (E) *E = X.h_sc[0].energy;
+  if (grad) {
+    const int nv = env.nv;
+    std::vector<R> g(3 * (size_t)nv);
+    TC_CHECK(cudaMemcpyAsync(g.data(), env.g, sizeof(R) * 3 * nv, cudaMemcpyDeviceToHost, X.stream));
+    TC_CHECK(cudaStreamSynchronize(X.stream));
+    for (int v = 0; v < nv; ++v)
+      for (int d = 0; d < 3; ++d) grad[3 * (size_t)v + d] = (double)g[(size_t)d * nv + v];
+  }
+  return TC_OK;
+}
+
 template <class R> tc_status contact_force_at_state(BatchExec<R>& X, Env& env, double* f) {
   std::vector<Env*> one{&env};
   tc_status st = ensure_candidates<R>(X, one);
@@ -599,6 +621,64 @@ template <class R> tc_status contact_force_at_state(BatchExec<R>& X, Env& env, d
   return TC_OK;
 }
 
+template <class R> tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, std::vector<PcgTune>& out) {
+  out.clear();
+  if (envs.empty()) return TC_OK;
+  tc_status st = ensure_candidates<R>(X, envs);
+  if (st != TC_OK) return st;
+  // the current Newton systems: element + contact + assembly
+  if ((st = X.build(envs, nullptr, nullptr)) != TC_OK) return st;
+  b_elem<R>(X.host, true, false, X.stream);
+  b_contact<R>(X.host, true, false, X.stream);
+  b_assemble<R>(X.host, X.stream);
+  if ((st = X.read()) != TC_OK) return st;
+  std::vector<double> tol2(envs.size());
+  int pcg_max = 0;
+  for (size_t i = 0; i < envs.size(); ++i) {
+    tol2[i] = 1e-6 * X.h_sc[i].gnorm2;  // a relative residual of 1e-3
+    pcg_max = std::max(pcg_max, envs[i]->pcg_max);
+  }
+  const PcgShape keep = pcg_shape<R>();
+  const int shapes[4][2] = {{16, 1024}, {8, 1024}, {16, 512}, {8, 512}};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TC_ERR_CUDA;
+  double best = 1e300;
+  int best_k = -1;
+  for (int k = 0; k < 4; ++k) {
+    if (set_pcg_shape<R>(shapes[k][0], shapes[k][1]) != TC_OK) continue;
+    const PcgShape sh = pcg_shape<R>();
+    double us = 1e300;
+    long long iters = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      if ((st = X.build(envs, tol2.data(), nullptr)) != TC_OK) break;
+      cudaEventRecord(e0, X.stream);
+      if ((st = b_pcg<R>(X.host, pcg_max, X.stream)) != TC_OK) break;
+      cudaEventRecord(e1, X.stream);
+      if ((st = X.read()) != TC_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      long long it = 0;
+      for (size_t i = 0; i < envs.size(); ++i) it += X.h_sc[i].pcg_iters;
+      if (it > 0 && rep > 0) us = std::min(us, 1e3 * ms / (double)it);
+      iters = it;
+    }
+    if (st != TC_OK) break;
+    out.push_back({sh.cs, sh.threads, sh.coresident, us, iters});
+    if (us < best) {
+      best = us;
+      best_k = k;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TC_OK) {
+    set_pcg_shape<R>(keep.cs, keep.threads);
+    return st;
+  }
+  if (best_k >= 0) return set_pcg_shape<R>(shapes[best_k][0], shapes[best_k][1]);
+  return set_pcg_shape<R>(keep.cs, keep.threads);
+}
+
 #define TC_INST(R)                                                                                              \
   template struct BatchExec<R>;                                                                                 \
   template tc_status ensure_candidates<R>(BatchExec<R>&, const std::vector<Env*>&);                             \
@@ -606,7 +686,9 @@ template <class R> tc_status contact_force_at_state(BatchExec<R>& X, Env& env, d
   template tc_status step_batch<R>(BatchExec<R>&, const std::vector<Env*>&, const std::vector<tc_pose>&,        \
                                    std::vector<tc_status>&);                                                    \
   template tc_status energy_at_state<R>(BatchExec<R>&, Env&, Scalars*);                                         \
-  template tc_status contact_force_at_state<R>(BatchExec<R>&, Env&, double*);
+  template tc_status contact_force_at_state<R>(BatchExec<R>&, Env&, double*);                                \
+  template tc_status energy_gradient_at_state<R>(BatchExec<R>&, Env&, double*, double*);                     \
+  template tc_status autotune_pcg<R>(BatchExec<R>&, const std::vector<Env*>&, std::vector<PcgTune>&);
 TC_INST(float)
 TC_INST(double)
 #undef TC_INST

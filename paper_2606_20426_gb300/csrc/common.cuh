@@ -201,67 +201,6 @@ inline unsigned grid_for(int64_t n, int nt = kBlock) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-// ------------------------------------------------------- symmetric eigen (Jacobi)
-
-// Cyclic Jacobi on a symmetric N x N matrix A (row-major, overwritten by its
-// eigenvalues on the diagonal); Q receives the eigenvectors as columns.
-template <class R, int N> TC_D void jacobi_eig(R* A, R* Q, int sweeps) {
-  for (int i = 0; i < N; ++i)
-    for (int j = 0; j < N; ++j) Q[i * N + j] = (i == j) ? R(1) : R(0);
-  for (int s = 0; s < sweeps; ++s) {
-    R off = 0, diag = 0;
-    for (int i = 0; i < N; ++i) {
-      diag += A[i * N + i] * A[i * N + i];
-      for (int j = i + 1; j < N; ++j) off += A[i * N + j] * A[i * N + j];
-    }
-    if (!(off > R(1e-30) * diag) || off == R(0)) break;
-    for (int p = 0; p < N - 1; ++p) {
-      for (int q = p + 1; q < N; ++q) {
-        const R apq = A[p * N + q];
-        if (apq == R(0)) continue;
-        const R theta = (A[q * N + q] - A[p * N + p]) / (R(2) * apq);
-        const R t = (theta >= R(0) ? R(1) : R(-1)) / (fabs(theta) + sqrt(theta * theta + R(1)));
-        const R c = R(1) / sqrt(t * t + R(1));
-        const R sn = t * c;
-        for (int k = 0; k < N; ++k) {  // columns p, q
-          const R akp = A[k * N + p], akq = A[k * N + q];
-          A[k * N + p] = c * akp - sn * akq;
-          A[k * N + q] = sn * akp + c * akq;
-        }
-        for (int k = 0; k < N; ++k) {  // rows p, q
-          const R apk = A[p * N + k], aqk = A[q * N + k];
-          A[p * N + k] = c * apk - sn * aqk;
-          A[q * N + k] = sn * apk + c * aqk;
-        }
-        for (int k = 0; k < N; ++k) {
-          const R qkp = Q[k * N + p], qkq = Q[k * N + q];
-          Q[k * N + p] = c * qkp - sn * qkq;
-          Q[k * N + q] = sn * qkp + c * qkq;
-        }
-      }
-    }
-  }
-}
-
-// Replace symmetric A (N x N, row-major) by its projection onto the PSD cone
-// (negative eigenvalues clamped to zero).
-template <class R, int N> TC_D void project_psd(R* A) {
-  R Q[N * N];
-  R W[N * N];
-  for (int i = 0; i < N * N; ++i) W[i] = A[i];
-  jacobi_eig<R, N>(W, Q, sizeof(R) == 4 ? 12 : 20);
-  for (int i = 0; i < N; ++i)
-    for (int j = i; j < N; ++j) {
-      R s = 0;
-      for (int k = 0; k < N; ++k) {
-        const R lk = W[k * N + k];
-        if (lk > R(0)) s += Q[i * N + k] * lk * Q[j * N + k];
-      }
-      A[i * N + j] = s;
-      A[j * N + i] = s;
-    }
-}
-
 // Index of (i, j), i <= j, in packed upper-triangular storage of an N x N
 // symmetric matrix (row-major upper triangle).
 TC_HD int sym_index(int i, int j, int N) {

@@ -287,7 +287,6 @@ template <class R> EnvView<R> Env::view() const {
 
 tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32_t nfixed,
                       const tc_trimesh* ind, const tc_grid* grid);
-tc_status check_initial(Env& env);
 // BSR pattern and fixed-order contribution lists of the Newton matrix
 // (host build from the host tets, after setup_scene)
 tc_status build_bsr(Env& env, const int32_t* tets, const int32_t* fixed_ids, int32_t nfixed);

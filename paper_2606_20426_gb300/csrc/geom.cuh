@@ -124,52 +124,6 @@ template <class T> TC_D T pair_dist2(int kind, const Vec3<T>* x, int* which) {
   return best;
 }
 
-// d^2 with gradient (12) and the NG x NG Hessian block of the gel slots
-// gs[0..ng) (NG = 3 ng).
-template <class T, int NG>
-TC_D T dist2_derivs(int kind, const Vec3<T>* x, const int* gs, T* grad12, T* Hg) {
-  int which;
-  pair_dist2<T>(kind, x, &which);
-  const Cand& c = kind == 0 ? c_pt_cand[which] : c_ee_cand[which];
-  CandEval<T> ev = eval_cand<T>(c, x);
-  for (int i = 0; i < 4; ++i) {
-    grad12[3 * i + 0] = T(2) * ev.w[i] * ev.r.x;
-    grad12[3 * i + 1] = T(2) * ev.w[i] * ev.r.y;
-    grad12[3 * i + 2] = T(2) * ev.w[i] * ev.r.z;
-  }
-  // Fbb^-1 (k <= 2), Fbb = 2 D^T D
-  T inv[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
-  if (ev.k == 1) {
-    inv[0][0] = T(1) / (T(2) * dot(ev.D[0], ev.D[0]));
-  } else if (ev.k == 2) {
-    const T a = T(2) * dot(ev.D[0], ev.D[0]), b = T(2) * dot(ev.D[0], ev.D[1]), d = T(2) * dot(ev.D[1], ev.D[1]);
-    const T id = T(1) / (a * d - b * b);
-    inv[0][0] = d * id;
-    inv[1][1] = a * id;
-    inv[0][1] = inv[1][0] = -b * id;
-  }
-  constexpr int ng = NG / 3;
-  T fxb[NG][2];
-  for (int s = 0; s < ng; ++s) {
-    const int i = gs[s];
-    for (int j = 0; j < 3; ++j) {
-      const T rj = j == 0 ? ev.r.x : (j == 1 ? ev.r.y : ev.r.z);
-      for (int q = 0; q < 2; ++q) {
-        const T Dqj = q < ev.k ? (j == 0 ? ev.D[q].x : (j == 1 ? ev.D[q].y : ev.D[q].z)) : T(0);
-        fxb[3 * s + j][q] = q < ev.k ? T(2) * (ev.B[i][q] * rj + ev.w[i] * Dqj) : T(0);
-      }
-    }
-  }
-  for (int a = 0; a < NG; ++a)
-    for (int b = 0; b < NG; ++b) {
-      const int ia = gs[a / 3], ib = gs[b / 3];
-      T h = (a % 3 == b % 3) ? T(2) * ev.w[ia] * ev.w[ib] : T(0);
-      for (int p = 0; p < ev.k; ++p)
-        for (int q = 0; q < ev.k; ++q) h -= fxb[a][p] * inv[p][q] * fxb[b][q];
-      Hg[a * NG + b] = h;
-    }
-  return ev.d2;
-}
 
 // IPC log barrier and its first two derivatives in d.
 template <class T> TC_D void barrier3(T d, T dhat, T* b, T* b1, T* b2) {
@@ -180,40 +134,6 @@ template <class T> TC_D void barrier3(T d, T dhat, T* b, T* b1, T* b2) {
   *b2 = -T(2) * L - T(4) * e / d + e * e / (d * d);
 }
 
-// Edge-edge mollifier m(c), c = |(x1-x0) x (x3-x2)|^2, on the gel edge
-// (slots 0, 1): value, gradient (6) and Hessian (6x6) w.r.t. x0, x1.
-template <class T> TC_D T mollifier_gel(const Vec3<T>* x, T eps_x, T* gm, T* Hm) {
-  const Vec3<T> u = x[1] - x[0], v = x[3] - x[2];
-  const T uu = dot(u, u), vv = dot(v, v), uv = dot(u, v);
-  const T c = uu * vv - uv * uv;
-  const T t = c / eps_x;
-  if (!(t < T(1))) {
-    for (int i = 0; i < 6; ++i) gm[i] = T(0);
-    for (int i = 0; i < 36; ++i) Hm[i] = T(0);
-    return T(1);
-  }
-  const T m = (T(2) - t) * t;
-  const T m1 = (T(2) - T(2) * t) / eps_x;
-  const T m2 = -T(2) / (eps_x * eps_x);
-  const T gu[3] = {T(2) * vv * u.x - T(2) * uv * v.x, T(2) * vv * u.y - T(2) * uv * v.y,
-                   T(2) * vv * u.z - T(2) * uv * v.z};
-  const T vj[3] = {v.x, v.y, v.z};
-  // d/dx0 = -d/du, d/dx1 = +d/du
-  for (int j = 0; j < 3; ++j) {
-    gm[j] = -m1 * gu[j];
-    gm[3 + j] = m1 * gu[j];
-  }
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) {
-      const T huu = (i == j ? T(2) * vv : T(0)) - T(2) * vj[i] * vj[j];
-      const T h = m2 * gu[i] * gu[j] + m1 * huu;
-      Hm[(0 + i) * 6 + (0 + j)] = h;
-      Hm[(3 + i) * 6 + (3 + j)] = h;
-      Hm[(0 + i) * 6 + (3 + j)] = -h;
-      Hm[(3 + i) * 6 + (0 + j)] = -h;
-    }
-  return m;
-}
 
 // Additive CCD for one pair moving linearly x(t) = x0 + t p: largest t found
 // at which the distance is still >= s d0 (s = 0.1), or t_max when the pair

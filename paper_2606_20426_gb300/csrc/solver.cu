@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include <cstdio>
+#include <mutex>
 #include <cstdlib>
 
 #include "env.cuh"
@@ -323,36 +324,6 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
   }
 }
 
-// q = A p for row v (BSR, one lane group per row); returns p.q on the
-// group's lane 0 (0 elsewhere).  Every lane of the warp calls it.
-template <class R> TC_D double bsr_q_group(const EnvView<R>& e, int v, bool valid) {
-  const int lane = threadIdx.x & (kLanes - 1);
-  const int nv = e.nv;
-  R q0 = 0, q1 = 0, q2 = 0;
-  if (valid) {
-    const int64_t nb = e.nnzb;
-    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
-      const int j = e.bsr_ci[k];
-      const R p0 = e.p[j], p1 = e.p[nv + j], p2 = e.p[2 * nv + j];
-      const R* B = e.bsr_val + k;
-      q0 += B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
-      q1 += B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
-      q2 += B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
-    }
-  }
-  q0 = group_sum(q0);
-  q1 = group_sum(q1);
-  q2 = group_sum(q2);
-  double pq = 0.0;
-  if (valid && lane == 0) {
-    e.q[v] = q0;
-    e.q[nv + v] = q1;
-    e.q[2 * nv + v] = q2;
-    pq = (double)e.p[v] * (double)q0 + (double)e.p[nv + v] * (double)q1 + (double)e.p[2 * nv + v] * (double)q2;
-  }
-  return pq;
-}
-
 // ------------------------------------------------- PCG, one cluster per env
 // Every env of the batch runs all of its CG iterations in one thread-block
 // cluster (16 CTAs where the GPU co-schedules them, else 8; 1024 threads
@@ -374,11 +345,10 @@ template <class R> TC_D double bsr_q_group(const EnvView<R>& e, int v, bool vali
 // every CTA derives bit-identical alpha, beta and stop decisions.  When the
 // halo does not fit the shared-memory budget the SpMV forms p = z + beta p of
 // the neighbours from HBM instead.  Results do not depend on the other envs.
-constexpr int kPcgThreads = 1024;
 constexpr int kPcgMaxChunks = 256;
 
-template <class R>
-__global__ void __launch_bounds__(kPcgThreads, 1)
+template <class R, int kPcgThreads>
+__global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     k_pcg_cluster(const BatchView<R> bv, PartLayout L, int max_iter, int smem_bytes) {
   using A = Acc<R>;
   using AT = typename A::T;
@@ -612,57 +582,91 @@ __global__ void __launch_bounds__(kPcgThreads, 1)
   cluster.sync();
 }
 
-// Launch shape of the PCG kernel: the largest cluster the GPU co-schedules
-// (16, non-portable, if possible, else the portable 8) and the dynamic shared
-// memory of one CTA (the per-block opt-in limit less the static part).
-template <class R> struct PcgShape {
-  int cs = 8;
-  int smem = 0;
-};
-template <class R> static PcgShape<R> pcg_shape_query() {
-  PcgShape<R> shape;
-  {
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    cudaFuncGetAttributes(&fa, k_pcg_cluster<R>);
-    shape.smem = std::max(0, optin - (int)fa.sharedSizeBytes - 1024);
-    cudaFuncSetAttribute(k_pcg_cluster<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, shape.smem);
-    if (cudaFuncSetAttribute(k_pcg_cluster<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(16);
-      cfg.blockDim = dim3(kPcgThreads);
-      cfg.dynamicSmemBytes = shape.smem;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = 16;
-      attr[0].val.clusterDim.y = 1;
-      attr[0].val.clusterDim.z = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<R>, &cfg) == cudaSuccess && n > 0) shape.cs = 16;
-      if (trace_on())
-        std::fprintf(stderr, "[tc] pcg cluster size %d, %d co-resident, %d B shared per CTA\n", shape.cs, n,
-                     shape.smem);
-    }
-    cudaGetLastError();
-  }
-  return shape;
+// Launch shape of the PCG kernel: cluster size (CTAs per env) and threads
+// per CTA.  The dynamic shared memory of a CTA is the SM's share for the
+// CTAs it holds (one of 1024 threads or two of 512) less the static part.
+// The shape in use is process-wide per precision (so an env's result does
+// not depend on when or with whom it is stepped): the largest co-schedulable
+// cluster of 1024-thread CTAs unless tc_pcg_shape / tc_autotune_pcg chose
+// another.
+template <class R, int NT> static PcgShape pcg_probe(int cs) {
+  PcgShape sh;
+  sh.cs = cs;
+  sh.threads = NT;
+  int dev = 0, optin = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k_pcg_cluster<R, NT>);
+  const int ctas = 1024 / NT;
+  sh.smem = std::max(0, std::min(optin, per_sm / ctas - 1024) - (int)fa.sharedSizeBytes - 1024);
+  cudaFuncSetAttribute(k_pcg_cluster<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+  if (cs > 8) cudaFuncSetAttribute(k_pcg_cluster<R, NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sh.smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<R, NT>, &cfg) != cudaSuccess) n = 0;
+  sh.coresident = n;
+  cudaGetLastError();
+  return sh;
 }
-template <class R> static const PcgShape<R>& pcg_shape() {
-  static const PcgShape<R> shape = pcg_shape_query<R>();  // thread-safe one-time init
-  return shape;
+
+template <class R> static PcgShape pcg_probe_any(int cs, int threads) {
+  return threads == 512 ? pcg_probe<R, 512>(cs) : pcg_probe<R, 1024>(cs);
+}
+
+template <class R> struct PcgSel {
+  std::mutex mu;
+  bool set = false;
+  PcgShape cur;
+};
+template <class R> static PcgSel<R>& pcg_sel() {
+  static PcgSel<R> sel;
+  return sel;
+}
+
+template <class R> PcgShape pcg_shape() {
+  PcgSel<R>& sel = pcg_sel<R>();
+  std::lock_guard<std::mutex> lk(sel.mu);
+  if (!sel.set) {
+    sel.cur = pcg_probe_any<R>(16, 1024);
+    if (sel.cur.coresident <= 0) sel.cur = pcg_probe_any<R>(8, 1024);
+    sel.set = true;
+    if (trace_on())
+      std::fprintf(stderr, "[tc] pcg shape: %d CTAs x %d threads, %d co-resident clusters, %d B shared per CTA\n",
+                   sel.cur.cs, sel.cur.threads, sel.cur.coresident, sel.cur.smem);
+  }
+  return sel.cur;
+}
+
+template <class R> tc_status set_pcg_shape(int cs, int threads) {
+  if ((cs != 8 && cs != 16) || (threads != 512 && threads != 1024)) return TC_ERR_INVALID_ARG;
+  const PcgShape sh = pcg_probe_any<R>(cs, threads);
+  if (sh.coresident <= 0) return TC_ERR_CAPACITY;
+  PcgSel<R>& sel = pcg_sel<R>();
+  std::lock_guard<std::mutex> lk(sel.mu);
+  sel.cur = sh;
+  sel.set = true;
+  return TC_OK;
 }
 
 template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s) {
   if (b.units[K_VERT] > 0) TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
   TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
-  const PcgShape<R>& sh = pcg_shape<R>();
+  const PcgShape sh = pcg_shape<R>();
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(b.nenv * sh.cs));
-  cfg.blockDim = dim3(kPcgThreads);
+  cfg.blockDim = dim3((unsigned)sh.threads);
   cfg.dynamicSmemBytes = (size_t)sh.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -673,7 +677,10 @@ template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStre
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t err = cudaSuccess;
-  TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R>, b.bv, b.L, max_iter, sh.smem));
+  if (sh.threads == 512)
+    TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R, 512>, b.bv, b.L, max_iter, sh.smem));
+  else
+    TC_LAUNCH("k_pcg_cluster", s, err = cudaLaunchKernelEx(&cfg, k_pcg_cluster<R, 1024>, b.bv, b.L, max_iter, sh.smem));
   return err == cudaSuccess ? TC_OK : TC_ERR_CUDA;
 }
 
@@ -750,7 +757,9 @@ template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStre
   template tc_status b_pcg<R>(const BatchHost<R>&, int, cudaStream_t);        \
   template void b_pmax<R>(const BatchHost<R>&, cudaStream_t);                 \
   template void b_trial<R>(const BatchHost<R>&, cudaStream_t);                \
-  template void b_step_vectors<R>(const BatchHost<R>&, int, cudaStream_t);
+  template void b_step_vectors<R>(const BatchHost<R>&, int, cudaStream_t);    \
+  template PcgShape pcg_shape<R>();                                           \
+  template tc_status set_pcg_shape<R>(int, int);
 TC_INST(float)
 TC_INST(double)
 #undef TC_INST

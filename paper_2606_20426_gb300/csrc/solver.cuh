@@ -11,10 +11,20 @@ struct PartLayout {
   int64_t asmb;      // K_VGRP units: (|g|^2, inertia energy)
   int64_t inert;     // K_VERT units: trial inertia energy
   int64_t ccd[3];    // contact units: min TOI
-  int64_t rz, rr;    // K_VERT units
+  int64_t rz, rr;    // K_VERT units: PCG start r.z, r.r
   int64_t env_s;     // 8 per env: PCG start values
   int64_t total;
 };
+
+// Launch shape of the per-env PCG cluster (process-wide per precision).
+struct PcgShape {
+  int cs = 16;          // CTAs per env (cluster size)
+  int threads = 1024;   // threads per CTA
+  int smem = 0;         // dynamic shared memory per CTA
+  int coresident = 0;   // clusters of this shape the GPU holds at once
+};
+template <class R> PcgShape pcg_shape();
+template <class R> tc_status set_pcg_shape(int cs, int threads);
 
 template <class R> struct BatchHost {
   int nenv = 0;

@@ -25,7 +25,8 @@ EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_tract
            "tc_surface_faces", "tc_boundary_faces", "tc_pixel_table", "tc_get_positions", "tc_set_positions",
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
            "tc_profile_read", "tc_pressure_map_noalloc", "tc_server_create", "tc_submit", "tc_poll", "tc_wait",
-           "tc_server_info", "tc_server_stream", "tc_server_destroy"]
+           "tc_server_info", "tc_server_stream", "tc_server_destroy", "tc_pcg_shape", "tc_autotune_pcg",
+           "tc_energy_gradient"]
 
 
 class TcError(RuntimeError):
@@ -85,6 +86,11 @@ class ServerStats(ctypes.Structure):
                 ("budget_bytes", ctypes.c_size_t)]
 
 
+class PcgTune(ctypes.Structure):
+    _fields_ = [("cluster_ctas", ctypes.c_int32), ("threads", ctypes.c_int32), ("coresident", ctypes.c_int32),
+                ("us_per_env_iter", ctypes.c_double), ("env_iters", ctypes.c_int64)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("nv", ctypes.c_int32), ("nt", ctypes.c_int32), ("nf", ctypes.c_int32), ("nfc", ctypes.c_int32),
                 ("nec", ctypes.c_int32), ("nvc", ctypes.c_int32), ("ind_nv", ctypes.c_int32),
@@ -116,6 +122,7 @@ def load():
         "tc_traction": [P, P, P, P],
         "tc_pressure_map": [P, P, P],
         "tc_contact_force": [P, P],
+        "tc_energy_gradient": [P, P, P],
         "tc_surface_faces": [P, P, P],
         "tc_boundary_faces": [P, P, P],
         "tc_pixel_table": [P, P, P],
@@ -133,6 +140,9 @@ def load():
         "tc_poll": [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(Result)],
         "tc_wait": [P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)],
         "tc_server_info": [P, ctypes.POINTER(ServerStats)],
+        "tc_pcg_shape": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
+        "tc_autotune_pcg": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(PcgTune), ctypes.c_int32,
+                            ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -273,6 +283,14 @@ class Env:
                "tc_pressure_map")
         return out, mask
 
+    def energy_gradient(self):
+        """(E, g): the incremental potential at the current state and its
+        gradient (nv, 3) with fixed vertices zeroed."""
+        E = ctypes.c_double()
+        g = np.empty((self.info["nv"], 3), dtype=np.float64)
+        _check(self.lib.tc_energy_gradient(self.h, ctypes.byref(E), g.ctypes.data), "tc_energy_gradient")
+        return E.value, g
+
     def contact_force(self):
         f = np.zeros(3)
         _check(self.lib.tc_contact_force(self.h, f.ctypes.data), "tc_contact_force")
@@ -401,6 +419,24 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pcg_shape(precision, cluster_ctas, threads):
+    """Select the PCG launch shape (process-wide for the precision)."""
+    prec = TC_FP64 if precision in ("fp64", TC_FP64) else TC_FP32_MIXED
+    _check(load().tc_pcg_shape(prec, int(cluster_ctas), int(threads)), "tc_pcg_shape")
+
+
+def autotune_pcg(envs):
+    """Time the envs' PCG solves under every launch shape, keep the fastest;
+    returns one dict per shape tried."""
+    envs = list(envs)
+    lib = load()
+    handles = (ctypes.c_void_p * len(envs))(*[e.h for e in envs])
+    res = (PcgTune * 8)()
+    n = ctypes.c_int32()
+    _check(lib.tc_autotune_pcg(handles, len(envs), res, 8, ctypes.byref(n)), "tc_autotune_pcg")
+    return [{k: getattr(res[i], k) for k, _ in PcgTune._fields_} for i in range(min(n.value, 8))]
 
 
 def step_batch(envs, poses, raise_on_error=False):

@@ -146,3 +146,22 @@ def block(nx=30, ny=30, nz=5, Lx=30e-3, Ly=30e-3, Lz=5e-3):
     """9DTact-like block."""
     return box(nx, ny, nz, Lx, Ly, Lz)
 
+
+def hertz_block(L=20e-3, H=10e-3, h_fine=0.12e-3, h_coarse=1.5e-3, r_core=1.8e-3, r_band=3.0e-3):
+    """Block [0,L]^2 x [0,H] for the sphere-indentation check: x/y spacing
+    h_fine within r_core of the centre, blending (cosine) to h_coarse over
+    r_band; z spacing h_fine at the top, growing linearly towards h_coarse at
+    the bottom."""
+    def hxy(x):
+        r = np.abs(x - L / 2)
+        s = np.clip((r - r_core) / r_band, 0.0, 1.0)
+        return h_fine + (h_coarse - h_fine) * 0.5 * (1.0 - np.cos(np.pi * s))
+
+    def hz(z):
+        d = H - z
+        return np.minimum(h_coarse, h_fine + 0.35 * d)
+
+    xs = _graded_nodes(L, hxy, 1.0)
+    zs = _graded_nodes(H, hz, 1.0, center=False)
+    return kuhn_grid(xs, xs, zs)
+

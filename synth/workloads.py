@@ -198,6 +198,25 @@ def mixed_envs(seed, n_per_family=20, pads=(5000, 60000), domes=(8000, 40000), b
     return out
 
 
+def hertz_env(nu=0.3, radius=5e-3, depth=0.25e-3, steps=5, dhat=0.01e-3, precision="fp32"):
+    """Frictionless sphere pressed quasi-statically into a 20 x 20 x 10 mm
+    block (bottom fixed) refined to 0.12 mm under the contact: the setting
+    of the Hertz force-indentation law F = 4/3 E* sqrt(R) delta^(3/2),
+    E* = E / (1 - nu^2), for a contact radius sqrt(R delta) << block size."""
+    X, T = meshes.hertz_block()
+    L = 20e-3
+    top = float(X[:, 2].max())
+    V, F = indenters.icosphere(radius, icosphere_level_for(radius, 0.1e-3))
+    z0 = top + dhat - indenters.lowest_z(V)
+    start = _pose(L / 2, L / 2, z0)
+    poses = [_pose(L / 2, L / 2, z0 - (dhat + depth) * k / steps) for k in range(1, steps + 1)]
+    mat = dict(MATERIAL)
+    mat["nu"] = nu
+    return dict(name=f"hertz-nu{nu}", X=X, tets=T, material=mat, fixed=_fixed_bottom(X), ind_V=V, ind_F=F,
+                start_pose=start, poses=poses, grid=None, opts=_opts(dhat, 0.0, precision), depth=depth,
+                radius=radius, top=top)
+
+
 def splitmix64_array(seed, n):
     """n outputs of splitmix64 as a counter-based generator: output i is the
     mix of state seed + (i+1)*gamma (vectorised, uint64 wrap-around)."""
