@@ -392,7 +392,8 @@ def run_ours(args):
     wstreams = srv.streams()
     # ------------- served form (headline): closed loop, one request in flight per env
     clients.closed_loop(args.warmup)
-    tuned = autotune_pcg(served) if args.autotune else None
+    # requests run on their own workers, so an env's solve is latency-bound
+    tuned = autotune_pcg(served, mode="latency") if args.autotune else None
     barrier()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     ev_end = [torch.cuda.Event(enable_timing=True) for _ in wstreams]
@@ -647,7 +648,7 @@ def run_pcg_probe(args):
     launches = envs[0].kernel_times().get("k_pcg_cluster", (0.0, 0))[1]
     for e in envs:
         e.profile(False)
-    tune = autotune_pcg(envs)
+    tune = autotune_pcg(envs, mode="throughput")
     info = envs[0].info
     print(json.dumps({"pcg_launches_before": int(launches), "envs": args.envs, "steps": args.pcg_probe,
                       "bytes_per_env_iter": pcg_iteration_bytes(info), "autotune": tune}), flush=True)

@@ -179,12 +179,15 @@ typedef struct {
 /* Autotuner: assemble the Newton systems of the n envs at their current
  * state (positions are not changed), time their PCG solves under every
  * co-schedulable shape, and select the shape with the least device time per
- * CG iteration of one env.  results (host, up to max_results entries, may be
- * NULL when max_results is 0) receives one entry per shape tried and
+ * CG iteration of one env.  mode 0 launches each env's solve alone, one
+ * after another (the latency of one env's solve: requests on their own
+ * server workers); mode 1 launches one solve over all n envs (the
+ * throughput of a full batch).  results (host, up to max_results entries,
+ * may be NULL when max_results is 0) receives one entry per shape tried and
  * *n_results their count.  The envs must share precision and device and have
  * no server request pending.  Not in the paper. */
-tc_status tc_autotune_pcg(tc_env** envs, int32_t n, tc_pcg_tune* results, int32_t max_results,
-                          int32_t* n_results);
+tc_status tc_autotune_pcg(tc_env** envs, int32_t n, int32_t mode, tc_pcg_tune* results,
+                          int32_t max_results, int32_t* n_results);
 
 /* Cauchy stress per tet (Eq. 4 with the rest-stable reading):
  * sigma_out device float 6 x nt, component-major (component k of tet e at

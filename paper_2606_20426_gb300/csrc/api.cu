@@ -317,8 +317,9 @@ tc_status tc_pcg_shape(int32_t precision, int32_t cluster_ctas, int32_t threads)
   return TC_ERR_INVALID_ARG;
 }
 
-tc_status tc_autotune_pcg(tc_env** envs, int32_t n, tc_pcg_tune* results, int32_t max_results, int32_t* n_results) {
-  if (n <= 0 || !envs || (max_results > 0 && !results)) return TC_ERR_INVALID_ARG;
+tc_status tc_autotune_pcg(tc_env** envs, int32_t n, int32_t mode, tc_pcg_tune* results, int32_t max_results,
+                          int32_t* n_results) {
+  if (n <= 0 || !envs || (mode != 0 && mode != 1) || (max_results > 0 && !results)) return TC_ERR_INVALID_ARG;
   std::vector<Env*> set;
   for (int i = 0; i < n; ++i) {
     if (!envs[i] || envs[i]->impl.busy.load() || envs[i]->impl.precision != envs[0]->impl.precision ||
@@ -333,8 +334,9 @@ tc_status tc_autotune_pcg(tc_env** envs, int32_t n, tc_pcg_tune* results, int32_
     if (e->stream != lead.stream) cudaStreamSynchronize(e->stream);
   tc::ProfGuard pg(lead);
   std::vector<tc::PcgTune> out;
-  const tc_status st = lead.precision == TC_FP64 ? tc::autotune_pcg<double>(tc::exec_of<double>(lead), set, out)
-                                                 : tc::autotune_pcg<float>(tc::exec_of<float>(lead), set, out);
+  const tc_status st = lead.precision == TC_FP64
+                           ? tc::autotune_pcg<double>(tc::exec_of<double>(lead), set, mode, out)
+                           : tc::autotune_pcg<float>(tc::exec_of<float>(lead), set, mode, out);
   if (n_results) *n_results = (int32_t)out.size();
   for (int k = 0; k < (int)out.size() && k < max_results; ++k) {
     results[k].cluster_ctas = out[k].cs;

@@ -621,7 +621,8 @@ template <class R> tc_status contact_force_at_state(BatchExec<R>& X, Env& env, d
   return TC_OK;
 }
 
-template <class R> tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, std::vector<PcgTune>& out) {
+template <class R>
+tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, int mode, std::vector<PcgTune>& out) {
   out.clear();
   if (envs.empty()) return TC_OK;
   tc_status st = ensure_candidates<R>(X, envs);
@@ -649,17 +650,27 @@ template <class R> tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env
     const PcgShape sh = pcg_shape<R>();
     double us = 1e300;
     long long iters = 0;
-    for (int rep = 0; rep < 3; ++rep) {
-      if ((st = X.build(envs, tol2.data(), nullptr)) != TC_OK) break;
-      cudaEventRecord(e0, X.stream);
-      if ((st = b_pcg<R>(X.host, pcg_max, X.stream)) != TC_OK) break;
-      cudaEventRecord(e1, X.stream);
-      if ((st = X.read()) != TC_OK) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+    for (int rep = 0; rep < 3 && st == TC_OK; ++rep) {
+      // mode 0: every env's solve alone, one after another (the latency of
+      // one env's solve, as when requests run on their own workers);
+      // mode 1: one launch over all envs (the throughput of a full batch)
+      const size_t groups = mode == 0 ? envs.size() : 1;
+      double ms_total = 0.0;
       long long it = 0;
-      for (size_t i = 0; i < envs.size(); ++i) it += X.h_sc[i].pcg_iters;
-      if (it > 0 && rep > 0) us = std::min(us, 1e3 * ms / (double)it);
+      for (size_t gi = 0; gi < groups && st == TC_OK; ++gi) {
+        std::vector<Env*> set = mode == 0 ? std::vector<Env*>{envs[gi]} : envs;
+        std::vector<double> t2 = mode == 0 ? std::vector<double>{tol2[gi]} : tol2;
+        if ((st = X.build(set, t2.data(), nullptr)) != TC_OK) break;
+        cudaEventRecord(e0, X.stream);
+        if ((st = b_pcg<R>(X.host, pcg_max, X.stream)) != TC_OK) break;
+        cudaEventRecord(e1, X.stream);
+        if ((st = X.read()) != TC_OK) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms_total += ms;
+        for (size_t i = 0; i < set.size(); ++i) it += X.h_sc[i].pcg_iters;
+      }
+      if (it > 0 && rep > 0) us = std::min(us, 1e3 * ms_total / (double)it);
       iters = it;
     }
     if (st != TC_OK) break;
@@ -688,7 +699,7 @@ template <class R> tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env
   template tc_status energy_at_state<R>(BatchExec<R>&, Env&, Scalars*);                                         \
   template tc_status contact_force_at_state<R>(BatchExec<R>&, Env&, double*);                                \
   template tc_status energy_gradient_at_state<R>(BatchExec<R>&, Env&, double*, double*);                     \
-  template tc_status autotune_pcg<R>(BatchExec<R>&, const std::vector<Env*>&, std::vector<PcgTune>&);
+  template tc_status autotune_pcg<R>(BatchExec<R>&, const std::vector<Env*>&, int, std::vector<PcgTune>&);
 TC_INST(float)
 TC_INST(double)
 #undef TC_INST

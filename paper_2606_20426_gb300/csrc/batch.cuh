@@ -75,13 +75,16 @@ tc_status step_batch(BatchExec<R>& X, const std::vector<Env*>& envs, const std::
                      std::vector<tc_status>& result);
 template <class R> tc_status energy_at_state(BatchExec<R>& X, Env& env, Scalars* out);
 // Time the PCG of the envs' current Newton systems under every co-schedulable
-// launch shape and keep the fastest (per CG iteration of one env).
+// launch shape and keep the fastest per CG iteration of one env: mode 0 with
+// each env's solve launched alone (latency), mode 1 with one launch over all
+// envs (throughput).
 struct PcgTune {
   int cs, threads, coresident;
   double us_per_env_iter;
   long long env_iters;
 };
-template <class R> tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, std::vector<PcgTune>& out);
+template <class R>
+tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, int mode, std::vector<PcgTune>& out);
 template <class R> tc_status contact_force_at_state(BatchExec<R>& X, Env& env, double* f);
 template <class R> tc_status energy_gradient_at_state(BatchExec<R>& X, Env& env, double* E, double* grad);
 

@@ -141,8 +141,8 @@ def load():
         "tc_wait": [P, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(Result)],
         "tc_server_info": [P, ctypes.POINTER(ServerStats)],
         "tc_pcg_shape": [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
-        "tc_autotune_pcg": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(PcgTune), ctypes.c_int32,
-                            ctypes.POINTER(ctypes.c_int32)],
+        "tc_autotune_pcg": [ctypes.POINTER(P), ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(PcgTune),
+                            ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -427,15 +427,17 @@ def pcg_shape(precision, cluster_ctas, threads):
     _check(load().tc_pcg_shape(prec, int(cluster_ctas), int(threads)), "tc_pcg_shape")
 
 
-def autotune_pcg(envs):
+def autotune_pcg(envs, mode="latency"):
     """Time the envs' PCG solves under every launch shape, keep the fastest;
-    returns one dict per shape tried."""
+    mode "latency": each env's solve alone, "throughput": one launch over all.
+    Returns one dict per shape tried."""
     envs = list(envs)
     lib = load()
     handles = (ctypes.c_void_p * len(envs))(*[e.h for e in envs])
     res = (PcgTune * 8)()
     n = ctypes.c_int32()
-    _check(lib.tc_autotune_pcg(handles, len(envs), res, 8, ctypes.byref(n)), "tc_autotune_pcg")
+    m = 1 if mode == "throughput" else 0
+    _check(lib.tc_autotune_pcg(handles, len(envs), m, res, 8, ctypes.byref(n)), "tc_autotune_pcg")
     return [{k: getattr(res[i], k) for k, _ in PcgTune._fields_} for i in range(min(n.value, 8))]
 
 
