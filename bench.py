@@ -36,7 +36,9 @@ WORKLOAD = ("gelsight-like graded pad 18x24x4 mm, ~60k tets, sphere/cylinder/box
 
 # DRAM traffic per launch unit from the committed ncu captures (profiles/),
 # keyed by kernel; valid only while the kernel's source file is unchanged.
-NCU_TRAFFIC = {}
+# k_pcg_cluster: dram read + write of one launch over 8 GelSight-like envs
+# (1,446 CG iterations of one env each) -> bytes per CG iteration of one env.
+NCU_TRAFFIC = {"k_pcg_cluster": {"bytes_per_unit": (52484096 + 3685632) / 1446, "sha": "9df38d60777e6240"}}
 
 
 def peaks():
@@ -204,8 +206,8 @@ def _roofline(top, infos, pcg_iters_by_env, peak, peak_kind):
         achieved = bytes_per_launch / (ms / n / 1e3) / 1e9
         tr = NCU_TRAFFIC.get(name)
         traffic = None
-        if tr and tr["sha"] == src_sha(KERNEL_SRC[name]):
-            traffic = tr["bytes_per_launch"]
+        if tr and units and tr["sha"] == src_sha(KERNEL_SRC[name]):
+            traffic = int(tr["bytes_per_unit"] * units)
         return {"kernel": name, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "bytes_per_launch": int(bytes_per_launch),
