@@ -265,11 +265,14 @@ TC_D void contact_prim_points(const EnvView<R>& e, const R* u, int prim, double 
 // primitive then adds its pairs in candidate order (fixed-order sums, no
 // atomics) before rotating the sums to the world frame into the slots.
 template <class R, int GK, int MODE>
-__global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
+__global__ void __launch_bounds__(MODE == 1 ? 128 : 512) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int NG = 3 * NGP;
   constexpr int NH = NG * (NG + 1) / 2;
-  constexpr int CH = MODE == 1 ? 512 / (int)sizeof(R) : 128;  // pairs per chunk
+  // threads: the energy-only pass has no per-pair scratch and spreads a
+  // unit's pairs over 512 threads; the pass with slots keeps 128
+  constexpr int NT = MODE == 1 ? 128 : 512;
+  constexpr int CH = MODE == 1 ? 512 / (int)sizeof(R) : NT;  // pairs per chunk
   __shared__ int s_off[129];
   __shared__ R s_gh[MODE == 1 ? CH : 1][MODE == 1 ? NG + NH : 1];
   __shared__ Origin s_o[128];
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
   const int n = prim_count(e, GK);
   const int32_t* cl = e.cand[GK];
   const int mine = base + (int)threadIdx.x;
-  const int kept = mine < n ? min(e.cand_n[GK][mine], e.cand_cap) : 0;
+  const int kept = (threadIdx.x < 128 && mine < n) ? min(e.cand_n[GK][mine], e.cand_cap) : 0;
   if (kept > 0) {  // the primitive's FP64 geometry, once, for all its pairs
     double bw[3][3];
     Origin o;
@@ -291,7 +294,7 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
     for (int l = 0; l < NGP; ++l) s_xg[threadIdx.x][l] = rel<R>(bw[l], o.d);
   }
   if (threadIdx.x == 0) s_off[0] = 0;
-  s_off[threadIdx.x + 1] = kept;
+  if (threadIdx.x < 128) s_off[threadIdx.x + 1] = kept;
   __syncthreads();
   if (threadIdx.x == 0)
     for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
@@ -314,7 +317,7 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
   else { gs[0] = 1; gs[1] = 2; gs[2] = 3; }
   const R dhat2 = (R)(e.dhat * e.dhat);
   for (int c0 = 0; c0 < total; c0 += CH) {
-    for (int q = c0 + (int)threadIdx.x; q < total && q < c0 + CH; q += 128) {
+    for (int q = c0 + (int)threadIdx.x; q < total && q < c0 + CH; q += NT) {
       int lo_i = 0, hi_i = 127;  // last i with s_off[i] <= q
       while (lo_i < hi_i) {
         const int mid = (lo_i + hi_i + 1) >> 1;
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
       __syncthreads();
     }
   }
-  if (MODE == 1 && mine < n) {
+  if (MODE == 1 && threadIdx.x < 128 && mine < n) {
     const int prim = mine;
     // body -> world: g_w = R g_b per point, H_w = R H_b R^T per 3x3 block
     R Rm[9];
@@ -401,8 +404,8 @@ __global__ void __launch_bounds__(128) k_contact(const BatchView<R> bv, PartLayo
           }
       }
   }
-  energy = block_sum<128>(energy);
-  dmin2 = block_min<128>(dmin2);
+  energy = block_sum<NT>(energy);
+  dmin2 = block_min<NT>(dmin2);
   if (threadIdx.x == 0) {
     part_out[2 * blockIdx.x] = energy;
     part_out[2 * blockIdx.x + 1] = dmin2;
@@ -422,9 +425,9 @@ template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, 
     if (ne) TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<ne, 128, 0, s>>>(b.bv, b.L, t));
     if (nf) TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<nf, 128, 0, s>>>(b.bv, b.L, t));
   } else {
-    if (nv) TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<nv, 128, 0, s>>>(b.bv, b.L, t));
-    if (ne) TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<ne, 128, 0, s>>>(b.bv, b.L, t));
-    if (nf) TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<nf, 128, 0, s>>>(b.bv, b.L, t));
+    if (nv) TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<nv, 512, 0, s>>>(b.bv, b.L, t));
+    if (ne) TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<ne, 512, 0, s>>>(b.bv, b.L, t));
+    if (nf) TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<nf, 512, 0, s>>>(b.bv, b.L, t));
   }
 }
 
@@ -503,8 +506,12 @@ TC_D void ccd_prim_box32(const EnvView<R>& e, const Motion& mo, const R* dir, in
 // and the narrow phase runs all threads of the block over the unit's
 // flattened (primitive, candidate) pairs: additive CCD per pair, so the few
 // primitives near the indenter do not serialise the block.
+// A unit's 128 primitives run the broad phase on the first 128 threads; all
+// kCcdThreads share its narrow phase.
+constexpr int kCcdThreads = 512;
+
 template <class R, int GK>
-__global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L) {
+__global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, PartLayout L) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
   __shared__ int s_off[129];
@@ -519,7 +526,7 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
   const int n = prim_count(e, GK);
   int32_t* cl = e.cand[GK];
   int kept = 0;
-  if (base + (int)threadIdx.x < n) {
+  if (threadIdx.x < 128 && base + (int)threadIdx.x < n) {
     const int prim = base + threadIdx.x;
     float lo[3], hi[3];
     ccd_prim_box32<R, GK>(e, mo, dir, prim, lo, hi);
@@ -545,7 +552,7 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
   }
   // exclusive prefix of the kept counts (128 threads, fixed order)
   if (threadIdx.x == 0) s_off[0] = 0;
-  s_off[threadIdx.x + 1] = kept;
+  if (threadIdx.x < 128) s_off[threadIdx.x + 1] = kept;
   __syncthreads();
   if (threadIdx.x == 0)
     for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
@@ -553,7 +560,7 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
   const int total = s_off[128];
   double tmin = 1.0;
   const int kind = GK == GE ? 1 : 0;
-  for (int q = threadIdx.x; q < total; q += 128) {
+  for (int q = threadIdx.x; q < total; q += kCcdThreads) {
     int lo_i = 0, hi_i = 127;  // last i with s_off[i] <= q
     while (lo_i < hi_i) {
       const int mid = (lo_i + hi_i + 1) >> 1;
@@ -585,7 +592,7 @@ __global__ void __launch_bounds__(128) k_ccd(const BatchView<R> bv, PartLayout L
     const R t = accd<R>(kind, x0, p, (R)1.0, 4096);
     tmin = fmin(tmin, (double)t);
   }
-  tmin = block_min<128>(tmin);
+  tmin = block_min<kCcdThreads>(tmin);
   if (threadIdx.x == 0) part_out[blockIdx.x] = tmin;
 }
 
@@ -604,9 +611,9 @@ __global__ void __launch_bounds__(kBlock) k_ccd_env(const BatchView<R> bv, PartL
 
 template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s) {
   const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
-  if (nv) TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<nv, 128, 0, s>>>(b.bv, b.L));
-  if (ne) TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<ne, 128, 0, s>>>(b.bv, b.L));
-  if (nf) TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<nf, 128, 0, s>>>(b.bv, b.L));
+  if (nv) TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<nv, kCcdThreads, 0, s>>>(b.bv, b.L));
+  if (ne) TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<ne, kCcdThreads, 0, s>>>(b.bv, b.L));
+  if (nf) TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<nf, kCcdThreads, 0, s>>>(b.bv, b.L));
   TC_LAUNCH("k_ccd_env", s, k_ccd_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
 }
 
