@@ -22,6 +22,9 @@
 
 namespace tc {
 
+// smallest forcing term of the inexact Newton solve in the mixed mode
+constexpr double kEtaFloor32 = 0.1;
+
 #define TC_CHECK(x)                                 \
   do {                                              \
     cudaError_t e_ = (x);                           \
@@ -426,13 +429,13 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         continue;
       }
       // forcing term of the inexact Newton solve: min(0.5, sqrt(|g| / |g0|)),
-      // floored in the mixed mode at 1e-2.  There the solve ends on the step
-      // test (|dx|_inf <= ptol), so a step known to 1 % is enough: the error
-      // left after the last step is ~1e-2 of a step already below ptol, while
-      // a tighter floor only multiplies the CG iterations of the final Newton
-      // iterations.
+      // floored in the mixed mode at 0.1.  There the solve ends on the step
+      // test (|dx|_inf <= ptol): near the solution each Newton step then cuts
+      // the error at least tenfold, so the step that passes the test leaves
+      // an error of ~0.1 ptol, while a tighter floor only multiplies the CG
+      // iterations of the last Newton iterations.
       double et = std::min(0.5, std::sqrt(gn / std::max(c.g0, 1e-300)));
-      et = std::max(et, e.precision == TC_FP64 ? 1e-10 : 1e-2);
+      et = std::max(et, e.precision == TC_FP64 ? 1e-10 : kEtaFloor32);
       P.push_back(N[j]);
       eta.push_back(et * et * sc.gnorm2);  // squared PCG stopping tolerance (eta |g|)^2
     }
