@@ -22,8 +22,9 @@
 
 namespace tc {
 
-// smallest forcing term of the inexact Newton solve in the mixed mode
+// smallest and largest forcing term of the inexact Newton solve in the mixed mode
 constexpr double kEtaFloor32 = 0.1;
+constexpr double kEtaCap32 = 0.1;
 
 #define TC_CHECK(x)                                 \
   do {                                              \
@@ -428,13 +429,15 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         fail(c, TC_ERR_NEWTON_MAXITER);
         continue;
       }
-      // forcing term of the inexact Newton solve: min(0.5, sqrt(|g| / |g0|)),
-      // floored in the mixed mode at 0.1.  There the solve ends on the step
-      // test (|dx|_inf <= ptol): near the solution each Newton step then cuts
-      // the error at least tenfold, so the step that passes the test leaves
-      // an error of ~0.1 ptol, while a tighter floor only multiplies the CG
-      // iterations of the last Newton iterations.
-      double et = std::min(0.5, std::sqrt(gn / std::max(c.g0, 1e-300)));
+      // forcing term of the inexact Newton solve: min(0.5, sqrt(|g| / |g0|))
+      // in FP64; 0.1 throughout in the mixed mode.  There the solve ends on
+      // the step test (|dx|_inf <= ptol): near the solution each Newton step
+      // then cuts the error at least tenfold, so the step that passes the
+      // test leaves an error of ~0.1 ptol, while a tighter floor only
+      // multiplies the CG iterations of the last Newton iterations, and a
+      // looser start (0.5) spends extra Newton iterations on nearly
+      // steepest-descent steps.
+      double et = std::min(e.precision == TC_FP64 ? 0.5 : kEtaCap32, std::sqrt(gn / std::max(c.g0, 1e-300)));
       et = std::max(et, e.precision == TC_FP64 ? 1e-10 : kEtaFloor32);
       P.push_back(N[j]);
       eta.push_back(et * et * sc.gnorm2);  // squared PCG stopping tolerance (eta |g|)^2
