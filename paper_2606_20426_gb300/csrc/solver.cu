@@ -686,12 +686,16 @@ template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStre
 
 // ------------------------------------------------------ per-env reductions
 
-// max-norm of dx -> pmax, and g.dx (minus twice the Newton decrement)
+// max-norm of dx -> pmax, and g.dx (minus twice the Newton decrement):
+// partials per K_VERT unit (the PCG's r.z / r.r regions, free again once the
+// PCG has run), folded per env in unit order
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_pmax(const BatchView<R> bv) {
-  const EnvView<R>& e = bv.views[blockIdx.x];
+__global__ void __launch_bounds__(kBlock) k_pmax(const BatchView<R> bv, PartLayout L) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const int v = l.chunk * kBlock + threadIdx.x;
   double m = 0.0, gd = 0.0;
-  for (int v = threadIdx.x; v < e.nv; v += blockDim.x)
+  if (v < e.nv)
     for (int i = 0; i < 3; ++i) {
       const double d = (double)e.dx[i * e.nv + v];
       m = fmax(m, fabs(d));
@@ -700,6 +704,21 @@ __global__ void __launch_bounds__(kBlock) k_pmax(const BatchView<R> bv) {
   m = block_max<kBlock>(m);
   gd = block_sum<kBlock>(gd);
   if (threadIdx.x == 0) {
+    bv.part[L.rz + blockIdx.x] = m;
+    bv.part[L.rr + blockIdx.x] = gd;
+  }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_pmax_env(const BatchView<R> bv, PartLayout L) {
+  const int env = blockIdx.x;
+  const EnvView<R>& e = bv.views[env];
+  const int* p = bv.prefix + K_VERT * (bv.nenv + 1);
+  double m = 0.0;
+  for (int u = p[env] + threadIdx.x; u < p[env + 1]; u += blockDim.x) m = fmax(m, bv.part[L.rz + u]);
+  m = block_max<kBlock>(m);
+  const double gd = env_unit_sum(bv, K_VERT, env, bv.part + L.rr);
+  if (threadIdx.x == 0) {
     e.sc->pmax = m;
     e.sc->reduce_tmp[3] = gd;
     if (!isfinite(m)) e.sc->status |= ST_NONFINITE;
@@ -707,7 +726,8 @@ __global__ void __launch_bounds__(kBlock) k_pmax(const BatchView<R> bv) {
 }
 
 template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s) {
-  TC_LAUNCH("k_pmax", s, k_pmax<R><<<b.nenv, kBlock, 0, s>>>(b.bv));
+  if (b.units[K_VERT] > 0) TC_LAUNCH("k_pmax", s, k_pmax<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
+  TC_LAUNCH("k_pmax_env", s, k_pmax_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
 }
 
 // trial point ut = u + alpha dx; alpha = min(1, TOI) when param < 0 (or no
