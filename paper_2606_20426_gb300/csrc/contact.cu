@@ -257,6 +257,13 @@ TC_D void contact_prim_points(const EnvView<R>& e, const R* u, int prim, double 
   *o = make_origin(bw[0]);
 }
 
+// Pairs per chunk of the pass with slots, and its dynamic shared memory.
+template <class R> constexpr int contact_chunk() { return sizeof(R) == 4 ? 512 : 256; }
+template <class R, int GK> constexpr size_t contact_smem() {
+  constexpr int NG = 3 * (GK == GV ? 1 : (GK == GE ? 2 : 3));
+  return (size_t)contact_chunk<R>() * (NG + NG * (NG + 1) / 2) * sizeof(R);
+}
+
 // One contact primitive pass over the candidate lists built by the last CCD
 // pass.  MODE 0: energy only; 1: energy + slots.  One unit = 128 gel
 // primitives; the unit's (primitive, candidate) pairs are flattened and
@@ -265,16 +272,17 @@ TC_D void contact_prim_points(const EnvView<R>& e, const R* u, int prim, double 
 // primitive then adds its pairs in candidate order (fixed-order sums, no
 // atomics) before rotating the sums to the world frame into the slots.
 template <class R, int GK, int MODE>
-__global__ void __launch_bounds__(MODE == 1 ? 128 : 512) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
+__global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int NG = 3 * NGP;
   constexpr int NH = NG * (NG + 1) / 2;
-  // threads: the energy-only pass has no per-pair scratch and spreads a
-  // unit's pairs over 512 threads; the pass with slots keeps 128
-  constexpr int NT = MODE == 1 ? 128 : 512;
-  constexpr int CH = MODE == 1 ? 512 / (int)sizeof(R) : NT;  // pairs per chunk
+  // a unit's pairs are spread over 512 threads; with slots, each pair's
+  // gradient and Hessian go through dynamic shared memory in chunks of CH
+  constexpr int NT = 512;
+  constexpr int CH = MODE == 1 ? contact_chunk<R>() : NT;  // pairs per chunk
   __shared__ int s_off[129];
-  __shared__ R s_gh[MODE == 1 ? CH : 1][MODE == 1 ? NG + NH : 1];
+  extern __shared__ __align__(16) unsigned char s_dyn_contact[];
+  R(*s_gh)[NG + NH] = reinterpret_cast<R(*)[NG + NH]>(s_dyn_contact);
   __shared__ Origin s_o[128];
   __shared__ Vec3<R> s_xg[128][NGP];
   const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
@@ -421,9 +429,16 @@ template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, 
   const int t = trial ? 1 : 0;
   const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
   if (hess) {
-    if (nv) TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<nv, 128, 0, s>>>(b.bv, b.L, t));
-    if (ne) TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<ne, 128, 0, s>>>(b.bv, b.L, t));
-    if (nf) TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<nf, 128, 0, s>>>(b.bv, b.L, t));
+    static const bool smem_set = [] {
+      cudaFuncSetAttribute(k_contact<R, GV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GV>());
+      cudaFuncSetAttribute(k_contact<R, GE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GE>());
+      cudaFuncSetAttribute(k_contact<R, GF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GF>());
+      return true;
+    }();
+    (void)smem_set;
+    if (nv) TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<nv, 512, contact_smem<R, GV>(), s>>>(b.bv, b.L, t));
+    if (ne) TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<ne, 512, contact_smem<R, GE>(), s>>>(b.bv, b.L, t));
+    if (nf) TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<nf, 512, contact_smem<R, GF>(), s>>>(b.bv, b.L, t));
   } else {
     if (nv) TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<nv, 512, 0, s>>>(b.bv, b.L, t));
     if (ne) TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<ne, 512, 0, s>>>(b.bv, b.L, t));
