@@ -132,6 +132,54 @@ template <class R, class F> TC_D void grid_visit(const EnvView<R>& e, int ik, co
       }
 }
 
+// The same visit by a group of NL consecutive lanes that share one query box:
+// the lanes take a cell's items NL at a time and a ballot over the group
+// compacts the hits, so write(pos, prim) receives the primitives in exactly
+// the order of grid_visit.  Every lane of the group must call it.  Returns the
+// number of primitives found.
+template <int NL, class R, class W>
+TC_D int grid_collect(const EnvView<R>& e, int ik, const float* lo, const float* hi, W write) {
+  const GridView& g = e.grid;
+  const float cell = 1.0f / g.inv_cell;
+  for (int d = 0; d < 3; ++d)
+    if (hi[d] < g.org[d] || lo[d] > g.org[d] + g.dims[d] * cell) return 0;
+  const int lane = (int)(threadIdx.x & 31) % NL;
+  const int base = (int)(threadIdx.x & 31) - lane;
+  const unsigned gmask = ((NL == 32) ? 0xffffffffu : ((1u << NL) - 1u)) << base;
+  int c0[3], c1[3];
+  for (int d = 0; d < 3; ++d) {
+    c0[d] = grid_cell(lo[d], g.org[d], g.inv_cell, g.dims[d]);
+    c1[d] = grid_cell(hi[d], g.org[d], g.inv_cell, g.dims[d]);
+  }
+  const int32_t* start = g.start[ik];
+  const int32_t* items = g.items[ik];
+  const float* box = g.box[ik];
+  int cnt = 0;
+  for (int z = c0[2]; z <= c1[2]; ++z)
+    for (int y = c0[1]; y <= c1[1]; ++y)
+      for (int x = c0[0]; x <= c1[0]; ++x) {
+        const int cell_id = x + g.dims[0] * (y + g.dims[1] * z);
+        const int k0 = start[cell_id], k1 = start[cell_id + 1];
+        for (int kb = k0; kb < k1; kb += NL) {
+          const int k = kb + lane;
+          bool hit = false;
+          int p = -1;
+          if (k < k1) {
+            p = items[k];
+            const float* b = box + 6 * (int64_t)p;
+            hit = !(b[0] > hi[0] || b[1] > hi[1] || b[2] > hi[2] || b[3] < lo[0] || b[4] < lo[1] || b[5] < lo[2]) &&
+                  grid_cell(fmaxf(lo[0], b[0]), g.org[0], g.inv_cell, g.dims[0]) == x &&
+                  grid_cell(fmaxf(lo[1], b[1]), g.org[1], g.inv_cell, g.dims[1]) == y &&
+                  grid_cell(fmaxf(lo[2], b[2]), g.org[2], g.inv_cell, g.dims[2]) == z;
+          }
+          const unsigned gm = (__ballot_sync(gmask, hit) & gmask) >> base;
+          if (hit) write(cnt + __popc(gm & ((1u << lane) - 1u)), p);
+          cnt += __popc(gm);
+        }
+      }
+  return cnt;
+}
+
 // Mollifier of an edge-edge pair in its dimensionless argument
 // t = c / eps_x, c = |(x1-x0) x (x3-x2)|^2: m(t) = (2 - t) t for t < 1, its
 // first two derivatives in t, and grad t on the gel edge (points 0, 1).
@@ -521,9 +569,10 @@ TC_D void ccd_prim_box32(const EnvView<R>& e, const Motion& mo, const R* dir, in
 // and the narrow phase runs all threads of the block over the unit's
 // flattened (primitive, candidate) pairs: additive CCD per pair, so the few
 // primitives near the indenter do not serialise the block.
-// A unit's 128 primitives run the broad phase on the first 128 threads; all
+// A unit's 128 primitives run the broad phase on kCcdLanes lanes each; all
 // kCcdThreads share its narrow phase.
 constexpr int kCcdThreads = 512;
+constexpr int kCcdLanes = kCcdThreads / 128;
 
 template <class R, int GK>
 __global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, PartLayout L) {
@@ -540,34 +589,38 @@ __global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, Part
   const int base = lc.chunk * 128;
   const int n = prim_count(e, GK);
   int32_t* cl = e.cand[GK];
+  // broad phase: kCcdLanes consecutive lanes per primitive share its grid
+  // visit (same candidate order as one thread alone)
+  const int pl = (int)threadIdx.x / kCcdLanes;  // primitive of the unit
+  const int prim = base + pl;
   int kept = 0;
-  if (threadIdx.x < 128 && base + (int)threadIdx.x < n) {
-    const int prim = base + threadIdx.x;
+  if (prim < n) {
     float lo[3], hi[3];
     ccd_prim_box32<R, GK>(e, mo, dir, prim, lo, hi);
-    int cnt = 0;
-    grid_visit<R>(e, ik, lo, hi, [&](int ip) {
-      if (cnt < e.cand_cap) cl[(int64_t)cnt * n + prim] = ip;
-      ++cnt;
+    const int cap = e.cand_cap;
+    const int cnt = grid_collect<kCcdLanes, R>(e, ik, lo, hi, [&](int pos, int ip) {
+      if (pos < cap) cl[(int64_t)pos * n + prim] = ip;
     });
-    e.cand_n[GK][prim] = cnt;
-    if (cnt > e.cand_cap) atomicMax(&e.sc->overflow, cnt);
-    kept = cnt < e.cand_cap ? cnt : e.cand_cap;
-    if (kept > 0) {
-      double b0[3][3], b1[3][3];
-      float blo[3], bhi[3];
-      ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, blo, bhi);
-      const Origin o = make_origin(b0[0]);
-      s_o[threadIdx.x] = o;
-      for (int l = 0; l < NGP; ++l) {
-        s_xg[threadIdx.x][l] = rel<R>(b0[l], o.d);
-        s_pg[threadIdx.x][l] = rel<R>(b1[l], b0[l]);
+    kept = cnt < cap ? cnt : cap;
+    if ((int)threadIdx.x % kCcdLanes == 0) {
+      e.cand_n[GK][prim] = cnt;
+      if (cnt > cap) atomicMax(&e.sc->overflow, cnt);
+      if (kept > 0) {
+        double b0[3][3], b1[3][3];
+        float blo[3], bhi[3];
+        ccd_prim_geom<R, GK>(e, mo, dir, prim, b0, b1, blo, bhi);
+        const Origin o = make_origin(b0[0]);
+        s_o[pl] = o;
+        for (int l = 0; l < NGP; ++l) {
+          s_xg[pl][l] = rel<R>(b0[l], o.d);
+          s_pg[pl][l] = rel<R>(b1[l], b0[l]);
+        }
       }
     }
   }
-  // exclusive prefix of the kept counts (128 threads, fixed order)
+  // exclusive prefix of the kept counts (128 primitives, fixed order)
   if (threadIdx.x == 0) s_off[0] = 0;
-  if (threadIdx.x < 128) s_off[threadIdx.x + 1] = kept;
+  if ((int)threadIdx.x % kCcdLanes == 0) s_off[pl + 1] = kept;
   __syncthreads();
   if (threadIdx.x == 0)
     for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
