@@ -66,7 +66,7 @@ template <class R> static tc_status alloc_state(Env& env) {
     *p = a.alloc<R>(n);
     return *p != nullptr;
   };
-  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.utrial, 3 * nv) && A(&env.kblk, 90 * nt) &&
+  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.utrial, 3 * nv) && A(&env.kblk, kblk_size(nt)) &&
             A(&env.eslot, 12 * nt) && A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) &&
             A(&env.Minv, 6 * nv) &&
             A(&env.dx, 3 * nv) && A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) &&

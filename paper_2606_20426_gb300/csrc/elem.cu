@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
         n[3][j] = Bm[2][j];
         n[0][j] = -(Bm[0][j] + Bm[1][j] + Bm[2][j]);
       }
-      R* K = e.kblk + (int64_t)el * 90;
+      R* K = e.kblk;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
           for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = a; b < 4; ++b) {
-              K[pidx * 9 + 3 * i + kk] = V * (n[a][0] * T[0][b] + n[a][1] * T[1][b] + n[a][2] * T[2][b]);
+              K[kblk_index(el, pidx * 9 + 3 * i + kk)] = V * (n[a][0] * T[0][b] + n[a][1] * T[1][b] + n[a][2] * T[2][b]);
               ++pidx;
             }
         }

@@ -44,6 +44,16 @@ TC_HD int grid_cell(float x, float org, float inv_cell, int dim) {
   return c;
 }
 
+// Entry q (0..89) of tet el's stiffness blocks: groups of 8 consecutive tets
+// store each entry contiguously, so a warp writing entry q of 32 tets fills
+// four 32-byte sectors, while the 9 entries of one block of one tet stay
+// within 288 bytes for the assembly gather.
+constexpr int kKblkGroup = 8;
+TC_HD int64_t kblk_index(int el, int q) {
+  return ((int64_t)(el / kKblkGroup) * 90 + q) * kKblkGroup + (el % kKblkGroup);
+}
+TC_HD int64_t kblk_size(int nt) { return (int64_t)90 * ((nt + kKblkGroup - 1) / kKblkGroup) * kKblkGroup; }
+
 // Everything a kernel needs, passed by value.
 template <class R> struct EnvView {
   int nv, nt, nfc, nec, nvc, ind_nv, ind_nf, ind_ne, npix;
@@ -61,8 +71,9 @@ template <class R> struct EnvView {
   const R* Dminv;             // 9 x nt (row-major entry k at k*nt + e)
   const R* vol;
   R* eslot;                   // 12 x nt element gradient per (corner, component)
-  R* kblk;                    // nt x 10 x 9: the element's PSD 12x12 stiffness as its 10
-                              // upper 3x3 corner blocks (a <= b, row-major), tet-major
+  R* kblk;                    // the element's PSD 12x12 stiffness as its 10 upper 3x3
+                              // corner blocks (a <= b, row-major): 90 entries per tet,
+                              // interleaved by groups of 8 tets (kblk_index)
   // per vertex
   const R* mass;              // nv (dynamic) or null
   R* u;                       // 3 x nv displacement

@@ -126,14 +126,14 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, Part
       for (int c = e.be_off[k]; c < e.be_off[k + 1]; ++c) {
         const int code = e.be_idx[c];
         const int t = code >> 4, a = (code >> 2) & 3, b = code & 3;
-        const R* K = e.kblk + (int64_t)t * 90;
+        const R* K = e.kblk;
         if (a <= b) {
-          const R* Kb = K + 9 * pair_index(a, b);
-          for (int q = 0; q < 9; ++q) B[q] += Kb[q];
+          const int q0 = 9 * pair_index(a, b);
+          for (int q = 0; q < 9; ++q) B[q] += K[kblk_index(t, q0 + q)];
         } else {
-          const R* Kb = K + 9 * pair_index(b, a);
+          const int q0 = 9 * pair_index(b, a);
           for (int r = 0; r < 3; ++r)
-            for (int cc = 0; cc < 3; ++cc) B[3 * r + cc] += Kb[3 * cc + r];
+            for (int cc = 0; cc < 3; ++cc) B[3 * r + cc] += K[kblk_index(t, q0 + 3 * cc + r)];
         }
       }
       for (int c = e.bc_off[k]; c < e.bc_off[k + 1]; ++c) add_contact_block<R>(e, (uint32_t)e.bc_idx[c], B);
