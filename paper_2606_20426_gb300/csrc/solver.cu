@@ -346,6 +346,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
 // halo does not fit the shared-memory budget the SpMV forms p = z + beta p of
 // the neighbours from HBM instead.  Results do not depend on the other envs.
 constexpr int kPcgMaxChunks = 256;
+template <class R> constexpr int kPcgUnroll = sizeof(R) == 4 ? 2 : 1;
 
 template <class R, int kPcgThreads>
 __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
@@ -446,24 +447,42 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
       const int ka = rp[ra], kb = rp[rb];
       const bool fits = kb - ka <= ycap;
       if (fits) {
-        for (int k = ka + (int)threadIdx.x; k < kb; k += kPcgThreads) {
-          const int j = ci[k];
-          R p0, p1, p2;
-          if (staged) {
-            const int l = j - cmin;
-            p0 = sp[l];
-            p1 = sp[H + l];
-            p2 = sp[2 * H + l];
-          } else {
-            p0 = z[j] + beta * pc[j];
-            p1 = z[nv + j] + beta * pc[nv + j];
-            p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
+        // kPcgUnroll<R> blocks per thread and pass: all their loads are issued
+        // before the first product, so a pass waits on L2 once
+        for (int k0 = ka + (int)threadIdx.x; k0 < kb; k0 += kPcgUnroll<R> * kPcgThreads) {
+          int jj[kPcgUnroll<R>];
+          R Bv[kPcgUnroll<R>][9];
+#pragma unroll
+          for (int u = 0; u < kPcgUnroll<R>; ++u) {
+            const int k = k0 + u * kPcgThreads;
+            if (k < kb) {
+              jj[u] = ci[k];
+#pragma unroll
+              for (int e9 = 0; e9 < 9; ++e9) Bv[u][e9] = val[k + e9 * nb];
+            }
           }
-          const R* B = val + k;
-          const int o = k - ka;
-          sy[o] = B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
-          sy[ycap + o] = B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
-          sy[2 * ycap + o] = B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
+#pragma unroll
+          for (int u = 0; u < kPcgUnroll<R>; ++u) {
+            const int k = k0 + u * kPcgThreads;
+            if (k >= kb) break;
+            const int j = jj[u];
+            R p0, p1, p2;
+            if (staged) {
+              const int l = j - cmin;
+              p0 = sp[l];
+              p1 = sp[H + l];
+              p2 = sp[2 * H + l];
+            } else {
+              p0 = z[j] + beta * pc[j];
+              p1 = z[nv + j] + beta * pc[nv + j];
+              p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
+            }
+            const R* B = Bv[u];
+            const int o = k - ka;
+            sy[o] = B[0] * p0 + B[1] * p1 + B[2] * p2;
+            sy[ycap + o] = B[3] * p0 + B[4] * p1 + B[5] * p2;
+            sy[2 * ycap + o] = B[6] * p0 + B[7] * p1 + B[8] * p2;
+          }
         }
         __syncthreads();
       }
