@@ -329,7 +329,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
 // cluster (16 CTAs where the GPU co-schedules them, else 8; 1024 threads
 // each) over a contiguous share of the env's rows, so envs iterate
 // independently: an env that converges frees its SMs at once, and no
-// grid-wide barrier ties envs together.  Per iteration, two cluster barriers:
+// grid-wide barrier ties envs together.  The rows are split so that every
+// CTA holds about the same number of matrix blocks.  Per iteration, two
+// cluster barriers:
 //   S  p = z + beta p over the CTA's halo (the columns its rows touch),
 //      staged in shared memory; the CTA's own rows also go to the next p
 //      buffer in HBM (two buffers alternate, so no CTA overwrites values
@@ -338,15 +340,101 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
 //      thread per row adds its blocks in order; p.q                 | barrier
 //   B  alpha = r.z / p.q, dx += alpha p, r -= alpha q, z = M^-1 r;
 //      r.z, r.r                                                     | barrier
+// Resident mode (the usual case): when the halo, the CTA's block products
+// and its free rows' r, z, dx, q and M^-1 all fit in shared memory, those
+// vectors stay there for the whole solve and only z and p are published to
+// HBM for the neighbours' halos; rows of fixed vertices (empty rows) are
+// skipped through a list of the free rows.  Otherwise every vector lives in
+// HBM and the rows are walked in chunks that fit the product buffer.
 // Dot products accumulate in double-float pairs (FP64 issues at a small
 // fraction of the FP32 rate on this part) with fixed reduction trees; each
-// CTA posts its partials in shared memory and thread 0 of every CTA adds the
-// posts of all ranks in the same order through distributed shared memory, so
-// every CTA derives bit-identical alpha, beta and stop decisions.  When the
-// halo does not fit the shared-memory budget the SpMV forms p = z + beta p of
-// the neighbours from HBM instead.  Results do not depend on the other envs.
+// CTA pushes its partials into a slot of every CTA's shared memory before
+// the cluster barrier, and every CTA adds the slots of all ranks in the same
+// order, so all derive bit-identical alpha, beta and stop decisions.  When
+// the halo does not fit the shared-memory budget the SpMV forms p = z + beta
+// p of the neighbours from HBM instead.  Results do not depend on the other
+// envs.
 constexpr int kPcgMaxChunks = 256;
+constexpr int kPcgMaxCluster = 16;
+// blocks per thread and pass of the SpMV: all their loads are issued before
+// the first product, so a pass waits on L2 once
 template <class R> constexpr int kPcgUnroll = sizeof(R) == 4 ? 2 : 1;
+
+// Rows [r0, r1) of cluster rank `rank`: rank k starts at the first row r
+// whose block offset rp[r] reaches k nnzb / CS, so every rank holds about the
+// same number of blocks and fixed vertices (empty rows) cost nothing.  Rank
+// 0 starts at row 0 and the last rank ends at row nv.  Two rounds of
+// parallel search over the row pointers; s_w holds 4 ints of scratch.
+template <int NT>
+TC_D void pcg_rows(const int32_t* __restrict__ rp, int nv, int CS, int rank, int* s_w, int& r0, int& r1) {
+  const int64_t wtot = rp[nv];
+  const int64_t tgt[2] = {wtot * rank / CS, wtot * (rank + 1) / CS};
+  const int s1 = (nv + NT) / NT;  // NT * s1 >= nv + 1
+  if (threadIdx.x < 2) {
+    s_w[threadIdx.x] = 0;
+    s_w[2 + threadIdx.x] = nv;
+  }
+  __syncthreads();
+  {
+    // coarse: the last sample row c s1 whose offset is below the target
+    const int rc = min(nv, (int)threadIdx.x * s1);
+    const int64_t wc = rp[rc];
+    for (int b = 0; b < 2; ++b)
+      if (wc < tgt[b]) atomicMax(&s_w[b], (int)threadIdx.x);
+  }
+  __syncthreads();
+  // fine: the first row reaching the target among c s1 .. (c + 1) s1
+  for (int b = 0; b < 2; ++b) {
+    const int lo = s_w[b] * s1;
+    for (int j = (int)threadIdx.x; j <= s1; j += NT) {
+      const int r = min(nv, lo + j);
+      if ((int64_t)rp[r] >= tgt[b]) atomicMin(&s_w[2 + b], r);
+    }
+  }
+  __syncthreads();
+  r0 = rank == 0 ? 0 : s_w[2];
+  r1 = rank == CS - 1 ? nv : s_w[3];
+}
+
+// Block sums of NV accumulators (fixed tree) pushed into slot
+// s_all[rank][slot + k] of every CTA of the cluster; the cluster barrier that
+// follows makes them visible.  Ends without a block barrier: s_red is next
+// written after that cluster barrier.
+template <class R, int NV>
+TC_D void cluster_push(typename Acc<R>::T* v, typename Acc<R>::T (*s_red)[32], typename Acc<R>::T (*s_all)[3],
+                       int slot, cg::cluster_group& cluster, int rank, int CS) {
+  using A = Acc<R>;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    typename A::T x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+    if (lane == 0) s_red[k][w] = x;
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      typename A::T x = lane < (int)(blockDim.x >> 5) ? s_red[k][lane] : A::zero();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+      if (lane < CS) cluster.map_shared_rank(&s_all[rank][slot + k], lane)[0] = x;
+    }
+  }
+}
+
+// Sum over ranks of slot `slot` (warp 0; fixed tree, the same in every CTA).
+template <class R> TC_D typename Acc<R>::T cluster_total(typename Acc<R>::T (*s_all)[3], int slot, int CS) {
+  using A = Acc<R>;
+  const int lane = threadIdx.x & 31;
+  typename A::T x = lane < CS ? s_all[lane][slot] : A::zero();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+  return x;
+}
+
+TC_D size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <class R, int kPcgThreads>
 __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
@@ -355,16 +443,21 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   using AT = typename A::T;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ AT s_red[3][32];
-  __shared__ AT s_post[3];
+  __shared__ AT s_all[kPcgMaxCluster][3];  // [rank][0 p.q, 1 r.z, 2 r.r]
   __shared__ R s_coef;
   __shared__ int s_flag;
   __shared__ int s_chunk[kPcgMaxChunks + 1];
   __shared__ int s_nchunk;
   __shared__ int s_lohi[2];
+  __shared__ int s_rows[4];
+  __shared__ int s_nfree;
+  __shared__ int s_wcnt[32];
+  __shared__ double s_sc[4];  // r.z, r.r, p.q, squared tolerance (thread 0)
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
   const int env = blockIdx.x / CS;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const EnvView<R>& ev = bv.views[env];
   const int nv = ev.nv;
   const int64_t nb = ev.nnzb;
@@ -377,35 +470,60 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   R* z = ev.z;
   R* dx = ev.dx;
   R* pbuf[2] = {ev.p, ev.p2};
-  const int r0 = (int)((int64_t)nv * rank / CS), r1 = (int)((int64_t)nv * (rank + 1) / CS);
-  // halo of the CTA's rows
+  int r0, r1;
+  pcg_rows<kPcgThreads>(rp, nv, CS, rank, s_rows, r0, r1);
+  // halo of the CTA's rows (columns within a row ascend, so its first and
+  // last blocks bound it) and its number of free rows
   if (threadIdx.x == 0) {
     s_lohi[0] = r0;
     s_lohi[1] = r1 - 1;
+    s_nfree = 0;
   }
   __syncthreads();
   {
-    int lo = r0, hi = r1 - 1;
-    for (int k = rp[r0] + (int)threadIdx.x; k < rp[r1]; k += kPcgThreads) {
-      const int j = ci[k];
-      lo = min(lo, j);
-      hi = max(hi, j);
+    int lo = r0, hi = r1 - 1, nfl = 0;
+    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
+      const int ka = rp[v], kb = rp[v + 1];
+      if (kb > ka) {
+        lo = min(lo, ci[ka]);
+        hi = max(hi, ci[kb - 1]);
+        ++nfl;
+      }
     }
     if (r1 > r0) {
       atomicMin(&s_lohi[0], lo);
       atomicMax(&s_lohi[1], hi);
     }
+    if (nfl) atomicAdd(&s_nfree, nfl);
   }
   __syncthreads();
   const int cmin = s_lohi[0];
   const int H = r1 > r0 ? s_lohi[1] - cmin + 1 : 0;
-  const size_t stage_bytes = ((size_t)3 * H * sizeof(R) + 15) & ~(size_t)15;
-  const bool staged = stage_bytes <= (size_t)smem_bytes / 2;
+  const int nf = s_nfree;
+  const int ka0 = rp[r0], nblk = rp[r1] - ka0;
+  // shared memory: halo p | resident vectors and row lists | block products
+  const size_t stage_bytes = align16((size_t)3 * H * sizeof(R));
+  const size_t vec_bytes = align16((size_t)18 * nf * sizeof(R));
+  const size_t lst_bytes = align16((size_t)(2 * nf + 1) * sizeof(int));
+  const bool res = r1 > r0 && stage_bytes + vec_bytes + lst_bytes + (size_t)3 * nblk * sizeof(R) <= (size_t)smem_bytes;
+  const bool staged = res || stage_bytes <= (size_t)smem_bytes / 2;
   R* sp = reinterpret_cast<R*>(s_dyn);
-  R* sy = reinterpret_cast<R*>(s_dyn + (staged ? stage_bytes : 0));
-  const int ycap = (int)((smem_bytes - (staged ? stage_bytes : 0)) / (3 * sizeof(R)));
+  const size_t y_off = staged ? stage_bytes + (res ? vec_bytes + lst_bytes : 0) : 0;
+  R* rs = reinterpret_cast<R*>(s_dyn + stage_bytes);  // resident: r, z, dx, q (3 nf each), M^-1 (6 nf)
+  R* zs = rs + 3 * nf;
+  R* dxs = zs + 3 * nf;
+  R* qs = dxs + 3 * nf;
+  R* ms = qs + 3 * nf;
+  int* lst = reinterpret_cast<int*>(s_dyn + stage_bytes + vec_bytes);  // free rows, ascending
+  int* rps = lst + nf;  // their first block (from ka0); rps[nf] = nblk
+  R* sy = reinterpret_cast<R*>(s_dyn + y_off);
+  const int ycap = (int)((smem_bytes - y_off) / (3 * sizeof(R)));
   // row chunks of at most ycap blocks (a longer row forms a chunk of its own)
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && nblk <= ycap) {  // the usual case: one chunk
+    s_chunk[0] = r0;
+    s_chunk[1] = r1;
+    s_nchunk = r1 > r0 ? 1 : 0;
+  } else if (threadIdx.x == 0) {
     int n = 0, a = r0;
     s_chunk[0] = r0;
     while (a < r1 && n < kPcgMaxChunks) {
@@ -417,11 +535,58 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     }
     s_nchunk = n;
   }
-  __syncthreads();
+  if (res) {
+    // list of the free rows in ascending order (ordered compaction)
+    int base = 0;
+    for (int v0 = r0; v0 < r1; v0 += kPcgThreads) {
+      const int v = v0 + (int)threadIdx.x;
+      int ka = 0;
+      bool f = false;
+      if (v < r1) {
+        ka = rp[v];
+        f = rp[v + 1] > ka;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) s_wcnt[wid] = __popc(m);
+      __syncthreads();
+      int off = base, tot = 0;
+      for (int w = 0; w < kPcgThreads / 32; ++w) {
+        const int c = s_wcnt[w];
+        off += w < wid ? c : 0;
+        tot += c;
+      }
+      if (f) {
+        const int idx = off + __popc(m & ((1u << lane) - 1u));
+        lst[idx] = v;
+        rps[idx] = ka - ka0;
+      }
+      base += tot;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) rps[nf] = nblk;
+    for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
+      const int v = lst[idx];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        rs[i * nf + idx] = r[i * nv + v];
+        zs[i * nf + idx] = z[i * nv + v];
+        dxs[i * nf + idx] = dx[i * nv + v];
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i) ms[i * nf + idx] = Minv[i * nv + v];
+    }
+  }
+  // every CTA of the cluster runs (and has set up its shared memory) before
+  // the first partials are pushed into it
+  cluster.sync();
   const int nchunk = s_nchunk;
   const double* es = bv.part + L.env_s + kEnvScalars * env;
-  double rz = es[0], rr = es[1], pq = 0.0;  // thread 0's copies are the ones used
-  const double tol2 = es[4];
+  if (threadIdx.x == 0) {
+    s_sc[0] = es[0];
+    s_sc[1] = es[1];
+    s_sc[2] = 0.0;
+    s_sc[3] = es[4];
+  }
   bool done = es[2] != 0.0;
   R beta = R(0);
   int it = 0;
@@ -429,14 +594,34 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     const R* pc = pbuf[it & 1];
     R* pn = pbuf[(it + 1) & 1];
     // S. direction update over the halo (or the own rows)
-    const int s0 = staged ? cmin : r0, s1 = staged ? cmin + H : r1;
-    for (int v = s0 + (int)threadIdx.x; v < s1; v += kPcgThreads) {
-      const bool own = v >= r0 && v < r1;
+    if (res) {
+      // the neighbours' halo rows from HBM
+      const int nlo = r0 - cmin, nother = H - (r1 - r0);
+      for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+        const int v = j < nlo ? cmin + j : r1 + (j - nlo);
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const R x = z[i * nv + v] + beta * pc[i * nv + v];
-        if (staged) sp[i * H + (v - cmin)] = x;
-        if (own) pn[i * nv + v] = x;
+        for (int i = 0; i < 3; ++i) sp[i * H + (v - cmin)] = z[i * nv + v] + beta * pc[i * nv + v];
+      }
+      // the own free rows from shared memory
+      for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
+        const int v = lst[idx], l = v - cmin;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const R x = it == 0 ? zs[i * nf + idx] : zs[i * nf + idx] + beta * sp[i * H + l];
+          sp[i * H + l] = x;
+          pn[i * nv + v] = x;
+        }
+      }
+    } else {
+      const int s0 = staged ? cmin : r0, s1 = staged ? cmin + H : r1;
+      for (int v = s0 + (int)threadIdx.x; v < s1; v += kPcgThreads) {
+        const bool own = v >= r0 && v < r1;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const R x = z[i * nv + v] + beta * pc[i * nv + v];
+          if (staged) sp[i * H + (v - cmin)] = x;
+          if (own) pn[i * nv + v] = x;
+        }
       }
     }
     __syncthreads();
@@ -447,8 +632,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
       const int ka = rp[ra], kb = rp[rb];
       const bool fits = kb - ka <= ycap;
       if (fits) {
-        // kPcgUnroll<R> blocks per thread and pass: all their loads are issued
-        // before the first product, so a pass waits on L2 once
         for (int k0 = ka + (int)threadIdx.x; k0 < kb; k0 += kPcgUnroll<R> * kPcgThreads) {
           int jj[kPcgUnroll<R>];
           R Bv[kPcgUnroll<R>][9];
@@ -485,6 +668,23 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
           }
         }
         __syncthreads();
+      }
+      if (res) {
+        for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
+          R a0 = 0, a1 = 0, a2 = 0;
+          const int k1 = rps[idx + 1];
+          for (int k = rps[idx]; k < k1; ++k) {
+            a0 += sy[k];
+            a1 += sy[ycap + k];
+            a2 += sy[2 * ycap + k];
+          }
+          qs[idx] = a0;
+          qs[nf + idx] = a1;
+          qs[2 * nf + idx] = a2;
+          const int l = lst[idx] - cmin;
+          pq_loc = A::add(pq_loc, A::add(A::add(A::prod(sp[l], a0), A::prod(sp[H + l], a1)), A::prod(sp[2 * H + l], a2)));
+        }
+        continue;  // one chunk; the block products are next written after two cluster barriers
       }
       for (int v = ra + (int)threadIdx.x; v < rb; v += kPcgThreads) {
         R a0 = 0, a1 = 0, a2 = 0;
@@ -524,61 +724,75 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
       }
       __syncthreads();
     }
-    block_acc_sum<R, 1>(&pq_loc, s_red);
-    if (threadIdx.x == 0) s_post[0] = s_red[0][0];
+    cluster_push<R, 1>(&pq_loc, s_red, s_all, 0, cluster, rank, CS);
     cluster.sync();
-    if (threadIdx.x < 32) {
-      AT x = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[0] : A::zero();
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x = A::add(x, A::shfl_xor(x, o));
+    if (wid == 0) {
+      const AT x = cluster_total<R>(s_all, 0, CS);
       if (threadIdx.x == 0) {
-        pq = A::to_double(x);
-        s_coef = (R)(pq > 0.0 ? rz / pq : 0.0);
+        const double pq = A::to_double(x);
+        s_sc[2] = pq;
+        s_coef = (R)(pq > 0.0 ? s_sc[0] / pq : 0.0);
       }
     }
     __syncthreads();
     const R alpha = s_coef;
     // B. vector update
     AT acc[2] = {A::zero(), A::zero()};
-    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
-      R rv[3], zv[3];
-      for (int i = 0; i < 3; ++i) {
-        const R pv = staged ? sp[i * H + (v - cmin)] : pn[i * nv + v];
-        dx[i * nv + v] += alpha * pv;
-        rv[i] = r[i * nv + v] - alpha * q[i * nv + v];
-        r[i * nv + v] = rv[i];
-      }
-      const R m0 = Minv[v], m1 = Minv[nv + v], m2 = Minv[2 * nv + v];
-      const R m3 = Minv[3 * nv + v], m4 = Minv[4 * nv + v], m5 = Minv[5 * nv + v];
-      zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
-      zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
-      zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
-      for (int i = 0; i < 3; ++i) {
-        z[i * nv + v] = zv[i];
-        acc[0] = A::add(acc[0], A::prod(rv[i], zv[i]));
-        acc[1] = A::add(acc[1], A::prod(rv[i], rv[i]));
-      }
-    }
-    block_acc_sum<R, 2>(acc, s_red);
-    if (threadIdx.x == 0) {
-      s_post[1] = s_red[0][0];
-      s_post[2] = s_red[1][0];
-    }
-    cluster.sync();
-    if (threadIdx.x < 32) {
-      AT x = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[1] : A::zero();
-      AT y = (int)threadIdx.x < CS ? cluster.map_shared_rank(s_post, threadIdx.x)[2] : A::zero();
+    if (res) {
+      for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
+        const int v = lst[idx], l = v - cmin;
+        R rv[3], zv[3];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        x = A::add(x, A::shfl_xor(x, o));
-        y = A::add(y, A::shfl_xor(y, o));
+        for (int i = 0; i < 3; ++i) {
+          dxs[i * nf + idx] += alpha * sp[i * H + l];
+          rv[i] = rs[i * nf + idx] - alpha * qs[i * nf + idx];
+          rs[i * nf + idx] = rv[i];
+        }
+        const R m0 = ms[idx], m1 = ms[nf + idx], m2 = ms[2 * nf + idx];
+        const R m3 = ms[3 * nf + idx], m4 = ms[4 * nf + idx], m5 = ms[5 * nf + idx];
+        zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
+        zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
+        zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          zs[i * nf + idx] = zv[i];
+          z[i * nv + v] = zv[i];
+          acc[0] = A::add(acc[0], A::prod(rv[i], zv[i]));
+          acc[1] = A::add(acc[1], A::prod(rv[i], rv[i]));
+        }
       }
+    } else {
+      for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
+        R rv[3], zv[3];
+        for (int i = 0; i < 3; ++i) {
+          const R pv = staged ? sp[i * H + (v - cmin)] : pn[i * nv + v];
+          dx[i * nv + v] += alpha * pv;
+          rv[i] = r[i * nv + v] - alpha * q[i * nv + v];
+          r[i * nv + v] = rv[i];
+        }
+        const R m0 = Minv[v], m1 = Minv[nv + v], m2 = Minv[2 * nv + v];
+        const R m3 = Minv[3 * nv + v], m4 = Minv[4 * nv + v], m5 = Minv[5 * nv + v];
+        zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
+        zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
+        zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
+        for (int i = 0; i < 3; ++i) {
+          z[i * nv + v] = zv[i];
+          acc[0] = A::add(acc[0], A::prod(rv[i], zv[i]));
+          acc[1] = A::add(acc[1], A::prod(rv[i], rv[i]));
+        }
+      }
+    }
+    cluster_push<R, 2>(acc, s_red, s_all, 1, cluster, rank, CS);
+    cluster.sync();
+    if (wid == 0) {
+      const AT x = cluster_total<R>(s_all, 1, CS);
+      const AT y = cluster_total<R>(s_all, 2, CS);
       if (threadIdx.x == 0) {
-        const double rz_new = A::to_double(x);
-        rr = A::to_double(y);
+        const double rz = s_sc[0], rz_new = A::to_double(x), rr = A::to_double(y), pq = s_sc[2];
         s_coef = (R)(rz > 0.0 ? rz_new / rz : 0.0);
-        rz = rz_new;
-        s_flag = (rr <= tol2 || !(pq > 0.0) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
+        s_sc[0] = rz_new;
+        s_sc[1] = rr;
+        s_flag = (rr <= s_sc[3] || !(pq > 0.0) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -587,17 +801,24 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     ++it;
     __syncthreads();  // s_coef / s_flag are rewritten in the next iteration
   }
+  if (res)
+    for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
+      const int v = lst[idx];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) dx[i * nv + v] = dxs[i * nf + idx];
+    }
   if (rank == 0 && threadIdx.x == 0) {
     Scalars* sc = ev.sc;
+    const double rr = s_sc[1], pq = s_sc[2];
     sc->pcg_iters = it;
-    sc->rz = rz;
+    sc->rz = s_sc[0];
     sc->rr = rr;
     sc->pq = pq;
-    sc->pcg_tol2 = tol2;
+    sc->pcg_tol2 = s_sc[3];
     sc->pcg_done = 1;
     if (!isfinite(rr) || !isfinite(pq)) sc->status |= ST_NONFINITE;
   }
-  // no CTA may leave while another can still read its shared memory
+  // no CTA may leave while another can still write into its shared memory
   cluster.sync();
 }
 
