@@ -103,6 +103,17 @@ TC_D DF df_prod(float a, float b) {
   const float p = a * b;
   return {p, fmaf(a, b, -p)};
 }
+// a / b rounded to float from double-float operands (b != 0): the quotient
+// of the leading parts, corrected once by the FMA residual of a - q b.
+TC_D float df_ratio(DF a, DF b) {
+  const float q0 = a.hi / b.hi;
+  const float e = fmaf(-q0, b.hi, a.hi) + (a.lo - q0 * b.lo);
+  return q0 + e / b.hi;
+}
+TC_D DF df_from_double(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
 TC_D DF df_shfl_xor(DF v, int o) {
   return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
@@ -116,6 +127,9 @@ template <> struct Acc<float> {
   static TC_D T add(T a, T b) { return df_add(a, b); }
   static TC_D T shfl_xor(T v, int o) { return df_shfl_xor(v, o); }
   static TC_D double to_double(T v) { return (double)v.hi + (double)v.lo; }
+  static TC_D T from_double(double x) { return df_from_double(x); }
+  static TC_D float ratio(T a, T b) { return df_ratio(a, b); }
+  static TC_D bool positive(T a) { return a.hi > 0.f; }
 };
 template <> struct Acc<double> {
   using T = double;
@@ -124,6 +138,9 @@ template <> struct Acc<double> {
   static TC_D T add(T a, T b) { return a + b; }
   static TC_D T shfl_xor(T v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
   static TC_D double to_double(T v) { return v; }
+  static TC_D T from_double(double x) { return x; }
+  static TC_D double ratio(T a, T b) { return a / b; }
+  static TC_D bool positive(T a) { return a > 0.0; }
 };
 
 // Block sums of NV accumulators per thread (fixed tree); totals in s[k][0]

@@ -350,7 +350,9 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
 // fraction of the FP32 rate on this part) with fixed reduction trees; each
 // CTA pushes its partials into a slot of every CTA's shared memory before
 // the cluster barrier, and every CTA adds the slots of all ranks in the same
-// order, so all derive bit-identical alpha, beta and stop decisions.  When
+// order, so all derive bit-identical alpha, beta and stop decisions (the
+// quotients are taken in float from the double-float sums with one residual
+// correction, so no FP64 division sits on the critical path).  When
 // the halo does not fit the shared-memory budget the SpMV forms p = z + beta
 // p of the neighbours from HBM instead.  Results do not depend on the other
 // envs.
@@ -452,7 +454,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   __shared__ int s_rows[4];
   __shared__ int s_nfree;
   __shared__ int s_wcnt[32];
-  __shared__ double s_sc[4];  // r.z, r.r, p.q, squared tolerance (thread 0)
+  __shared__ AT s_at[2];      // r.z, p.q (thread 0)
+  __shared__ double s_sc[2];  // r.r, squared tolerance (thread 0)
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
   const int rank = (int)cluster.block_rank();
@@ -582,10 +585,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   const int nchunk = s_nchunk;
   const double* es = bv.part + L.env_s + kEnvScalars * env;
   if (threadIdx.x == 0) {
-    s_sc[0] = es[0];
-    s_sc[1] = es[1];
-    s_sc[2] = 0.0;
-    s_sc[3] = es[4];
+    s_at[0] = A::from_double(es[0]);
+    s_at[1] = A::zero();
+    s_sc[0] = es[1];
+    s_sc[1] = es[4];
   }
   bool done = es[2] != 0.0;
   R beta = R(0);
@@ -729,9 +732,8 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     if (wid == 0) {
       const AT x = cluster_total<R>(s_all, 0, CS);
       if (threadIdx.x == 0) {
-        const double pq = A::to_double(x);
-        s_sc[2] = pq;
-        s_coef = (R)(pq > 0.0 ? s_sc[0] / pq : 0.0);
+        s_at[1] = x;
+        s_coef = A::positive(x) ? (R)A::ratio(s_at[0], x) : R(0);
       }
     }
     __syncthreads();
@@ -788,11 +790,11 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
       const AT x = cluster_total<R>(s_all, 1, CS);
       const AT y = cluster_total<R>(s_all, 2, CS);
       if (threadIdx.x == 0) {
-        const double rz = s_sc[0], rz_new = A::to_double(x), rr = A::to_double(y), pq = s_sc[2];
-        s_coef = (R)(rz > 0.0 ? rz_new / rz : 0.0);
-        s_sc[0] = rz_new;
-        s_sc[1] = rr;
-        s_flag = (rr <= s_sc[3] || !(pq > 0.0) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
+        const double rr = A::to_double(y);
+        s_coef = A::positive(s_at[0]) ? (R)A::ratio(x, s_at[0]) : R(0);
+        s_at[0] = x;
+        s_sc[0] = rr;
+        s_flag = (rr <= s_sc[1] || !A::positive(s_at[1]) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -809,12 +811,12 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     }
   if (rank == 0 && threadIdx.x == 0) {
     Scalars* sc = ev.sc;
-    const double rr = s_sc[1], pq = s_sc[2];
+    const double rr = s_sc[0], pq = A::to_double(s_at[1]);
     sc->pcg_iters = it;
-    sc->rz = s_sc[0];
+    sc->rz = A::to_double(s_at[0]);
     sc->rr = rr;
     sc->pq = pq;
-    sc->pcg_tol2 = s_sc[3];
+    sc->pcg_tol2 = s_sc[1];
     sc->pcg_done = 1;
     if (!isfinite(rr) || !isfinite(pq)) sc->status |= ST_NONFINITE;
   }
