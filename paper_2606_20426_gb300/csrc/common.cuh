@@ -118,6 +118,18 @@ TC_D DF df_shfl_xor(DF v, int o) {
   return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
+// Asynchronous global -> shared copy of one 4- or 8-byte word (no register
+// holds it in flight); complete once the issuing thread passes
+// cp_async_wait_all.
+template <class T> TC_D void cp_async_word(T* smem_dst, const T* gmem_src) {
+  static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte words");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const size_t g = __cvta_generic_to_global(gmem_src);
+  if (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(g) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(g) : "memory");
+}
+TC_D void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Accumulator of a precision: double-float for FP32 work, double for FP64.
 template <class R> struct Acc;
 template <> struct Acc<float> {

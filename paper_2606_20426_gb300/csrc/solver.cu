@@ -598,12 +598,32 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     R* pn = pbuf[(it + 1) & 1];
     // S. direction update over the halo (or the own rows)
     if (res) {
-      // the neighbours' halo rows from HBM
+      // the neighbours' halo rows from HBM: z into the halo buffer and the
+      // old p into the (idle) product buffer by asynchronous copies, so
+      // every load of the thread is in flight at once; each thread then
+      // combines the words it copied
       const int nlo = r0 - cmin, nother = H - (r1 - r0);
-      for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
-        const int v = j < nlo ? cmin + j : r1 + (j - nlo);
+      if (H <= ycap) {
+        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+          const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) sp[i * H + (v - cmin)] = z[i * nv + v] + beta * pc[i * nv + v];
+          for (int i = 0; i < 3; ++i) {
+            cp_async_word(&sp[i * H + l], &z[i * nv + v]);
+            cp_async_word(&sy[i * H + l], &pc[i * nv + v]);
+          }
+        }
+        cp_async_wait_all();
+        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+          const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) sp[i * H + l] = sp[i * H + l] + beta * sy[i * H + l];
+        }
+      } else {
+        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+          const int v = j < nlo ? cmin + j : r1 + (j - nlo);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) sp[i * H + (v - cmin)] = z[i * nv + v] + beta * pc[i * nv + v];
+        }
       }
       // the own free rows from shared memory
       for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
