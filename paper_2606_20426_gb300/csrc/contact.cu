@@ -319,6 +319,32 @@ template <class R, int GK> constexpr size_t contact_smem() {
 // writes its gradient and Hessian to shared memory, and the thread owning a
 // primitive then adds its pairs in candidate order (fixed-order sums, no
 // atomics) before rotating the sums to the world frame into the slots.
+// In place: s_off[1..128] holds 128 counts on entry (stored before a block
+// barrier) and their inclusive prefix sums on exit (s_off[0] stays 0).
+// Warps 0-3 scan one count per lane (integer sums: the same as a serial
+// pass).  Needs at least 128 threads; ends with a block barrier.
+TC_D void prefix128(int* s_off) {
+  __shared__ int s_w4[4];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  int incl = 0;
+  if (t < 128) {
+    incl = s_off[t + 1];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += v;
+    }
+    if (lane == 31) s_w4[w] = incl;
+  }
+  __syncthreads();
+  if (t < 128) {
+    int off = 0;
+    for (int k = 0; k < w; ++k) off += s_w4[k];
+    s_off[t + 1] = off + incl;
+  }
+  __syncthreads();
+}
+
 template <class R, int GK, int MODE>
 __global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
@@ -352,9 +378,7 @@ __global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayo
   if (threadIdx.x == 0) s_off[0] = 0;
   if (threadIdx.x < 128) s_off[threadIdx.x + 1] = kept;
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
-  __syncthreads();
+  prefix128(s_off);
   const int total = s_off[128];
   double energy = 0.0;
   double dmin2 = 1e300;
@@ -622,9 +646,7 @@ __global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, Part
   if (threadIdx.x == 0) s_off[0] = 0;
   if ((int)threadIdx.x % kCcdLanes == 0) s_off[pl + 1] = kept;
   __syncthreads();
-  if (threadIdx.x == 0)
-    for (int i = 0; i < 128; ++i) s_off[i + 1] += s_off[i];
-  __syncthreads();
+  prefix128(s_off);
   const int total = s_off[128];
   double tmin = 1.0;
   const int kind = GK == GE ? 1 : 0;
