@@ -452,7 +452,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       pcg_max = std::max(pcg_max, tasks[i].env->pcg_max);
     }
     if ((st = X.build(set, eta.data(), nullptr)) != TC_OK) return st;
-    if ((st = b_pcg<R>(X.host, pcg_max, X.stream)) != TC_OK) return st;
+    if ((st = b_pcg<R>(X.host, pcg_max, true, X.stream)) != TC_OK) return st;
     b_pmax<R>(X.host, X.stream);
     if ((st = X.read()) != TC_OK) return st;
     std::vector<Scalars> pre(X.h_sc, X.h_sc + set.size());
@@ -668,7 +668,7 @@ tc_status autotune_pcg(BatchExec<R>& X, const std::vector<Env*>& envs, int mode,
         std::vector<double> t2 = mode == 0 ? std::vector<double>{tol2[gi]} : tol2;
         if ((st = X.build(set, t2.data(), nullptr)) != TC_OK) break;
         cudaEventRecord(e0, X.stream);
-        if ((st = b_pcg<R>(X.host, pcg_max, X.stream)) != TC_OK) break;
+        if ((st = b_pcg<R>(X.host, pcg_max, false, X.stream)) != TC_OK) break;
         cudaEventRecord(e1, X.stream);
         if ((st = X.read()) != TC_OK) break;
         float ms = 0.f;

@@ -269,23 +269,88 @@ template <class R> TC_D void apply_minv(const EnvView<R>& e, int v, const R r[3]
   z[2] = m5 * r[0] + m4 * r[1] + m2 * r[2];
 }
 
-// r = -g, z = M^-1 r, p = z, dx = 0; partials r.z, r.r per K_VERT unit
+// Per-env PCG start values written by k_pcg_init_env: 0 r.z, 1 r.r,
+// 2 done (1 when the start residual already meets the tolerance),
+// 3 iterations, 4 squared tolerance, 5 p.q; 6 the warm-start scale s.
+constexpr int kEnvScalars = 8;
+
+// Warm start from the previous solve: its solution d (still in dx) scaled by
+// the minimiser s = -g.d / d.A d of the quadratic model along d, so the start
+// point s d is never worse for the model than 0.  This pass forms q = A d
+// (one lane group per row, blocks in row order) and the per-unit partials
+// -g.d and d.q (K_VGRP units, in the assembly's partial region, which is
+// free once the assembly has been folded).
 template <class R>
-__global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, PartLayout L) {
+__global__ void __launch_bounds__(kBlock) k_pcg_warm(const BatchView<R> bv, PartLayout L) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VGRP, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const int lane = threadIdx.x & (kLanes - 1);
+  const int v = l.chunk * 32 + threadIdx.x / kLanes;
+  const int nv = e.nv;
+  const int64_t nb = e.nnzb;
+  double gd = 0.0, dq = 0.0;
+  R a[3] = {0, 0, 0};
+  if (v < nv)
+    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
+      const int j = e.bsr_ci[k];
+      const R d0 = e.dx[j], d1 = e.dx[nv + j], d2 = e.dx[2 * nv + j];
+      const R* B = e.bsr_val + k;
+      a[0] += B[0] * d0 + B[nb] * d1 + B[2 * nb] * d2;
+      a[1] += B[3 * nb] * d0 + B[4 * nb] * d1 + B[5 * nb] * d2;
+      a[2] += B[6 * nb] * d0 + B[7 * nb] * d1 + B[8 * nb] * d2;
+    }
+  for (int i = 0; i < 3; ++i) a[i] = group_sum(a[i]);
+  if (v < nv && lane == 0)
+    for (int i = 0; i < 3; ++i) {
+      const R d = e.dx[i * nv + v];
+      e.q[i * nv + v] = a[i];
+      gd -= (double)e.g[i * nv + v] * (double)d;
+      dq += (double)d * (double)a[i];
+    }
+  gd = block_sum<kBlock>(gd);
+  dq = block_sum<kBlock>(dq);
+  if (threadIdx.x == 0) {
+    bv.part[L.asmb + 2 * (int64_t)blockIdx.x] = gd;
+    bv.part[L.asmb + 2 * (int64_t)blockIdx.x + 1] = dq;
+  }
+}
+
+// per env: the warm-start scale s (0 when d.A d is not positive or the
+// quotient is not finite: then the solve starts from 0)
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_pcg_warm_env(const BatchView<R> bv, PartLayout L) {
+  const int env = blockIdx.x;
+  const double gd = env_unit_sum(bv, K_VGRP, env, bv.part + L.asmb, 2, 0);
+  const double dq = env_unit_sum(bv, K_VGRP, env, bv.part + L.asmb, 2, 1);
+  if (threadIdx.x == 0) {
+    double sc = dq > 0.0 ? gd / dq : 0.0;
+    if (!isfinite(sc)) sc = 0.0;
+    bv.part[L.env_s + kEnvScalars * env + 6] = sc;
+  }
+}
+
+// dx = s d, r = -g - s A d (cold start: s = 0, dx = 0, r = -g), z = M^-1 r,
+// p = z; partials r.z, r.r per K_VERT unit
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, PartLayout L, int warm) {
   const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
   const EnvView<R>& e = bv.views[l.env];
   const int v = l.chunk * kBlock + threadIdx.x;
   const int nv = e.nv;
+  const R sw = warm ? (R)bv.part[L.env_s + kEnvScalars * l.env + 6] : R(0);
   double rz = 0.0, rr = 0.0;
   if (v < nv) {
     R r[3], z[3];
-    for (int i = 0; i < 3; ++i) r[i] = e.fixed[v] ? R(0) : -e.g[i * nv + v];
+    for (int i = 0; i < 3; ++i) {
+      r[i] = e.fixed[v] ? R(0) : -e.g[i * nv + v];
+      if (sw != R(0) && !e.fixed[v]) r[i] -= sw * e.q[i * nv + v];
+    }
     apply_minv<R>(e, v, r, z);
     for (int i = 0; i < 3; ++i) {
       e.r[i * nv + v] = r[i];
       e.z[i * nv + v] = z[i];
       e.p[i * nv + v] = z[i];
-      e.dx[i * nv + v] = R(0);
+      e.dx[i * nv + v] = sw != R(0) ? sw * e.dx[i * nv + v] : R(0);
       rz += (double)r[i] * (double)z[i];
       rr += (double)r[i] * (double)r[i];
     }
@@ -297,11 +362,6 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, Part
     bv.part[L.rr + blockIdx.x] = rr;
   }
 }
-
-// Per-env PCG start values written by k_pcg_init_env: 0 r.z, 1 r.r,
-// 2 done (1 when the start residual already meets the tolerance),
-// 3 iterations, 4 squared tolerance, 5 p.q.
-constexpr int kEnvScalars = 8;
 
 // per env: r.z, r.r and the squared stopping tolerance (param[env]) -> buffer 0
 template <class R>
@@ -922,8 +982,13 @@ template <class R> tc_status set_pcg_shape(int cs, int threads) {
   return TC_OK;
 }
 
-template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s) {
-  if (b.units[K_VERT] > 0) TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L));
+template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, bool warm, cudaStream_t s) {
+  if (warm && b.units[K_VGRP] > 0) {
+    TC_LAUNCH("k_pcg_warm", s, k_pcg_warm<R><<<b.units[K_VGRP], kBlock, 0, s>>>(b.bv, b.L));
+    TC_LAUNCH("k_pcg_warm_env", s, k_pcg_warm_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
+  }
+  if (b.units[K_VERT] > 0)
+    TC_LAUNCH("k_pcg_init", s, k_pcg_init<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv, b.L, warm ? 1 : 0));
   TC_LAUNCH("k_pcg_init_env", s, k_pcg_init_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
   const PcgShape sh = pcg_shape<R>();
   cudaLaunchConfig_t cfg = {};
@@ -1036,7 +1101,7 @@ template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStre
 #define TC_INST(R)                                                            \
   template void b_assemble<R>(const BatchHost<R>&, cudaStream_t);             \
   template void b_trial_energy<R>(const BatchHost<R>&, cudaStream_t);         \
-  template tc_status b_pcg<R>(const BatchHost<R>&, int, cudaStream_t);        \
+  template tc_status b_pcg<R>(const BatchHost<R>&, int, bool, cudaStream_t);        \
   template void b_pmax<R>(const BatchHost<R>&, cudaStream_t);                 \
   template void b_trial<R>(const BatchHost<R>&, cudaStream_t);                \
   template void b_step_vectors<R>(const BatchHost<R>&, int, cudaStream_t);    \

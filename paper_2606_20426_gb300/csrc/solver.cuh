@@ -39,7 +39,7 @@ template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_force(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_assemble(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_trial_energy(const BatchHost<R>& b, cudaStream_t s);
-template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, cudaStream_t s);
+template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, bool warm, cudaStream_t s);
 template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s);
 // mode 0: u0 = u and (dynamic) utilde = u + dt vel; mode 1: vel = (u - u0) / dt
