@@ -38,7 +38,7 @@ WORKLOAD = ("gelsight-like graded pad 18x24x4 mm, ~60k tets, sphere/cylinder/box
 # keyed by kernel; valid only while the kernel's source file is unchanged.
 # k_pcg_cluster: dram read + write of one launch over 8 GelSight-like envs
 # (1,446 CG iterations of one env each) -> bytes per CG iteration of one env.
-NCU_TRAFFIC = {"k_pcg_cluster": {"bytes_per_unit": (50658048 + 1486080) / 1461, "sha": "30d356cb27df6230"}}
+NCU_TRAFFIC = {"k_pcg_cluster": {"bytes_per_unit": (50658048 + 1486080) / 1461, "sha": "5522867b4ebf1280"}}
 
 
 def peaks():
@@ -85,7 +85,7 @@ def algorithmic_bytes(name, info):
 
 # Source a kernel's DRAM counters were taken on: a file, or the section of a
 # file between two marker lines (the counters go stale when it changes).
-KERNEL_SRC = {"k_pcg_cluster": ("solver.cu", "// ------------------------------------------------------------------ PCG",
+KERNEL_SRC = {"k_pcg_cluster": ("solver.cu", "// ------------------------------------------------- PCG, one cluster per env",
                                 "// Launch shape of the PCG kernel"),
               "k_stress": "elem.cu", "k_traction": "extract.cu", "k_vertex_avg": "extract.cu", "k_splat": "extract.cu"}
 
