@@ -70,13 +70,14 @@ template <class R> static tc_status alloc_state(Env& env) {
             A(&env.eslot, 12 * nt) && A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) &&
             A(&env.Minv, 6 * nv) &&
             A(&env.dx, 3 * nv) && A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) &&
-            A(&env.p2, 3 * nv) &&
+            A(&env.p2, 3 * nv) && A(&env.dfirst, 3 * nv) &&
             A(&env.cv_slot, 9 * (int64_t)std::max(env.nvc, 1)) && A(&env.ce_slot, 27 * (int64_t)std::max(env.nec, 1)) &&
             A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1));
   if (ok && env.dynamic) ok = A(&env.vel, 3 * nv) && A(&env.utilde, 3 * nv);
   if (!ok) return TC_ERR_OOM;
   TC_CHECK(cudaMemsetAsync(env.u, 0, sizeof(R) * 3 * nv, env.stream));
   TC_CHECK(cudaMemsetAsync(env.dx, 0, sizeof(R) * 3 * nv, env.stream));
+  TC_CHECK(cudaMemsetAsync(env.dfirst, 0, sizeof(R) * 3 * nv, env.stream));
   if (env.dynamic) {
     TC_CHECK(cudaMemsetAsync(env.vel, 0, sizeof(R) * 3 * nv, env.stream));
     TC_CHECK(cudaMemsetAsync(env.utilde, 0, sizeof(R) * 3 * nv, env.stream));

@@ -451,8 +451,19 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       set.push_back(tasks[i].env);
       pcg_max = std::max(pcg_max, tasks[i].env->pcg_max);
     }
-    if ((st = X.build(set, eta.data(), nullptr)) != TC_OK) return st;
+    // a substep's first solve warm-starts from the previous substep's first
+    // solution (kept in dfirst, and replaced by this one); later solves from
+    // the previous solve
+    for (int i : P) tasks[i].env->warm_first = tasks[i].newton == 0;
+    st = X.build(set, eta.data(), nullptr);
+    for (int i : P) tasks[i].env->warm_first = false;
+    if (st != TC_OK) return st;
     if ((st = b_pcg<R>(X.host, pcg_max, true, X.stream)) != TC_OK) return st;
+    for (int i : P)
+      if (tasks[i].newton == 0) {
+        Env& e = *tasks[i].env;
+        TC_CHECK(cudaMemcpyAsync(e.dfirst, e.dx, sizeof(R) * 3 * (size_t)e.nv, cudaMemcpyDeviceToDevice, X.stream));
+      }
     b_pmax<R>(X.host, X.stream);
     if ((st = X.read()) != TC_OK) return st;
     std::vector<Scalars> pre(X.h_sc, X.h_sc + set.size());

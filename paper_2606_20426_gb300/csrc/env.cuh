@@ -86,6 +86,7 @@ template <class R> struct EnvView {
   R* Minv;                    // 6 x nv block-Jacobi inverse (xx,yy,zz,xy,yz,zx)
   R *dx, *r, *z, *p, *q;      // 3 x nv PCG vectors
   R* p2;                      // 3 x nv second direction buffer (alternates with p)
+  const R* wd;                // 3 x nv warm-start direction of the next solve (dx or dfirst)
   // contact surface
   const int32_t* cverts;      // nvc vertex ids
   const int32_t* cedges;      // 2 x nec
@@ -240,6 +241,8 @@ struct Env {
   int32_t *be_off = nullptr, *be_idx = nullptr, *bc_off = nullptr, *bc_idx = nullptr;
   void *g = nullptr, *Minv = nullptr, *dx = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   void* p2 = nullptr;
+  void* dfirst = nullptr;     // solution of the last substep's first Newton solve (warm start)
+  bool warm_first = false;    // the next solve is a substep's first: warm-start from dfirst
   void *cv_slot = nullptr, *ce_slot = nullptr, *cf_slot = nullptr;
   void* utrial = nullptr;
   // extraction scratch (float)
@@ -272,6 +275,7 @@ template <class R> EnvView<R> Env::view() const {
   e.mass = (const R*)mass; e.u = (R*)u; e.ut = (R*)utrial; e.utilde = (R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
   e.u0 = (R*)ut; e.vel = (R*)vel; e.dt = dynamic ? dt : 0.0;
   e.dx = (R*)dx; e.r = (R*)r; e.z = (R*)z; e.p = (R*)p; e.q = (R*)q; e.p2 = (R*)p2;
+  e.wd = (const R*)(warm_first && dfirst ? dfirst : dx);
   e.cverts = cverts; e.cedges = cedges; e.cfaces = cfaces; e.vslot = vslot;
   e.cv_face_off = cv_face_off; e.cv_face_idx = cv_face_idx; e.cv_edge_off = cv_edge_off; e.cv_edge_idx = cv_edge_idx;
   e.gel_elen2 = gel_elen2;

@@ -274,9 +274,12 @@ template <class R> TC_D void apply_minv(const EnvView<R>& e, int v, const R r[3]
 // 3 iterations, 4 squared tolerance, 5 p.q; 6 the warm-start scale s.
 constexpr int kEnvScalars = 8;
 
-// Warm start from the previous solve: its solution d (still in dx) scaled by
-// the minimiser s = -g.d / d.A d of the quadratic model along d, so the start
-// point s d is never worse for the model than 0.  This pass forms q = A d
+// Warm start from a previous solve: its solution d scaled by the minimiser
+// s = -g.d / d.A d of the quadratic model along d, so the start point s d is
+// never worse for the model than 0.  d (EnvView::wd) is the previous solve's
+// solution (still in dx), or for the first Newton solve of a substep the
+// first solve of the previous substep (the response to the previous
+// indenter advance).  This pass forms q = A d
 // (one lane group per row, blocks in row order) and the per-unit partials
 // -g.d and d.q (K_VGRP units, in the assembly's partial region, which is
 // free once the assembly has been folded).
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_warm(const BatchView<R> bv, Part
   if (v < nv)
     for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
       const int j = e.bsr_ci[k];
-      const R d0 = e.dx[j], d1 = e.dx[nv + j], d2 = e.dx[2 * nv + j];
+      const R d0 = e.wd[j], d1 = e.wd[nv + j], d2 = e.wd[2 * nv + j];
       const R* B = e.bsr_val + k;
       a[0] += B[0] * d0 + B[nb] * d1 + B[2 * nb] * d2;
       a[1] += B[3 * nb] * d0 + B[4 * nb] * d1 + B[5 * nb] * d2;
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_warm(const BatchView<R> bv, Part
   for (int i = 0; i < 3; ++i) a[i] = group_sum(a[i]);
   if (v < nv && lane == 0)
     for (int i = 0; i < 3; ++i) {
-      const R d = e.dx[i * nv + v];
+      const R d = e.wd[i * nv + v];
       e.q[i * nv + v] = a[i];
       gd -= (double)e.g[i * nv + v] * (double)d;
       dq += (double)d * (double)a[i];
@@ -350,7 +353,7 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init(const BatchView<R> bv, Part
       e.r[i * nv + v] = r[i];
       e.z[i * nv + v] = z[i];
       e.p[i * nv + v] = z[i];
-      e.dx[i * nv + v] = sw != R(0) ? sw * e.dx[i * nv + v] : R(0);
+      e.dx[i * nv + v] = sw != R(0) ? sw * e.wd[i * nv + v] : R(0);
       rz += (double)r[i] * (double)z[i];
       rr += (double)r[i] * (double)r[i];
     }
