@@ -547,7 +547,9 @@ def run_ours(args):
         "extraction": _extraction_fracs(prof, infos, peak),
         "kernels": kernel_table,
         "solver": {"newton_per_env_step": sum(e.get_info()["newton_iters"] for e in batched) / steps_done,
-                   "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in batched) / steps_done},
+                   "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in batched) / steps_done,
+                   "substeps_per_env_step": sum(e.get_info()["substeps"] for e in batched) / steps_done,
+                   "halvings_per_env_step": sum(e.get_info()["line_search_halvings"] for e in batched) / steps_done},
     }
     for e in served + batched + plain:
         e.close()

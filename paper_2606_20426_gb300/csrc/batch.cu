@@ -25,6 +25,11 @@ namespace tc {
 // smallest and largest forcing term of the inexact Newton solve in the mixed mode
 constexpr double kEtaFloor32 = 0.1;
 constexpr double kEtaCap32 = 0.1;
+// continuation of an accepted full step: taken when the energy fell by more
+// than kExtendRatio times the model's predicted decrease, to at most
+// kExtendMax times the step
+constexpr double kExtendRatio = 1.2;
+constexpr double kExtendMax = 8.0;
 
 #define TC_CHECK(x)                                 \
   do {                                              \
@@ -505,7 +510,26 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         c.newton++;
         c.phase = StepCtl::NEWTON;
         // rounding floor: the step is tiny and the energy did not move
-        if (Et == c.E0 && pmax <= 10.0 * e.ptol) finish_substep(c);
+        if (Et == c.E0 && pmax <= 10.0 * e.ptol) {
+          finish_substep(c);
+          continue;
+        }
+        // continuation: a full step that lowered the energy clearly more than
+        // the quadratic model predicted (model too stiff along dx -- the
+        // Gauss-Newton contact blocks drop the barrier's negative curvature
+        // term) goes on along dx to the minimiser of the parabola through
+        // E0, the slope g.dx and E(1): alpha* = 1 / (2 - r), r = (E0 - E1) /
+        // decrement, capped at kExtendMax
+        const double dE = c.E0 - Et;
+        if (c.alpha >= 1.0 && decrement > 0.0 && dE > 20.0 * e_noise) {
+          const double r = dE / decrement;
+          if (r > kExtendRatio) {
+            const double astar = r >= 2.0 - 1.0 / kExtendMax ? kExtendMax : 1.0 / (2.0 - r);
+            c.ext = astar - 1.0;
+            c.E1 = Et;
+            c.phase = StepCtl::EXTEND;
+          }
+        }
         continue;
       }
       c.alpha *= 0.5;
@@ -515,6 +539,34 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     }
   }
   // ---- one halving of every env in the line search
+  // ---- continuation of accepted full steps along dx (CCD-bounded; kept
+  // only if it lowers the energy further)
+  std::vector<int> Ex = pick(StepCtl::EXTEND);
+  if (!Ex.empty()) {
+    std::vector<Env*> set;
+    std::vector<double> fac;
+    std::vector<Motion> mot;
+    for (int i : Ex) {
+      set.push_back(tasks[i].env);
+      fac.push_back(tasks[i].ext);
+      mot.push_back(make_motion(tasks[i].env->pose, tasks[i].env->pose, 1));
+    }
+    if ((st = X.build(set, fac.data(), nullptr)) != TC_OK) return st;
+    b_scale_dx<R>(X.host, X.stream);
+    std::vector<Scalars> sc;
+    if ((st = ccd_phase<R>(X, set, mot, true, sc)) != TC_OK) return st;
+    for (size_t j = 0; j < Ex.size(); ++j) {
+      StepCtl& c = tasks[Ex[j]];
+      Env& e = *c.env;
+      const double Ee = sc[j].energy;
+      const bool ok = !(sc[j].status & ST_NONFINITE) && std::isfinite(Ee) && Ee <= c.E1;
+      if (ok) std::swap(e.u, e.utrial);
+      if (trace_on())
+        std::fprintf(stderr, "[tc] req %llu   continue x%.3f ccd=%.6f E=%.17g %s\n", (unsigned long long)c.tag,
+                     1.0 + c.ext, sc[j].ccd_t, Ee, ok ? "kept" : "dropped");
+      c.phase = StepCtl::NEWTON;
+    }
+  }
   std::vector<int> Ls = pick(StepCtl::LINESEARCH);
   if (!Ls.empty()) {
     std::vector<Env*> set;

@@ -41,8 +41,9 @@ struct StepCtl {
   uint64_t tag = 0;
   tc_pose pose0{}, target{};
   double s = 0.0, g0 = -1.0, E0 = 0.0, alpha = 1.0;
+  double E1 = 0.0, ext = 0.0;  // energy after an accepted full step; continuation factor - 1
   int sub = 0, newton = 0, halvings = 0;
-  enum Phase { START, ADVANCE, NEWTON, LINESEARCH, DONE, FAILED } phase = START;
+  enum Phase { START, ADVANCE, NEWTON, LINESEARCH, EXTEND, DONE, FAILED } phase = START;
   tc_status status = TC_OK;
 };
 

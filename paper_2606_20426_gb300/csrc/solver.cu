@@ -1077,6 +1077,22 @@ template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s) {
   if (b.units[K_VERT] > 0) TC_LAUNCH("k_trial", s, k_trial<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv));
 }
 
+// dx *= param (per env): the continuation of an accepted step along its
+// direction, whose length the CCD pass that follows then bounds
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_scale_dx(const BatchView<R> bv) {
+  const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
+  const EnvView<R>& e = bv.views[l.env];
+  const R f = (R)bv.param[l.env];
+  const int v = l.chunk * kBlock + threadIdx.x;
+  if (v < e.nv)
+    for (int i = 0; i < 3; ++i) e.dx[i * e.nv + v] *= f;
+}
+
+template <class R> void b_scale_dx(const BatchHost<R>& b, cudaStream_t s) {
+  if (b.units[K_VERT] > 0) TC_LAUNCH("k_scale_dx", s, k_scale_dx<R><<<b.units[K_VERT], kBlock, 0, s>>>(b.bv));
+}
+
 // mode 0 (step start): u0 = u and, when dynamic, utilde = u + dt vel;
 // mode 1 (step end, dynamic): vel = (u - u0) / dt
 template <class R>
@@ -1107,6 +1123,7 @@ template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStre
   template tc_status b_pcg<R>(const BatchHost<R>&, int, bool, cudaStream_t);        \
   template void b_pmax<R>(const BatchHost<R>&, cudaStream_t);                 \
   template void b_trial<R>(const BatchHost<R>&, cudaStream_t);                \
+  template void b_scale_dx<R>(const BatchHost<R>&, cudaStream_t);             \
   template void b_step_vectors<R>(const BatchHost<R>&, int, cudaStream_t);    \
   template PcgShape pcg_shape<R>();                                           \
   template tc_status set_pcg_shape<R>(int, int);

@@ -42,6 +42,7 @@ template <class R> void b_trial_energy(const BatchHost<R>& b, cudaStream_t s);
 template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, bool warm, cudaStream_t s);
 template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s);
+template <class R> void b_scale_dx(const BatchHost<R>& b, cudaStream_t s);  // dx *= param per env
 // mode 0: u0 = u and (dynamic) utilde = u + dt vel; mode 1: vel = (u - u0) / dt
 template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStream_t s);
 
