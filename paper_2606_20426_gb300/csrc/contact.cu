@@ -346,7 +346,7 @@ TC_D void prefix128(int* s_off) {
 }
 
 template <class R, int GK, int MODE>
-__global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayout L, int trial) {
+TC_D void contact_unit(const BatchView<R>& bv, const PartLayout& L, int trial, int unit) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int NG = 3 * NGP;
   constexpr int NH = NG * (NG + 1) / 2;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayo
   R(*s_gh)[NG + NH] = reinterpret_cast<R(*)[NG + NH]>(s_dyn_contact);
   __shared__ Origin s_o[128];
   __shared__ Vec3<R> s_xg[128][NGP];
-  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
+  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, unit);
   const EnvView<R>& e = bv.views[lc.env];
   const R* __restrict__ u = trial ? e.ut : e.u;
   double* part_out = bv.part + L.cont[GK];
@@ -487,9 +487,19 @@ __global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayo
   energy = block_sum<NT>(energy);
   dmin2 = block_min<NT>(dmin2);
   if (threadIdx.x == 0) {
-    part_out[2 * blockIdx.x] = energy;
-    part_out[2 * blockIdx.x + 1] = dmin2;
+    part_out[2 * unit] = energy;
+    part_out[2 * unit + 1] = dmin2;
   }
+}
+
+// All three gel primitive kinds in one launch, the slowest kind (edges)
+// first: blocks [0, ne) edges, then faces, then vertices.
+template <class R, int MODE>
+__global__ void __launch_bounds__(512) k_contact(const BatchView<R> bv, PartLayout L, int trial, int ne, int nf) {
+  const int b = blockIdx.x;
+  if (b < ne) contact_unit<R, GE, MODE>(bv, L, trial, b);
+  else if (b < ne + nf) contact_unit<R, GF, MODE>(bv, L, trial, b - ne);
+  else contact_unit<R, GV, MODE>(bv, L, trial, b - ne - nf);
 }
 
 template <class R> struct ContactGrid {
@@ -500,21 +510,18 @@ template <class R> struct ContactGrid {
 template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s) {
   const int t = trial ? 1 : 0;
   const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
+  const unsigned n = (unsigned)(nv + ne + nf);
+  if (n == 0) return;
+  constexpr size_t smem = std::max(contact_smem<R, GV>(), std::max(contact_smem<R, GE>(), contact_smem<R, GF>()));
   if (hess) {
     static const bool smem_set = [] {
-      cudaFuncSetAttribute(k_contact<R, GV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GV>());
-      cudaFuncSetAttribute(k_contact<R, GE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GE>());
-      cudaFuncSetAttribute(k_contact<R, GF, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)contact_smem<R, GF>());
+      cudaFuncSetAttribute(k_contact<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       return true;
     }();
     (void)smem_set;
-    if (nv) TC_LAUNCH("k_contact", s, k_contact<R, GV, 1><<<nv, 512, contact_smem<R, GV>(), s>>>(b.bv, b.L, t));
-    if (ne) TC_LAUNCH("k_contact", s, k_contact<R, GE, 1><<<ne, 512, contact_smem<R, GE>(), s>>>(b.bv, b.L, t));
-    if (nf) TC_LAUNCH("k_contact", s, k_contact<R, GF, 1><<<nf, 512, contact_smem<R, GF>(), s>>>(b.bv, b.L, t));
+    TC_LAUNCH("k_contact", s, k_contact<R, 1><<<n, 512, smem, s>>>(b.bv, b.L, t, ne, nf));
   } else {
-    if (nv) TC_LAUNCH("k_contact_energy", s, k_contact<R, GV, 0><<<nv, 512, 0, s>>>(b.bv, b.L, t));
-    if (ne) TC_LAUNCH("k_contact_energy", s, k_contact<R, GE, 0><<<ne, 512, 0, s>>>(b.bv, b.L, t));
-    if (nf) TC_LAUNCH("k_contact_energy", s, k_contact<R, GF, 0><<<nf, 512, 0, s>>>(b.bv, b.L, t));
+    TC_LAUNCH("k_contact_energy", s, k_contact<R, 0><<<n, 512, 0, s>>>(b.bv, b.L, t, ne, nf));
   }
 }
 
