@@ -604,15 +604,17 @@ TC_D void ccd_prim_box32(const EnvView<R>& e, const Motion& mo, const R* dir, in
 // kCcdThreads share its narrow phase.
 constexpr int kCcdThreads = 512;
 constexpr int kCcdLanes = kCcdThreads / 128;
+// registers per thread of the fused CCD kernel (one 512-thread block per SM)
+constexpr int kCcdRegs = 96;
 
 template <class R, int GK>
-__global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, PartLayout L) {
+TC_D void ccd_unit(const BatchView<R>& bv, const PartLayout& L, int unit) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
   constexpr int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
   __shared__ int s_off[129];
   __shared__ Origin s_o[128];
   __shared__ Vec3<R> s_xg[128][NGP], s_pg[128][NGP];
-  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, blockIdx.x);
+  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + GK, unit);
   const EnvView<R>& e = bv.views[lc.env];
   const Motion& mo = bv.motion[lc.env];
   const R* __restrict__ dir = mo.use_dir ? e.dx : nullptr;
@@ -690,7 +692,17 @@ __global__ void __launch_bounds__(kCcdThreads) k_ccd(const BatchView<R> bv, Part
     tmin = fmin(tmin, (double)t);
   }
   tmin = block_min<kCcdThreads>(tmin);
-  if (threadIdx.x == 0) part_out[blockIdx.x] = tmin;
+  if (threadIdx.x == 0) part_out[unit] = tmin;
+}
+
+// All three gel primitive kinds in one launch, edges first (the slowest
+// kind), then faces, then vertices.
+template <class R>
+__global__ void __maxnreg__(kCcdRegs) k_ccd(const BatchView<R> bv, PartLayout L, int ne, int nf) {
+  const int b = blockIdx.x;
+  if (b < ne) ccd_unit<R, GE>(bv, L, b);
+  else if (b < ne + nf) ccd_unit<R, GF>(bv, L, b - ne);
+  else ccd_unit<R, GV>(bv, L, b - ne - nf);
 }
 
 // per env: min TOI over its contact units -> ccd_t
@@ -708,9 +720,8 @@ __global__ void __launch_bounds__(kBlock) k_ccd_env(const BatchView<R> bv, PartL
 
 template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s) {
   const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
-  if (nv) TC_LAUNCH("k_ccd", s, k_ccd<R, GV><<<nv, kCcdThreads, 0, s>>>(b.bv, b.L));
-  if (ne) TC_LAUNCH("k_ccd", s, k_ccd<R, GE><<<ne, kCcdThreads, 0, s>>>(b.bv, b.L));
-  if (nf) TC_LAUNCH("k_ccd", s, k_ccd<R, GF><<<nf, kCcdThreads, 0, s>>>(b.bv, b.L));
+  if (nv + ne + nf > 0)
+    TC_LAUNCH("k_ccd", s, k_ccd<R><<<(unsigned)(nv + ne + nf), kCcdThreads, 0, s>>>(b.bv, b.L, ne, nf));
   TC_LAUNCH("k_ccd_env", s, k_ccd_env<R><<<b.nenv, kBlock, 0, s>>>(b.bv, b.L));
 }
 
