@@ -85,9 +85,27 @@ void pose_interp(const tc_pose& a, const tc_pose& b, double s, tc_pose* out) {
 
 // ------------------------------------------------------------ executor
 
+bool graphs_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("TACAUCHY_GRAPHS");
+    return !(v && v[0] == '0');
+  }();
+  return on;
+}
+
 template <class R> BatchExec<R>::~BatchExec() { release(); }
 
+template <class R> void BatchExec<R>::drop_graphs() {
+  for (auto& g : graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  graphs.clear();
+  ++gen;
+}
+
 template <class R> void BatchExec<R>::release() {
+  drop_graphs();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
   if (arena) {
     arena->put(d_views);
     arena->put(d_prefix);
@@ -117,6 +135,7 @@ template <class R> void BatchExec<R>::release() {
 }
 
 template <class R> tc_status BatchExec<R>::reserve(int nenv, int64_t part) {
+  if (nenv > cap_env || part > cap_part) drop_graphs();  // the tables move
   if (nenv > cap_env) {
     const int cap = std::max(nenv, 2 * cap_env);
     arena->put(d_views);
@@ -286,11 +305,15 @@ static tc_status ccd_phase(BatchExec<R>& X, const std::vector<Env*>& set, const 
     }
     tc_status st = X.build(sub, nullptr, m.data());
     if (st != TC_OK) return st;
-    b_ccd<R>(X.host, X.stream);
-    if (trial) {
-      b_trial<R>(X.host, X.stream);
-      b_trial_energy<R>(X.host, X.stream);
-    }
+    st = X.launch(3, {trial ? 1 : 0}, [&]() -> tc_status {
+      b_ccd<R>(X.host, X.stream);
+      if (trial) {
+        b_trial<R>(X.host, X.stream);
+        b_trial_energy<R>(X.host, X.stream);
+      }
+      return TC_OK;
+    });
+    if (st != TC_OK) return st;
     if ((st = X.read()) != TC_OK) return st;
     std::vector<int> again;
     for (size_t j = 0; j < todo.size(); ++j) {
@@ -410,9 +433,13 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     std::vector<Env*> set;
     for (int i : N) set.push_back(tasks[i].env);
     if ((st = X.build(set, nullptr, nullptr)) != TC_OK) return st;
-    b_elem<R>(X.host, true, false, X.stream);
-    b_contact<R>(X.host, true, false, X.stream);
-    b_assemble<R>(X.host, X.stream);
+    st = X.launch(1, {}, [&]() -> tc_status {
+      b_elem<R>(X.host, true, false, X.stream);
+      b_contact<R>(X.host, true, false, X.stream);
+      b_assemble<R>(X.host, X.stream);
+      return TC_OK;
+    });
+    if (st != TC_OK) return st;
     if ((st = X.read()) != TC_OK) return st;
     for (size_t j = 0; j < N.size(); ++j) {
       StepCtl& c = tasks[N[j]];
@@ -463,13 +490,18 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     st = X.build(set, eta.data(), nullptr);
     for (int i : P) tasks[i].env->warm_first = false;
     if (st != TC_OK) return st;
-    if ((st = b_pcg<R>(X.host, pcg_max, true, X.stream)) != TC_OK) return st;
+    const PcgShape sh = pcg_shape<R>();
+    st = X.launch(2, {pcg_max, sh.cs, sh.threads, sh.smem}, [&]() -> tc_status {
+      const tc_status ps = b_pcg<R>(X.host, pcg_max, true, X.stream);
+      b_pmax<R>(X.host, X.stream);
+      return ps;
+    });
+    if (st != TC_OK) return st;
     for (int i : P)
       if (tasks[i].newton == 0) {
         Env& e = *tasks[i].env;
         TC_CHECK(cudaMemcpyAsync(e.dfirst, e.dx, sizeof(R) * 3 * (size_t)e.nv, cudaMemcpyDeviceToDevice, X.stream));
       }
-    b_pmax<R>(X.host, X.stream);
     if ((st = X.read()) != TC_OK) return st;
     std::vector<Scalars> pre(X.h_sc, X.h_sc + set.size());
     std::vector<Motion> mot;
@@ -576,8 +608,12 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       al.push_back(tasks[i].alpha);
     }
     if ((st = X.build(set, al.data(), nullptr)) != TC_OK) return st;
-    b_trial<R>(X.host, X.stream);
-    b_trial_energy<R>(X.host, X.stream);
+    st = X.launch(4, {}, [&]() -> tc_status {
+      b_trial<R>(X.host, X.stream);
+      b_trial_energy<R>(X.host, X.stream);
+      return TC_OK;
+    });
+    if (st != TC_OK) return st;
     if ((st = X.read()) != TC_OK) return st;
     for (size_t j = 0; j < Ls.size(); ++j) {
       StepCtl& c = tasks[Ls[j]];
