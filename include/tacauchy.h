@@ -143,7 +143,11 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material,
 
 /* One step (Algorithm 2, physics line): move the indenter from its current
  * pose to *target in CCD-limited substeps and minimise the incremental
- * potential of the gel at each substep. */
+ * potential of the gel at each substep.  Each Newton system is solved by
+ * block-Jacobi PCG started from an earlier solve's solution d kept with the
+ * env (the previous solve's; for the first solve of a substep, the previous
+ * substep's first), scaled by the minimiser -g.d / d.A d of the quadratic
+ * model along d; a fresh env starts from zero. */
 tc_status tc_step(tc_env* env, const tc_pose* target);
 
 /* One step of each of n independent envs (Algorithm 2, physics line, applied
@@ -185,7 +189,8 @@ typedef struct {
  * throughput of a full batch).  results (host, up to max_results entries,
  * may be NULL when max_results is 0) receives one entry per shape tried and
  * *n_results their count.  The envs must share precision and device and have
- * no server request pending.  Not in the paper. */
+ * no server request pending.  The timed solves start from zero and leave
+ * their solution as the envs' next PCG warm start.  Not in the paper. */
 tc_status tc_autotune_pcg(tc_env** envs, int32_t n, int32_t mode, tc_pcg_tune* results,
                           int32_t max_results, int32_t* n_results);
 
