@@ -432,7 +432,9 @@ def run_ours(args):
             host[1][b].copy_(outs_s[b][1], non_blocking=True)
         cstreams[b].synchronize()
 
-    e2e_steps = max(1, min(args.steps, 3))
+    # as many env-steps per env as the timed served form: the next K poses of
+    # each env's 40-pose load/unload cycle (the same poses when K = 40)
+    e2e_steps = max(1, args.steps)
     barrier()
     t0 = time.perf_counter()
     clients.closed_loop(e2e_steps, on_done=copy_back)
@@ -673,7 +675,7 @@ def run_pcg_probe(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40, help="timed env-steps per env: poses W .. W+K-1 of the 40-pose load/unload cycle")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--envs", type=int, default=8)
     ap.add_argument("--plain", type=int, default=1, help="also time the plain one-env-per-launch form")
