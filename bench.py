@@ -619,26 +619,85 @@ def cpu_baseline(newton_per_env_step, budget):
                        f"scaled by {newton_per_env_step:.1f} Newton iterations per env-step")}
 
 
+ORACLE_REF_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import scipy.sparse.linalg as spla
+from synth import workloads
+from oracle.sim import Scene
+env = workloads.gelsight_env({seed})
+sc = Scene(env)
+Y0 = sc.indenter(sc.pose); Y1 = sc.indenter(env["poses"][0])
+frac, _ = sc.ccd_alpha(sc.x, 0 * sc.x, Y0, Y1)
+s = 1.0 if frac >= 1 else frac
+Ys = (1 - s) * Y0 + s * Y1
+x = sc.x.copy(); xt = x + sc.h * sc.v
+fr = np.repeat(sc.free, 3)
+times = []
+for it in range({n_its}):
+    t0 = time.perf_counter()
+    E, g, H = sc.gradient_hessian(x, Ys, xt)
+    g[~sc.free] = 0
+    p = np.zeros(3 * sc.nv); p[fr] = spla.spsolve(H[fr][:, fr].tocsc(), -g.ravel()[fr]); p = p.reshape(-1, 3)
+    a, cand = sc.ccd_alpha(x, p, Ys)
+    for _ in range(61):
+        if sc.energy(x + a * p, Ys, cand, xt) <= E: break
+        a *= 0.5
+    x = x + a * p
+    times.append(time.perf_counter() - t0)
+t0 = time.perf_counter(); sig = sc.stress(x); m = sc.pressure_map(x=x); t_ext = time.perf_counter() - t0
+print(json.dumps(dict(times=times, t_extract=t_ext, nt=sc.nt)))
+"""
+
+
 def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on the host cores.  Each
+    step is a bounded sample of the workload: one oracle Newton iteration
+    (direct solve, CCD, line search) of a GelSight-like env, scaled by the
+    Newton iterations per env-step, plus the stress / pressure-map
+    extraction.  The W + K samples run in concurrent single-threaded
+    processes (one env each, as independent envs would), so the value is
+    the whole-CPU throughput: processes / mean seconds per env-step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     t0 = time.perf_counter()
-    samples = []
-    newton_per_env_step = args.ref_newton_per_step
-    for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(newton_per_env_step, max(2.0, args.cpu_seconds / max(1, args.steps)))
-        if k >= args.warmup:
-            samples.append(cb)
-    vals = [s["value"] for s in samples if s.get("value")]
-    value = statistics.mean(vals) if vals else None
+    total = args.warmup + args.steps
+    procs = max(1, min(total, os.cpu_count() or 1, 16))
+    per = -(-total // procs)
+    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    runs = [subprocess.Popen([sys.executable, "-c", ORACLE_REF_SNIPPET.format(root=ROOT, seed=i, n_its=per)],
+                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=envv)
+            for i in range(procs)]
+    res, err = [], None
+    for r in runs:
+        out_s, err_s = r.communicate(timeout=1800)
+        if r.returncode != 0:
+            err = err_s[-400:]
+            continue
+        res.append(json.loads(out_s.strip().splitlines()[-1]))
+    if not res:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle sample failed: {err}"}), flush=True)
+        return
+    # samples in order of (iteration, process); the first W are the warm-up
+    order = [(i, j) for i in range(per) for j in range(len(res)) if i < len(res[j]["times"])]
+    t_ext = statistics.mean(d["t_extract"] for d in res)
+    n_newton = args.ref_newton_per_step
+    timed = [res[j]["times"][i] * n_newton + t_ext for i, j in order][args.warmup:args.warmup + args.steps]
+    per_step_s = statistics.mean(timed)
+    value = round(len(res) / per_step_s, 6)
+    sample = (f"{len(timed)} timed oracle Newton iterations ({statistics.mean(res[0]['times']):.2f} s each, "
+              f"{res[0]['nt']}-tet GelSight-like envs) over {len(res)} concurrent single-threaded processes, "
+              f"+ one stress/pressure-map extraction ({t_ext:.2f} s), scaled by {n_newton:.1f} Newton iterations "
+              f"per env-step")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": (1e3 / value) if value else None, "higher_is_better": True, "scaling": "weak",
+           "ms_per_step": round(1e3 / value, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "envs_per_gpu": 1, "form": "FP64 CPU oracle, single thread"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": samples[-1].get("sample") if samples else None},
+           "config": {"workload": WORKLOAD, "envs_per_gpu": len(res),
+                      "form": "FP64 CPU oracle, one single-threaded process per env on the host cores"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(res), "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": round(time.perf_counter() - t0, 1)}
     print(json.dumps(out), flush=True)
@@ -687,8 +746,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-newton-per-step", type=float, default=40.0,
-                    help="Newton iterations per env-step used to scale the reference arm's sample")
+    ap.add_argument("--ref-newton-per-step", type=float, default=16.0,
+                    help="Newton iterations per env-step that scale the reference arm's sample (the GPU "
+                         "path's measured count on this workload; the oracle's exact solves need no more)")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="profiling probe: this many batched steps, then the PCG autotuner (see run_pcg_probe)")
     args = ap.parse_args()
