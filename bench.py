@@ -568,38 +568,6 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-ORACLE_SNIPPET = r"""
-import json, os, sys, time
-sys.path.insert(0, {root!r})
-from synth import workloads
-from oracle.sim import Scene
-budget = {budget}
-env = workloads.gelsight_env(0)
-t0 = time.perf_counter(); sc = Scene(env); t_setup = time.perf_counter() - t0
-Y0 = sc.indenter(sc.pose); Y1 = sc.indenter(env["poses"][0])
-frac, _ = sc.ccd_alpha(sc.x, 0 * sc.x, Y0, Y1)
-s = 1.0 if frac >= 1 else frac
-Ys = (1 - s) * Y0 + s * Y1
-x = sc.x.copy(); xt = x + sc.h * sc.v
-its = 0; t0 = time.perf_counter()
-import numpy as np
-import scipy.sparse.linalg as spla
-fr = np.repeat(sc.free, 3)
-while time.perf_counter() - t0 < budget or its == 0:
-    E, g, H = sc.gradient_hessian(x, Ys, xt)
-    g[~sc.free] = 0
-    p = np.zeros(3 * sc.nv); p[fr] = spla.spsolve(H[fr][:, fr].tocsc(), -g.ravel()[fr]); p = p.reshape(-1, 3)
-    a, cand = sc.ccd_alpha(x, p, Ys)
-    for _ in range(61):
-        if sc.energy(x + a * p, Ys, cand, xt) <= E: break
-        a *= 0.5
-    x = x + a * p; its += 1
-t_newton = (time.perf_counter() - t0) / its
-t0 = time.perf_counter(); sig = sc.stress(x); m = sc.pressure_map(x=x); t_ext = time.perf_counter() - t0
-print(json.dumps(dict(t_newton=t_newton, iters=its, t_extract=t_ext, t_setup=t_setup, nt=sc.nt)))
-"""
-
-
 def cpu_baseline(newton_per_env_step, budget):
     """The oracle, single-threaded, on a bounded sample: Newton iterations of
     the first substep of one GelSight-like env for ~budget seconds, plus one
@@ -607,11 +575,12 @@ def cpu_baseline(newton_per_env_step, budget):
     iterations per env-step + t_extract), with the iteration count per
     env-step taken from the timed run (same solver settings)."""
     envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_SNIPPET.format(root=ROOT, budget=float(budget))
+    code = ORACLE_REF_SNIPPET.format(root=ROOT, seed=0, n_its=100000, budget=float(budget))
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
+    d["t_newton"], d["iters"] = statistics.mean(d["times"]), len(d["times"])
     per_env_step = d["t_newton"] * newton_per_env_step + d["t_extract"]
     return {"value": round(1.0 / per_env_step, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": (f"{d['iters']} oracle Newton iterations ({d['t_newton']:.2f} s each) of the first substep of "
@@ -635,7 +604,10 @@ Ys = (1 - s) * Y0 + s * Y1
 x = sc.x.copy(); xt = x + sc.h * sc.v
 fr = np.repeat(sc.free, 3)
 times = []
+t_start = time.perf_counter()
 for it in range({n_its}):
+    if times and {budget} > 0 and time.perf_counter() - t_start >= {budget}:
+        break
     t0 = time.perf_counter()
     E, g, H = sc.gradient_hessian(x, Ys, xt)
     g[~sc.free] = 0
@@ -667,9 +639,9 @@ def run_reference(args):
     procs = max(1, min(total, os.cpu_count() or 1, 16))
     per = -(-total // procs)
     envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    runs = [subprocess.Popen([sys.executable, "-c", ORACLE_REF_SNIPPET.format(root=ROOT, seed=i, n_its=per)],
-                             stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=envv)
-            for i in range(procs)]
+    codes = [ORACLE_REF_SNIPPET.format(root=ROOT, seed=i, n_its=per, budget=0.0) for i in range(procs)]
+    runs = [subprocess.Popen([sys.executable, "-c", c], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                             env=envv) for c in codes]
     res, err = [], None
     for r in runs:
         out_s, err_s = r.communicate(timeout=1800)
