@@ -159,3 +159,245 @@ def test_initial_penetration_rejected():
     env["start_pose"]["t"] = env["start_pose"]["t"] - np.array([0, 0, 0.5e-3])
     with pytest.raises(InitialPenetration):
         Scene(env)
+
+
+# ------------------------------------------------------------------ inertia
+# The dynamic branch of the incremental potential (Algorithm 2's step at
+# dt > 0): E(x) = 1/(2 h^2) |x - x_tilde|_M^2 + elastic + barrier with
+# x_tilde = x_t + h v_t, and the update v = (x - x_t) / h.  Mechanics fixes
+# what implicit Euler must give without contact: a rigid translation is
+# exact, total momentum is conserved when nothing is fixed, and a linear
+# oscillator follows (I + h^2 M^-1 K)^-1 (x_t + h v_t).
+
+def _free_floating(seed=3, dt=1.0 / 60.0):
+    """small_env with nothing fixed and the indenter 10 mm above the pad (no
+    contact pair can form), for the inertia pins."""
+    env = copy.deepcopy(workloads.small_env(seed, dt=dt, steps=1))
+    env["fixed"] = np.zeros(0, dtype=np.int32)
+    env["start_pose"]["t"] = env["start_pose"]["t"] + np.array([0.0, 0.0, 10e-3])
+    env["poses"] = [copy.deepcopy(env["start_pose"]) for _ in range(3)]
+    env["grid"] = None
+    return env
+
+
+def _lumped_mass(X, T, rho):
+    """rho V / 4 to each corner, V = det[X1-X0, X2-X0, X3-X0] / 6 (textbook
+    lumped mass, computed here without the oracle's mesh module)."""
+    m = np.zeros(len(X))
+    for t in T:
+        V = np.linalg.det(np.stack([X[t[1]] - X[t[0]], X[t[2]] - X[t[0]], X[t[3]] - X[t[0]]], axis=1)) / 6.0
+        m[t] += rho * V / 4.0
+    return m
+
+
+def test_inertia_rigid_translation_is_exact():
+    """Uniform v0 and no constraint: every step moves the body by h v0 and
+    keeps v = v0 (the elastic energy of a translation is zero, so x_tilde
+    itself is the minimiser)."""
+    env = _free_floating()
+    sc = Scene(env)
+    h = env["opts"]["dt"]
+    v0 = np.array([3e-3, -2e-3, 1e-3])
+    sc.v = np.tile(v0, (sc.nv, 1))
+    for k in range(1, 4):
+        sc.step(env["poses"][k - 1])
+        assert np.abs(sc.x - (sc.X + k * h * v0)).max() <= 1e-12
+        assert np.abs(sc.v - v0).max() <= 1e-9 * np.abs(v0).max()
+
+
+def test_inertia_conserves_total_momentum():
+    """No fixed vertex and no contact: internal forces sum to zero, so
+    implicit Euler keeps sum_v m_v v_v (lumped masses) exactly; a wrong mass
+    vector or an x_tilde without h v_t breaks it."""
+    env = _free_floating(seed=5)
+    sc = Scene(env)
+    rng = np.random.default_rng(11)
+    v0 = 2e-3 * rng.standard_normal((sc.nv, 3))       # stretching + shearing field
+    sc.v = v0.copy()
+    m = _lumped_mass(sc.X, sc.T, env["material"]["density"])
+    p0 = (m[:, None] * v0).sum(axis=0)
+    sc.step(env["poses"][0])
+    p1 = (m[:, None] * sc.v).sum(axis=0)
+    assert np.abs(sc.x - sc.X).max() > 1e-6             # the body deformed
+    assert np.abs(p1 - p0).max() <= 1e-8 * np.abs(m[:, None] * v0).sum(axis=0).max()
+    # the velocity field changed (elastic forces acted), momentum did not
+    assert np.abs(sc.v - v0).max() > 1e-2 * np.abs(v0).max()
+
+
+def test_implicit_euler_one_free_vertex_closed_form():
+    """One tet, three base vertices fixed, the apex free.  For small motion the
+    apex is a 3-D linear oscillator with stiffness K = V [mu |n|^2 I +
+    (lam + mu) n n^T] (linear elasticity with Eq. 1's Lame parameters, the
+    small-strain limit of the material) and lumped mass m = rho V / 4; implicit
+    Euler gives u_{k+1} = (I + h^2 K / m)^-1 (u_k + h v_k).  h is chosen so that
+    h^2 K / m is of order one, so a wrong power of h fails."""
+    L = 1e-3
+    X = np.array([[0.0, 0.0, 0.0], [L, 0.0, 0.0], [0.0, L, 0.0], [0.3 * L, 0.35 * L, L]])
+    T = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    E, nu, rho = 3.0e5, 0.45, 1100.0
+    mu = E / (2 * (1 + nu))
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    V = L ** 3 / 6.0
+    # gradient of the apex's barycentric (hat) function: N(X_a) = 1, 0 elsewhere
+    c = np.linalg.solve(np.hstack([X, np.ones((4, 1))]), np.array([0.0, 0.0, 0.0, 1.0]))
+    n = c[:3]
+    K = V * (mu * (n @ n) * np.eye(3) + (lam + mu) * np.outer(n, n))
+    m = rho * V / 4.0
+    h = float(np.sqrt(m / np.linalg.eigvalsh(K).mean()))
+    Vi, Fi = workloads.indenters.icosphere(1e-3, 1)
+    pose = dict(R=np.eye(3), t=np.array([0.3 * L, 0.35 * L, 20e-3]))
+    env = dict(X=X, tets=T, material=dict(E=E, nu=nu, density=rho), fixed=np.array([0, 1, 2], dtype=np.int32),
+               ind_V=Vi, ind_F=Fi, start_pose=pose, grid=None,
+               opts=dict(dhat=0.05e-3, kappa=1.0, dt=h, newton_rtol=1e-10, newton_max=50))
+    sc = Scene(env)
+    v0 = np.array([2e-4, -1e-4, 3e-4])                 # h v0 ~ 1e-8 m: strain ~1e-5
+    sc.v[3] = v0
+    A = np.linalg.inv(np.eye(3) + h * h * K / m)
+    u, v = np.zeros(3), v0.copy()
+    for _ in range(2):
+        u_next = A @ (u + h * v)
+        sc.step(pose)
+        got = sc.x[3] - X[3]
+        assert np.linalg.norm(got - u_next) <= 1e-4 * np.linalg.norm(u_next)
+        assert np.linalg.norm(sc.v[3] - (u_next - u) / h) <= 1e-4 * np.linalg.norm(v0)
+        u, v = u_next, (u_next - u) / h
+    assert np.abs(sc.x[:3] - X[:3]).max() == 0.0
+
+
+# -------------------------------------------------- area weighting and map
+# R7 reading (vertex value = sum_f A_f p_f / sum_f A_f over the incident
+# contact faces, deformed areas) and the pixel gather of the pressure map.
+
+def _bare_scene(X, faces):
+    sc = Scene.__new__(Scene)
+    sc.X = np.asarray(X, dtype=np.float64)
+    sc.x = sc.X.copy()
+    sc.cfaces = np.asarray(faces, dtype=np.int64)
+    sc.cverts, sc.csr_off, sc.csr_idx = msh.vertex_face_csr(sc.cfaces)
+    return sc
+
+
+def test_vertex_pressure_worked_example_deformed_areas():
+    """A three-face fan with deformed areas 1/2, 1 and 3 (mm^2) carrying
+    p = 1, 2, 5: the hub's value is (1/2 + 2 + 15) / (9/2) = 35/9 (an
+    unweighted mean gives 8/3, rest areas -- all equal here -- give 8/3)."""
+    mm = 1e-3
+    x = mm * np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-2, 0, 0], [0, -3, 0]], dtype=np.float64)
+    X = mm * np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 0]], dtype=np.float64)
+    faces = [[0, 1, 2], [0, 2, 3], [0, 3, 4]]
+    sc = _bare_scene(X, faces)
+    pv = sc.vertex_pressure(x=x, p_face=np.array([1.0, 2.0, 5.0]))
+    # slots follow sorted vertex ids 0..4
+    expect = np.array([35 / 9, 1.0, 5 / 3, 17 / 4, 5.0])
+    assert np.allclose(pv, expect, rtol=1e-14)
+
+
+def test_vertex_pressure_invariant_under_face_split():
+    """Splitting a face of the hub's fan into two faces with the same pressure
+    leaves the hub's weighted mean unchanged (a face counts by its area, not
+    by its count); vertices 1 and 2, whose fans are untouched, keep theirs."""
+    mm = 1e-3
+    x = mm * np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-2, 0, 0], [0, -3, 0], [-1, -1.5, 0]], dtype=np.float64)
+    whole = _bare_scene(x[:5], [[0, 1, 2], [0, 2, 3], [0, 3, 4]])
+    split = _bare_scene(x, [[0, 1, 2], [0, 2, 3], [0, 3, 5], [0, 5, 4]])
+    a = whole.vertex_pressure(x=x[:5], p_face=np.array([1.0, 2.0, 5.0]))
+    b = split.vertex_pressure(x=x, p_face=np.array([1.0, 2.0, 5.0, 5.0]))
+    assert np.allclose(b[:3], a[:3], rtol=1e-14)
+    assert b[0] == pytest.approx(35 / 9, rel=1e-14)
+    # vertex 3 now sees only the half (area 3/2) of the split face: (2 + 7.5) / 2.5
+    assert b[3] == pytest.approx(3.8, rel=1e-14)
+
+
+def _pixel_centres(grid):
+    H, W = grid["H"], grid["W"]
+    u = grid["origin"][0] + (np.arange(W) + 0.5) * grid["pixel"][0]
+    v = grid["origin"][1] + (np.arange(H) + 0.5) * grid["pixel"][1]
+    return np.meshgrid(u, v)  # (H, W) each: u along columns, v along rows
+
+
+@pytest.mark.parametrize("which", ["pad", "graded"])
+def test_pressure_map_reproduces_linear_vertex_field(which):
+    """Barycentric interpolation reproduces a linear field exactly: with
+    p_v = a . (u_v, v_v) + b at the contact vertices (rest coordinates in the
+    grid plane), every covered pixel shows a . (u_c, v_c) + b at its centre.
+    A permuted vertex slot, a wrong weight order or swapped grid axes fails."""
+    if which == "pad":
+        env = workloads.pad_env(0, steps=1)
+    else:
+        env = workloads.gelsight_env(2, steps=1, target_tets=4000, grid_hw=(30, 40))
+    sc = Scene(env)
+    g = env["grid"]
+    a, b = np.array([2.0e5, -7.0e5]), 30.0
+    Xc = sc.X[sc.cverts]
+    pv = a[0] * Xc[:, g["axis_u"]] + a[1] * Xc[:, g["axis_v"]] + b
+    m, mask = sc.pressure_map(p_vertex=pv)
+    U, Vv = _pixel_centres(g)
+    expect = a[0] * U + a[1] * Vv + b
+    cov = mask.astype(bool)
+    assert cov.mean() > 0.9
+    scale = np.abs(expect).max()
+    assert np.abs(m[cov] - expect[cov]).max() <= 2e-6 * scale
+    assert np.all(m[~cov] == 0.0)
+
+
+def test_linear_face_pressure_gives_linear_vertex_and_map_values():
+    """On the uniform Kuhn top of the 1,800-tet pad every interior vertex has a
+    point-symmetric fan of six equal triangles, and an in-plane affine map x =
+    A X keeps it so.  A face field p_f = a . c_f + b (c_f the deformed face
+    centroid) therefore averages to p_v = a . (A X_v) + b at interior vertices,
+    and the map shows a . (A X_c) + b at pixels inside faces of interior
+    vertices."""
+    env = workloads.pad_env(0, steps=1)
+    sc = Scene(env)
+    A = np.array([[1.08, 0.04, 0.0], [-0.02, 0.95, 0.0], [0.0, 0.0, 1.0]])
+    x = sc.X @ A.T
+    a, b = np.array([3.0e5, -1.0e5]), 12.0
+    f = sc.cfaces
+    cent = (x[f[:, 0]] + x[f[:, 1]] + x[f[:, 2]]) / 3.0
+    pf = a[0] * cent[:, 0] + a[1] * cent[:, 1] + b
+    pv = sc.vertex_pressure(x=x, p_face=pf)
+    Xc = sc.X[sc.cverts]
+    L = 20e-3
+    interior = (Xc[:, 0] > 0) & (Xc[:, 0] < L) & (Xc[:, 1] > 0) & (Xc[:, 1] < L)
+    xv = Xc @ A.T
+    lin = a[0] * xv[:, 0] + a[1] * xv[:, 1] + b
+    assert interior.sum() == 81
+    assert np.abs(pv[interior] - lin[interior]).max() <= 1e-9 * np.abs(lin).max()
+    assert np.abs(pv[~interior] - lin[~interior]).max() > 1e-3 * np.abs(lin).max()  # boundary fans are one-sided
+    m, mask = sc.pressure_map(p_vertex=pv)
+    U, Vv = _pixel_centres(env["grid"])
+    P = np.stack([U, Vv, np.zeros_like(U)], axis=-1) @ A.T
+    expect = a[0] * P[..., 0] + a[1] * P[..., 1] + b
+    slot = -np.ones(sc.nv, dtype=np.int64)
+    slot[sc.cverts] = np.arange(len(sc.cverts))
+    pf_ = sc.pix_face.reshape(mask.shape)
+    inner = np.zeros(mask.shape, dtype=bool)
+    cov = pf_ >= 0
+    inner[cov] = interior[slot[sc.cfaces[pf_[cov]]]].all(axis=1)
+    assert inner.sum() > 400
+    assert np.abs(m[inner] - expect[inner]).max() <= 2e-6 * np.abs(expect).max()
+
+
+def test_dynamic_energy_matches_gradient_by_finite_differences():
+    """The line search's energy (Scene.energy) and the Newton gradient
+    (Scene.gradient_hessian) describe one potential in the dynamic case:
+    central differences of the energy along random directions equal g . d,
+    and both report the same value, with contact pairs and inertia active."""
+    env = workloads.small_env(4, dt=1.0 / 60.0, steps=2)
+    sc = Scene(env)
+    sc.step(env["poses"][0])
+    Y = sc.indenter(env["poses"][1])
+    rng = np.random.default_rng(5)
+    sc.v = sc.v + 1e-3 * rng.standard_normal(sc.v.shape)
+    x_tilde = sc.x + sc.h * sc.v
+    x = sc.x.copy()
+    E, g, _ = sc.gradient_hessian(x, Y, x_tilde)
+    cand = sc.candidates(x, Y)
+    assert sum(len(gi) for gi, _ in cand.values()) > 0
+    assert sc.energy(x, Y, cand, x_tilde) == pytest.approx(E, rel=1e-12)
+    eps = 1e-10
+    for _ in range(3):
+        d = rng.standard_normal(x.shape)
+        d[sc.fixed] = 0.0
+        fd = (sc.energy(x + eps * d, Y, cand, x_tilde) - sc.energy(x - eps * d, Y, cand, x_tilde)) / (2 * eps)
+        assert fd == pytest.approx(float(np.sum(g * d)), rel=1e-5)
