@@ -283,8 +283,11 @@ tc_status tc_stress_from_F(const float* F, int64_t n, double E, double nu,
  * of fixed size, shared by every call: at most 262,144 contact faces and
  * 262,144 contact vertices (TC_ERR_CAPACITY beyond), about 3 MB held on every
  * GPU that loads the library until the process exits.  The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * it once per device before any stream capture.  Calls that overlap on the
+ * device looks up that array's device address (cudaGetSymbolAddress) and
+ * keeps it; if the lookup fails the call returns TC_ERR_CUDA and the next call
+ * tries again.  Make that first call on each device before any stream
+ * capture.  With no contact face (nfc = 0) every pix_face entry must be -1;
+ * out and mask are then all 0.  Calls that overlap on the
  * GPU (different streams, or different host threads) race on the shared
  * array; serialise them.  Synchronises `stream` before returning. */
 tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const float* sigma, int32_t nt,

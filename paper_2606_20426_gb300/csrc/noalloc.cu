@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "env.cuh"
+#include "prof.cuh"
 
 namespace tc {
 
@@ -22,20 +23,25 @@ constexpr int kNoAllocMaxFaces = 262144;
 constexpr int kNoAllocMaxVerts = 262144;
 static __device__ __align__(256) float g_noalloc_scratch[2 * kNoAllocMaxFaces + kNoAllocMaxVerts];
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up per device on the first
+// call that succeeds and cached from then on; a failed lookup (for example
+// before the device has a usable context) is not cached, so a later call
+// retries it instead of failing for the rest of the process.
 static float* scratch_address(int device, tc_status* st) {
   constexpr int kMaxDevices = 64;
   static float* addr[kMaxDevices] = {};
-  static std::once_flag once[kMaxDevices];
+  static std::mutex lock;
   if (device < 0 || device >= kMaxDevices) {
     *st = TC_ERR_INVALID_ARG;
     return nullptr;
   }
-  std::call_once(once[device], [&] {
+  std::lock_guard<std::mutex> g(lock);
+  if (!addr[device]) {
     void* p = nullptr;
     // the calling thread has `device` current here
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) == cudaSuccess) addr[device] = (float*)p;
-  });
+    else (void)cudaGetLastError();  // clear the non-sticky error of the failed lookup
+  }
   *st = addr[device] ? TC_OK : TC_ERR_CUDA;
   return addr[device];
 }
@@ -94,8 +100,9 @@ extern "C" tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const f
   // every scratch entry read below is written first in the same call, so
   // nothing has to be cleared
   if (nfc > 0)
-    k_face_pressure_from_sigma<<<grid_for(nfc), kBlock, 0, s>>>(x, nv, sigma, nt, cfaces, cparent, nfc, face_p,
-                                                                 face_A);
+    TC_LAUNCH("k_face_pressure_from_sigma", s,
+              k_face_pressure_from_sigma<<<grid_for(nfc), kBlock, 0, s>>>(x, nv, sigma, nt, cfaces, cparent, nfc,
+                                                                           face_p, face_A));
   launch_vertex_avg(nvc, cv_face_off, cv_face_idx, face_p, face_A, vert_p, s);
   launch_splat(npix, pix_face, pix_w, cface_slot, nfc, vert_p, out, mask, s);
   if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;

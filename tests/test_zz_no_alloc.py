@@ -59,9 +59,34 @@ def test_noalloc_pressure_map_matches_env_map(precision):
 
 
 def test_noalloc_rejects_oversize():
-    import ctypes
     from paper_2606_20426_gb300 import tacauchy
     lib = tacauchy.load()
+    # more contact faces than the scratch holds
     rc = lib.tc_pressure_map_noalloc(None, 0, None, 0, None, None, None, 262145, None, None, 0,
                                      None, None, 0, None, None, None)
     assert rc == 12  # TC_ERR_CAPACITY
+    # more contact vertices than the scratch holds
+    rc = lib.tc_pressure_map_noalloc(None, 0, None, 0, None, None, None, 0, None, None, 262145,
+                                     None, None, 0, None, None, None)
+    assert rc == 12
+
+
+def test_noalloc_without_contact_faces_gives_zero_map():
+    """No contact face and no pixel covered: every value and mask entry is 0,
+    whatever the shared scratch held from earlier calls."""
+    import torch
+    from paper_2606_20426_gb300.tacauchy import pressure_map_noalloc
+    npix = 1000
+    z32 = torch.zeros((3, 0), dtype=torch.int32, device="cuda")
+    x = torch.zeros((3, 4), dtype=torch.float32, device="cuda")
+    sig = torch.zeros((6, 1), dtype=torch.float32, device="cuda")
+    off = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    idx = torch.zeros((0,), dtype=torch.int32, device="cuda")
+    pix_face = torch.full((npix,), -1, dtype=torch.int32, device="cuda")
+    pix_w = torch.full((3, npix), 0.25, dtype=torch.float32, device="cuda")
+    out = torch.full((npix,), float("nan"), dtype=torch.float32, device="cuda")
+    mask = torch.full((npix,), 7, dtype=torch.uint8, device="cuda")
+    pressure_map_noalloc(x, sig, z32, torch.zeros((0,), dtype=torch.int32, device="cuda"), z32, off, idx,
+                         pix_face, pix_w, out, mask)
+    assert torch.count_nonzero(out).item() == 0 and not torch.isnan(out).any().item()
+    assert torch.count_nonzero(mask).item() == 0
