@@ -351,6 +351,9 @@ def run_ours(args):
     cfgs = make_envs(B, rank)
     with torch.cuda.stream(stream):
         served = [Env(c, precision="fp32", stream=stream) for c in cfgs]
+        # a second set for the end-to-end leg: the same requests (poses W ..
+        # W+K-1 after the same warm-up) with the results copied to the host
+        served_e2e = [Env(c, precision="fp32", stream=stream) for c in cfgs] if args.e2e else []
         batched = [Env(c, precision="fp32", stream=stream) for c in cfgs]
         plain = [Env(c, precision="fp32", stream=stream) for c in cfgs] if args.plain else []
     infos = [e.info for e in served]
@@ -432,15 +435,19 @@ def run_ours(args):
             host[1][b].copy_(outs_s[b][1], non_blocking=True)
         cstreams[b].synchronize()
 
-    # as many env-steps per env as the timed served form: the next K poses of
-    # each env's 40-pose load/unload cycle (the same poses when K = 40)
-    e2e_steps = max(1, args.steps)
-    barrier()
-    t0 = time.perf_counter()
-    clients.closed_loop(e2e_steps, on_done=copy_back)
-    barrier()
-    e2e_s = slowest(time.perf_counter() - t0)
-    e2e_value = job_rate(B * e2e_steps, world, e2e_s)
+    # the envs of the end-to-end leg take the same warm-up poses and then the
+    # same timed poses W .. W+K-1 as the served form, through the public call
+    # (tc_submit / tc_wait) with each result copied to pinned host memory
+    e2e_value = None
+    if served_e2e:
+        clients_e2e = _Clients(srv, served_e2e, pose_of, outs_s)
+        clients_e2e.closed_loop(args.warmup)
+        barrier()
+        t0 = time.perf_counter()
+        clients_e2e.closed_loop(args.steps, on_done=copy_back)
+        barrier()
+        e2e_s = slowest(time.perf_counter() - t0)
+        e2e_value = job_rate(B * args.steps, world, e2e_s)
     d2h = sum(4 * 6 * i["nt"] + 4 * i["H"] * i["W"] for i in infos)
     h2d = B * 96  # the target pose (12 doubles) per env-step
     # ------------- open-loop Poisson arrivals at fractions of the measured capacity
@@ -545,7 +552,10 @@ def run_ours(args):
         "plain": plain_out,
         "poisson": poisson or None,
         "clocks": clocks,
-        "e2e": {"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": ({"value": round(e2e_value, 3), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                 "form": "served form on a second set of envs, same warm-up and timed poses, wall clock from the "
+                         "first submit to the last result in pinned host memory (sigma and map per request)"}
+                if e2e_value is not None else None),
         "gpu_launches": int(launches),
         "gpu_launches_note": "kernel launches of the profiled repeat of the batched form",
         "roofline": roof,
@@ -556,122 +566,129 @@ def run_ours(args):
                    "substeps_per_env_step": sum(e.get_info()["substeps"] for e in batched) / steps_done,
                    "halvings_per_env_step": sum(e.get_info()["line_search_halvings"] for e in batched) / steps_done},
     }
-    for e in served + batched + plain:
+    for e in served + served_e2e + batched + plain:
         e.close()
     if args.sweep:
         out["stress_sweep"] = stress_sweep(dev, stream, peak)
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(out["solver"]["newton_per_env_step"], args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(max(1, min((os.cpu_count() or 2) - 1, args.cpu_procs)))
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
 
-def cpu_baseline(newton_per_env_step, budget):
-    """The oracle, single-threaded, on a bounded sample: Newton iterations of
-    the first substep of one GelSight-like env for ~budget seconds, plus one
-    stress + pressure-map extraction; env-steps/s = 1 / (t_newton x Newton
-    iterations per env-step + t_extract), with the iteration count per
-    env-step taken from the timed run (same solver settings)."""
-    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ORACLE_REF_SNIPPET.format(root=ROOT, seed=0, n_its=100000, budget=float(budget))
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=envv, timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": r.stderr[-400:]}
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    d["t_newton"], d["iters"] = statistics.mean(d["times"]), len(d["times"])
-    per_env_step = d["t_newton"] * newton_per_env_step + d["t_extract"]
-    return {"value": round(1.0 / per_env_step, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{d['iters']} oracle Newton iterations ({d['t_newton']:.2f} s each) of the first substep of "
-                       f"one {d['nt']}-tet env + one stress/pressure-map extraction ({d['t_extract']:.2f} s), "
-                       f"scaled by {newton_per_env_step:.1f} Newton iterations per env-step")}
-
-
-ORACLE_REF_SNIPPET = r"""
+ORACLE_ENVSTEP_SNIPPET = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
-import numpy as np
-import scipy.sparse.linalg as spla
-from synth import workloads
+from synth import meshes, workloads
 from oracle.sim import Scene
-env = workloads.gelsight_env({seed})
+kind, seed, nsteps = {kind!r}, {seed}, {nsteps}
+t0 = time.perf_counter()
+env = workloads.gelsight_env(seed, mesh=meshes.graded_pad()) if kind == "bench" else workloads.pad_env(seed)
 sc = Scene(env)
-Y0 = sc.indenter(sc.pose); Y1 = sc.indenter(env["poses"][0])
-frac, _ = sc.ccd_alpha(sc.x, 0 * sc.x, Y0, Y1)
-s = 1.0 if frac >= 1 else frac
-Ys = (1 - s) * Y0 + s * Y1
-x = sc.x.copy(); xt = x + sc.h * sc.v
-fr = np.repeat(sc.free, 3)
+setup_s = time.perf_counter() - t0
 times = []
-t_start = time.perf_counter()
-for it in range({n_its}):
-    if times and {budget} > 0 and time.perf_counter() - t_start >= {budget}:
-        break
+for k in range(nsteps):
     t0 = time.perf_counter()
-    E, g, H = sc.gradient_hessian(x, Ys, xt)
-    g[~sc.free] = 0
-    p = np.zeros(3 * sc.nv); p[fr] = spla.spsolve(H[fr][:, fr].tocsc(), -g.ravel()[fr]); p = p.reshape(-1, 3)
-    a, cand = sc.ccd_alpha(x, p, Ys)
-    for _ in range(61):
-        if sc.energy(x + a * p, Ys, cand, xt) <= E: break
-        a *= 0.5
-    x = x + a * p
+    sc.step(env["poses"][k])
+    sig = sc.stress()
+    m = sc.pressure_map()
     times.append(time.perf_counter() - t0)
-t0 = time.perf_counter(); sig = sc.stress(x); m = sc.pressure_map(x=x); t_ext = time.perf_counter() - t0
-print(json.dumps(dict(times=times, t_extract=t_ext, nt=sc.nt)))
+print(json.dumps(dict(times=times, setup_s=setup_s, nt=int(sc.nt), newton=sc.stats["newton"],
+                      substeps=sc.stats["substeps"])))
 """
+
+
+def oracle_env_steps(jobs, procs):
+    """Run the FP64 oracle on whole env-steps (Scene.step + stress +
+    pressure_map, each timed on its own; scene setup not timed), one
+    single-threaded process per job, at most `procs` at a time.  jobs: list of
+    (kind, seed, nsteps) with kind "bench" (the GelSight-like 59,220-tet env of
+    that seed, its first nsteps load poses) or "pad1800" (the 1,800-tet pad of
+    that seed, its first nsteps poses).  Returns one result dict per job (or
+    an "error" entry)."""
+    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = [None] * len(jobs)
+    running = []
+    todo = list(enumerate(jobs))
+    while todo or running:
+        while todo and len(running) < procs:
+            i, (kind, seed, n) = todo.pop(0)
+            code = ORACLE_ENVSTEP_SNIPPET.format(root=ROOT, kind=kind, seed=seed, nsteps=n)
+            running.append((i, subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                                stderr=subprocess.PIPE, text=True, env=envv)))
+        i, p = running.pop(0)
+        o, e = p.communicate(timeout=3600)
+        out[i] = json.loads(o.strip().splitlines()[-1]) if p.returncode == 0 else {"error": e[-400:]}
+    return out
+
+
+def cpu_baseline(procs):
+    """The oracle as it stands on the host cores, timed on whole env-steps:
+    `procs` concurrent single-threaded processes each run the first load
+    env-step (step + stress + pressure map) of one GelSight-like 59,220-tet env
+    of the bench workload (seeds 0 .. procs-1); the aggregate is procs / mean
+    seconds per env-step.  One more process runs the 1,800-tet pad of the
+    paper-sized configuration in full (10 quasi-static FP64 steps)."""
+    jobs = [("bench", s, 1) for s in range(procs)] + [("pad1800", 0, 10)]
+    t0 = time.perf_counter()
+    res = oracle_env_steps(jobs, procs + 1)
+    wall = time.perf_counter() - t0
+    bench = [r for r in res[:-1] if "times" in r]
+    if not bench:
+        return {"value": None, "unit": UNIT, "cores": procs, "kind": "oracle", "error": res[0].get("error")}
+    per = statistics.mean(r["times"][0] for r in bench)
+    pad = res[-1]
+    out = {"value": round(len(bench) / per, 6), "unit": UNIT, "cores": len(bench), "kind": "oracle",
+           "seconds_per_env_step": round(per, 2), "wall_s": round(wall, 1),
+           "sample": (f"{len(bench)} concurrent single-threaded oracle processes, each one whole env-step "
+                      f"(Scene.step + stress + pressure_map) of a {bench[0]['nt']}-tet GelSight-like env: its first "
+                      f"load pose (light contact; mean {statistics.mean(r['newton'] for r in bench):.1f} Newton "
+                      f"iterations), mean {per:.1f} s per env-step; value = processes / mean seconds")}
+    if "times" in pad:
+        out["config1_pad1800"] = {"env_steps_per_s_one_core": round(len(pad["times"]) / sum(pad["times"]), 4),
+                                  "steps": len(pad["times"]), "tets": pad["nt"], "newton": pad["newton"],
+                                  "seconds": [round(t, 2) for t in pad["times"]]}
+    return out
 
 
 def run_reference(args):
     """Reference arm: the FP64 oracle as it stands, on the host cores.  Each
-    step is a bounded sample of the workload: one oracle Newton iteration
-    (direct solve, CCD, line search) of a GelSight-like env, scaled by the
-    Newton iterations per env-step, plus the stress / pressure-map
-    extraction.  The W + K samples run in concurrent single-threaded
-    processes (one env each, as independent envs would), so the value is
-    the whole-CPU throughput: processes / mean seconds per env-step."""
+    of the W + K steps is one whole env-step (Scene.step + stress +
+    pressure_map) of the bench workload -- the first load pose of a
+    GelSight-like env, one seed per step -- run in concurrent single-threaded
+    processes (at most one per core, 16 at most); the first W are the warm-up.
+    value = processes / mean seconds per timed env-step (whole-CPU
+    throughput)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     t0 = time.perf_counter()
     total = args.warmup + args.steps
     procs = max(1, min(total, os.cpu_count() or 1, 16))
-    per = -(-total // procs)
-    envv = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    codes = [ORACLE_REF_SNIPPET.format(root=ROOT, seed=i, n_its=per, budget=0.0) for i in range(procs)]
-    runs = [subprocess.Popen([sys.executable, "-c", c], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
-                             env=envv) for c in codes]
-    res, err = [], None
-    for r in runs:
-        out_s, err_s = r.communicate(timeout=1800)
-        if r.returncode != 0:
-            err = err_s[-400:]
-            continue
-        res.append(json.loads(out_s.strip().splitlines()[-1]))
-    if not res:
+    res = oracle_env_steps([("bench", s, 1) for s in range(total)], procs)
+    ok = [r for r in res if "times" in r]
+    if len(ok) < total:
+        err = next(r.get("error") for r in res if "times" not in r)
         print(json.dumps({"impl": "reference", "unavailable": f"oracle sample failed: {err}"}), flush=True)
         return
-    # samples in order of (iteration, process); the first W are the warm-up
-    order = [(i, j) for i in range(per) for j in range(len(res)) if i < len(res[j]["times"])]
-    t_ext = statistics.mean(d["t_extract"] for d in res)
-    n_newton = args.ref_newton_per_step
-    timed = [res[j]["times"][i] * n_newton + t_ext for i, j in order][args.warmup:args.warmup + args.steps]
-    per_step_s = statistics.mean(timed)
-    value = round(len(res) / per_step_s, 6)
-    sample = (f"{len(timed)} timed oracle Newton iterations ({statistics.mean(res[0]['times']):.2f} s each, "
-              f"{res[0]['nt']}-tet GelSight-like envs) over {len(res)} concurrent single-threaded processes, "
-              f"+ one stress/pressure-map extraction ({t_ext:.2f} s), scaled by {n_newton:.1f} Newton iterations "
-              f"per env-step")
+    timed = [r["times"][0] for r in res[args.warmup:]]
+    per = statistics.mean(timed)
+    value = round(procs / per, 6)
+    wall = time.perf_counter() - t0
+    sample = (f"{len(timed)} timed whole env-steps (Scene.step + stress + pressure_map; first load pose of "
+              f"{len(timed)} {ok[0]['nt']}-tet GelSight-like envs, mean {per:.1f} s each) after {args.warmup} "
+              f"warm-up ones, over {procs} concurrent single-threaded processes; value = processes / mean seconds")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(1e3 / value, 3), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "envs_per_gpu": len(res),
+           "config": {"workload": WORKLOAD, "envs_per_gpu": procs,
                       "form": "FP64 CPU oracle, one single-threaded process per env on the host cores"},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(res), "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "wall_s": round(time.perf_counter() - t0, 1)}
+           "wall_s": round(wall, 1)}
     print(json.dumps(out), flush=True)
 
 
@@ -710,17 +727,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--envs", type=int, default=8)
     ap.add_argument("--plain", type=int, default=1, help="also time the plain one-env-per-launch form")
+    ap.add_argument("--e2e", type=int, default=1, help="also time the end-to-end leg (results copied to the host)")
     ap.add_argument("--sweep", type=int, default=1, help="also run the tc_stress_from_F size sweep")
     ap.add_argument("--poisson", type=int, default=1, help="also run open-loop Poisson arrivals")
     ap.add_argument("--workers", type=int, default=0, help="server worker threads (0: one per env)")
     ap.add_argument("--autotune", type=int, default=1, help="pick the PCG launch shape on the bench envs first")
     ap.add_argument("--poisson-seconds", type=float, default=4.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-procs", type=int, default=15,
+                    help="concurrent oracle processes of the CPU baseline (one core each, at most cores - 1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-newton-per-step", type=float, default=16.0,
-                    help="Newton iterations per env-step that scale the reference arm's sample (the GPU "
-                         "path's measured count on this workload; the oracle's exact solves need no more)")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="profiling probe: this many batched steps, then the PCG autotuner (see run_pcg_probe)")
     args = ap.parse_args()

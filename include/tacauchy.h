@@ -44,7 +44,11 @@ enum {
   TC_ERR_INVALID_MESH = 2,         /* tet with det(Dm) <= 0, index out of range */
   TC_ERR_INITIAL_PENETRATION = 3,  /* indenter touches or crosses the gel      */
   TC_ERR_NEWTON_MAXITER = 4,       /* Newton (or indenter substeps) hit the cap */
-  TC_ERR_PCG_MAXITER = 5,          /* reserved: PCG stops at pcg_max silently   */
+  TC_ERR_PCG_MAXITER = 5,          /* reserved, never returned: a PCG solve that
+                                      reaches pcg_max is not an error; its
+                                      iterate is still a descent direction and
+                                      the Newton loop goes on with it
+                                      (tc_info.pcg_capped counts such solves) */
   TC_ERR_LINESEARCH = 6,           /* no energy decrease after 60 halvings     */
   TC_ERR_NONFINITE = 7,            /* NaN/Inf in a pose, energy or direction   */
   TC_ERR_CUDA = 8,                 /* a CUDA runtime call failed               */
@@ -78,7 +82,8 @@ typedef struct { double E, nu, density; } tc_material;
  *               decrease is below the rounding level of the energy (1e-14 |E|
  *               in FP64, 1e-7 |E| in FP32 mixed).
  *   newton_max  Newton iterations per substep (1024 in Sec. III-B).
- *   pcg_max     PCG iterations per Newton iteration.
+ *   pcg_max     PCG iterations per Newton iteration (per env, also when it
+ *               runs in a batch with envs of other caps).
  *   precision   TC_FP64 (all device arithmetic in double) or TC_FP32_MIXED
  *               (element, barrier, PCG in float; energies, line-search and
  *               PCG dot-product accumulators in double; barrier distance in
@@ -125,6 +130,8 @@ typedef struct {
   double kappa;              /* barrier stiffness in use (N/m)              */
   size_t device_bytes;       /* device memory held by the env               */
   int64_t nnzb;              /* 3x3 blocks of the Newton matrix (free rows)  */
+  int64_t pcg_capped;        /* PCG solves that stopped at pcg_max above     */
+                             /* their tolerance (not an error, see TC_ERR_PCG_MAXITER) */
 } tc_info;
 
 /* Scene setup (row a0): rest shape Dm^-1 and volumes, lumped masses, boundary
@@ -147,7 +154,10 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material,
  * block-Jacobi PCG started from an earlier solve's solution d kept with the
  * env (the previous solve's; for the first solve of a substep, the previous
  * substep's first), scaled by the minimiser -g.d / d.A d of the quadratic
- * model along d; a fresh env starts from zero. */
+ * model along d; a fresh env starts from zero.  A step that fails
+ * (TC_ERR_NEWTON_MAXITER, TC_ERR_LINESEARCH, TC_ERR_NONFINITE) leaves the env
+ * as it was before the call: positions, velocities and indenter pose of the
+ * step start. */
 tc_status tc_step(tc_env* env, const tc_pose* target);
 
 /* One step of each of n independent envs (Algorithm 2, physics line, applied
@@ -207,11 +217,18 @@ tc_status tc_stress(tc_env* env, float* sigma_out);
  * to skip that output. */
 tc_status tc_traction(tc_env* env, float* t, float* p, float* t_tau);
 
-/* Pressure map: per-face pressure area-weighted to contact vertices (deformed
- * areas), interpolated barycentrically at every pixel of the grid given at
- * create time.  out: device float H x W; mask: device uint8 H x W (1 = pixel
- * covered by a contact face) or NULL. */
-tc_status tc_pressure_map(tc_env* env, float* out, uint8_t* mask);
+/* Pressure map on a sensor pixel grid (Sec. III-C: the traction field of
+ * Algorithm 1 splatted onto the sensor's pixels): per-face pressure
+ * area-weighted to contact vertices (deformed areas), interpolated
+ * barycentrically at every pixel of `grid`.  grid: host tc_grid, or NULL for
+ * the grid given at create time (TC_ERR_INVALID_ARG if there was none).  A
+ * grid is binned over the rest contact surface on its first use and the
+ * binning is kept with the env (the four most recently used grids besides
+ * the create-time one); invalid grids (H or W <= 0, equal or out-of-range
+ * axes, pixel sizes below 1 nm, non-finite values) give TC_ERR_INVALID_ARG.
+ * out: device float H x W; mask: device uint8 H x W (1 = pixel covered by a
+ * contact face) or NULL. */
+tc_status tc_pressure_map(tc_env* env, const tc_grid* grid, float* out, uint8_t* mask);
 
 /* Incremental potential at the current positions and indenter pose
  * (Algorithm 2's minimisation objective: elastic energy + kappa * barrier

@@ -109,11 +109,55 @@ template <class R> static tc_status contact_force(Env& env, double* out) {
   return st;
 }
 
-template <class R> static tc_status pressure_map(Env& env, float* out, uint8_t* mask) {
+// Binning tables of `grid` (NULL: the grid given at create time), binned on
+// first use and kept per env; the least recently used is dropped beyond
+// Env::kGridCache grids.
+static tc_status grid_table(Env& env, const tc_grid* grid, const int32_t** pf, const float** pw, int* npix) {
+  if (!grid || (env.H * env.W > 0 && same_grid(*grid, env.grid0))) {
+    if (env.H * env.W == 0) return TC_ERR_INVALID_ARG;
+    *pf = env.pix_face;
+    *pw = env.pix_w;
+    *npix = env.H * env.W;
+    return TC_OK;
+  }
+  if (!grid_valid(grid)) return TC_ERR_INVALID_ARG;
+  const uint64_t now = ++env.grid_clock;
+  for (auto& t : env.grid_tables)
+    if (same_grid(t.key, *grid)) {
+      t.last_use = now;
+      *pf = t.pix_face;
+      *pw = t.pix_w;
+      *npix = grid->H * grid->W;
+      return TC_OK;
+    }
+  if ((int)env.grid_tables.size() >= Env::kGridCache) {
+    auto old = std::min_element(env.grid_tables.begin(), env.grid_tables.end(),
+                                [](const Env::GridTable& a, const Env::GridTable& b) { return a.last_use < b.last_use; });
+    if (cudaStreamSynchronize(env.stream) != cudaSuccess) return TC_ERR_CUDA;
+    env.arena.put(old->pix_face);
+    env.arena.put(old->pix_w);
+    env.grid_tables.erase(old);
+  }
+  Env::GridTable t{*grid, nullptr, nullptr, now};
+  const tc_status st = bin_pixel_grid(env, grid, &t.pix_face, &t.pix_w);
+  if (st != TC_OK) return st;
+  env.grid_tables.push_back(t);
+  *pf = t.pix_face;
+  *pw = t.pix_w;
+  *npix = grid->H * grid->W;
+  return TC_OK;
+}
+
+template <class R> static tc_status pressure_map(Env& env, const tc_grid* grid, float* out, uint8_t* mask) {
+  const int32_t* pf = nullptr;
+  const float* pw = nullptr;
+  int npix = 0;
+  const tc_status st = grid_table(env, grid, &pf, &pw, &npix);
+  if (st != TC_OK) return st;
   EnvView<R> e = env.view<R>();
   launch_traction<R>(e, env.cparent, nullptr, nullptr, nullptr, env.face_p, env.face_A, env.stream);
   launch_vertex_avg(env.nvc, env.cv_face_off, env.cv_face_idx, env.face_p, env.face_A, env.vert_p, env.stream);
-  launch_splat(env.H * env.W, env.pix_face, env.pix_w, env.cface_slot, env.nfc, env.vert_p, out, mask, env.stream);
+  launch_splat(npix, pf, pw, env.cface_slot, env.nfc, env.vert_p, out, mask, env.stream);
   TC_CHECK(cudaGetLastError());
   TC_CHECK(cudaStreamSynchronize(env.stream));
   if (env.prof) env.prof->collect();
@@ -372,12 +416,12 @@ tc_status tc_traction(tc_env* h, float* t, float* p, float* t_tau) {
   return TC_OK;
 }
 
-tc_status tc_pressure_map(tc_env* h, float* out, uint8_t* mask) {
+tc_status tc_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint8_t* mask) {
   if (!h || !out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
   tc::ProfGuard pg(env);
-  if (env.H * env.W == 0) return TC_ERR_INVALID_ARG;
-  return env.precision == TC_FP64 ? tc::pressure_map<double>(env, out, mask) : tc::pressure_map<float>(env, out, mask);
+  return env.precision == TC_FP64 ? tc::pressure_map<double>(env, grid, out, mask)
+                                  : tc::pressure_map<float>(env, grid, out, mask);
 }
 
 tc_status tc_contact_force(tc_env* h, double* out) {
@@ -458,6 +502,7 @@ tc_status tc_env_info(tc_env* h, tc_info* info) {
   info->kappa = env.kappa;
   info->device_bytes = env.arena.bytes;
   info->nnzb = env.nnzb;
+  info->pcg_capped = env.stats.pcg_capped;
   return TC_OK;
 }
 

@@ -512,6 +512,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       StepCtl& c = tasks[P[j]];
       Env& e = *c.env;
       e.stats.pcg += pre[j].pcg_iters;
+      if (pre[j].pcg_capped) e.stats.pcg_capped++;
       if (pre[j].status & ST_NONFINITE) {
         fail(c, TC_ERR_NONFINITE);
         continue;
@@ -650,6 +651,16 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     b_step_vectors<R>(X.host, 1, X.stream);
     TC_CHECK(cudaStreamSynchronize(X.stream));
   }
+  // a failed step leaves its env as it was before the step: displacement of
+  // the step start (kept in u0), indenter pose of the step start; the
+  // velocity is only written by a completed step
+  for (StepCtl& c : tasks)
+    if (c.phase == StepCtl::FAILED) {
+      Env& e = *c.env;
+      TC_CHECK(cudaMemcpyAsync(e.u, e.ut, sizeof(R) * 3 * (size_t)e.nv, cudaMemcpyDeviceToDevice, X.stream));
+      e.pose = c.pose0;
+      e.cand_valid = false;
+    }
   std::vector<StepCtl> keep;
   for (StepCtl& c : tasks) {
     if (c.phase == StepCtl::DONE) finished.push_back({c.tag, c.env, TC_OK});

@@ -40,6 +40,7 @@ struct Scalars {
   int pcg_done;        // set when |r| <= tol
   int pcg_iters;       // iterations taken by the last solve
   int overflow;        // grid/pair capacity overflow
+  int pcg_capped;      // the last solve stopped at the env's pcg_max above its tolerance
 };
 
 template <class R> struct Vec3 {

@@ -60,6 +60,7 @@ template <class R> struct EnvView {
   R mu, lam_hat, alpha;       // material (rest-stable Neo-Hookean)
   R inv_h2;                   // 1/dt^2 (dynamic) or 0
   double dhat, kappa;
+  int pcg_max;                // this env's PCG iteration cap
   // topology
   const int4* tets;
   const double* X0;           // rest positions, SoA x|y|z, each nv
@@ -186,6 +187,7 @@ TC_HD int units_for(int count, int kind) { return (count + unit_items(kind) - 1)
 
 struct EnvStats {
   int64_t newton = 0, pcg = 0, substeps = 0, steps = 0, halvings = 0;
+  int64_t pcg_capped = 0;  // PCG solves that stopped at pcg_max above their tolerance
 };
 
 // Host-side environment.
@@ -214,8 +216,20 @@ struct Env {
   int32_t *cface_slot = nullptr;  // 3 x nfc contact-vertex slots of each face
   int32_t *cv_face_off = nullptr, *cv_face_idx = nullptr, *cv_edge_off = nullptr, *cv_edge_idx = nullptr;
   double* gel_elen2 = nullptr;
-  int32_t* pix_face = nullptr;
+  int32_t* pix_face = nullptr;   // binning of the grid given at create time (grid0)
   float* pix_w = nullptr;
+  tc_grid grid0{};
+  // binnings of other grids passed to tc_pressure_map, least recently used
+  // first out once more than kGridCache are held
+  struct GridTable {
+    tc_grid key;
+    int32_t* pix_face;
+    float* pix_w;
+    uint64_t last_use;
+  };
+  static constexpr int kGridCache = 4;
+  std::vector<GridTable> grid_tables;
+  uint64_t grid_clock = 0;
   // indenter
   double* IV = nullptr;
   float *IVhi = nullptr, *IVlo = nullptr;
@@ -267,7 +281,7 @@ template <class R> EnvView<R> Env::view() const {
   e.ind_nv = ind_nv; e.ind_nf = ind_nf; e.ind_ne = ind_ne; e.npix = H * W;
   e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
-  e.dhat = dhat; e.kappa = kappa;
+  e.dhat = dhat; e.kappa = kappa; e.pcg_max = pcg_max;
   e.tets = tets; e.X0 = X0; e.X0f = X0f; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
   e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.eslot = (R*)eslot; e.kblk = (R*)kblk;
   e.nnzb = nnzb; e.bsr_rp = bsr_rp; e.bsr_ci = bsr_ci; e.bsr_diag = bsr_diag; e.bsr_val = (R*)bsr_val;
@@ -302,6 +316,11 @@ template <class R> EnvView<R> Env::view() const {
 
 tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32_t nfixed,
                       const tc_trimesh* ind, const tc_grid* grid);
+// Pixel binning of a sensor grid over the env's rest contact surface
+// (device tables allocated from the env's arena); grid checks.
+tc_status bin_pixel_grid(Env& env, const tc_grid* grid, int32_t** pix_face, float** pix_w);
+bool grid_valid(const tc_grid* g);
+bool same_grid(const tc_grid& a, const tc_grid& b);
 // BSR pattern and fixed-order contribution lists of the Newton matrix
 // (host build from the host tets, after setup_scene)
 tc_status build_bsr(Env& env, const int32_t* tets, const int32_t* fixed_ids, int32_t nfixed);

@@ -354,6 +354,53 @@ __global__ void k_bin_weights(const int32_t* cfaces, int nfc, const double* X, i
   w[2 * npix + i] = w2;
 }
 
+bool grid_valid(const tc_grid* g) {
+  if (!g || g->H <= 0 || g->W <= 0 || (int64_t)g->H * g->W > (int64_t)INT32_MAX / 3) return false;
+  if (g->axis_u < 0 || g->axis_u > 2 || g->axis_v < 0 || g->axis_v > 2 || g->axis_u == g->axis_v) return false;
+  for (int k = 0; k < 2; ++k)
+    if (!std::isfinite(g->origin[k]) || !std::isfinite(g->pixel[k])) return false;
+  return std::nearbyint(g->pixel[0] * 1e9) > 0 && std::nearbyint(g->pixel[1] * 1e9) > 0;
+}
+
+bool same_grid(const tc_grid& a, const tc_grid& b) {
+  return a.axis_u == b.axis_u && a.axis_v == b.axis_v && a.origin[0] == b.origin[0] && a.origin[1] == b.origin[1] &&
+         a.pixel[0] == b.pixel[0] && a.pixel[1] == b.pixel[1] && a.H == b.H && a.W == b.W;
+}
+
+// Covering contact face and FP32 barycentric weights of every pixel of
+// `grid` over the rest contact surface (the binning reading of the pixel
+// map: nanometre-snapped coordinates, exact edge functions, lowest face wins).
+// Allocates the two tables from the env's arena on the env's stream.
+tc_status bin_pixel_grid(Env& env, const tc_grid* grid, int32_t** pix_face, float** pix_w) {
+  if (!grid_valid(grid)) return TC_ERR_INVALID_ARG;
+  Arena& a = env.arena;
+  cudaStream_t s = env.stream;
+  const int npix = grid->H * grid->W;
+  PixGrid g;
+  g.au = grid->axis_u;
+  g.av = grid->axis_v;
+  g.H = grid->H;
+  g.W = grid->W;
+  g.u0 = 2ll * (long long)std::nearbyint(grid->origin[0] * 1e9);
+  g.v0 = 2ll * (long long)std::nearbyint(grid->origin[1] * 1e9);
+  g.du = (long long)std::nearbyint(grid->pixel[0] * 1e9);
+  g.dv = (long long)std::nearbyint(grid->pixel[1] * 1e9);
+  int32_t* pf = a.alloc<int32_t>(npix);
+  float* pw = a.alloc<float>(3 * (int64_t)npix);
+  if (!pf || !pw) {
+    if (pf) a.put(pf);
+    if (pw) a.put(pw);
+    return TC_ERR_OOM;
+  }
+  k_fill_i32<<<grid_for(npix), kBlock, 0, s>>>(pf, npix, 0x7fffffff);
+  if (env.nfc > 0) k_bin_faces<<<grid_for(env.nfc), kBlock, 0, s>>>(env.cfaces, env.nfc, env.X0, env.nv, g, pf);
+  k_bin_weights<<<grid_for(npix), kBlock, 0, s>>>(env.cfaces, env.nfc, env.X0, env.nv, g, pf, pw);
+  if (cudaGetLastError() != cudaSuccess) return TC_ERR_CUDA;
+  *pix_face = pf;
+  *pix_w = pw;
+  return TC_OK;
+}
+
 // ----------------------------------------------------------- indenter grid
 
 // FP32 hi/lo pair of each indenter coordinate (x = hi + lo to ~2^-48 relative)
@@ -764,26 +811,13 @@ tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed_ids, i
     a.put(part);
   }
   // --- pixel binning
-  if (grid && grid->H > 0 && grid->W > 0) {
+  if (grid) {
+    st = bin_pixel_grid(env, grid, &env.pix_face, &env.pix_w);
+    if (st != TC_OK) return st;
     env.H = grid->H;
     env.W = grid->W;
+    env.grid0 = *grid;
     const int npix = env.H * env.W;
-    PixGrid g;
-    g.au = grid->axis_u;
-    g.av = grid->axis_v;
-    g.H = env.H;
-    g.W = env.W;
-    g.u0 = 2ll * (long long)std::nearbyint(grid->origin[0] * 1e9);
-    g.v0 = 2ll * (long long)std::nearbyint(grid->origin[1] * 1e9);
-    g.du = (long long)std::nearbyint(grid->pixel[0] * 1e9);
-    g.dv = (long long)std::nearbyint(grid->pixel[1] * 1e9);
-    if (g.du <= 0 || g.dv <= 0) return TC_ERR_INVALID_ARG;
-    env.pix_face = a.alloc<int32_t>(npix);
-    env.pix_w = a.alloc<float>(3 * (int64_t)npix);
-    if (!env.pix_face || !env.pix_w) return TC_ERR_OOM;
-    k_fill_i32<<<grid_for(npix), kBlock, 0, s>>>(env.pix_face, npix, 0x7fffffff);
-    if (nfc > 0) k_bin_faces<<<grid_for(nfc), kBlock, 0, s>>>(env.cfaces, nfc, env.X0, nv, g, env.pix_face);
-    k_bin_weights<<<grid_for(npix), kBlock, 0, s>>>(env.cfaces, nfc, env.X0, nv, g, env.pix_face, env.pix_w);
     env.h_pix_face.resize(npix);
     env.h_pix_w.resize(3 * (size_t)npix);
     std::vector<float> soa(3 * (size_t)npix);

@@ -654,6 +654,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     s_sc[1] = es[4];
   }
   bool done = es[2] != 0.0;
+  // each env stops at its own cap (max_iter bounds the launch as a whole), so
+  // its iterations do not depend on the caps of the other envs in the batch
+  const int cap = ev.pcg_max > 0 ? min(max_iter, ev.pcg_max) : max_iter;
   R beta = R(0);
   int it = 0;
   while (!done) {
@@ -877,7 +880,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
         s_coef = A::positive(s_at[0]) ? (R)A::ratio(x, s_at[0]) : R(0);
         s_at[0] = x;
         s_sc[0] = rr;
-        s_flag = (rr <= s_sc[1] || !A::positive(s_at[1]) || !isfinite(rr) || it + 1 >= max_iter) ? 1 : 0;
+        s_flag = (rr <= s_sc[1] || !A::positive(s_at[1]) || !isfinite(rr) || it + 1 >= cap) ? 1 : 0;
       }
     }
     __syncthreads();
@@ -896,6 +899,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     Scalars* sc = ev.sc;
     const double rr = s_sc[0], pq = A::to_double(s_at[1]);
     sc->pcg_iters = it;
+    sc->pcg_capped = (it >= cap && !(rr <= s_sc[1])) ? 1 : 0;
     sc->rz = A::to_double(s_at[0]);
     sc->rr = rr;
     sc->pq = pq;

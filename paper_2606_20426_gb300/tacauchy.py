@@ -97,7 +97,8 @@ class Info(ctypes.Structure):
                 ("ind_nf", ctypes.c_int32), ("ind_ne", ctypes.c_int32), ("H", ctypes.c_int32),
                 ("W", ctypes.c_int32), ("newton_iters", ctypes.c_int64), ("pcg_iters", ctypes.c_int64),
                 ("substeps", ctypes.c_int64), ("steps", ctypes.c_int64), ("line_search_halvings", ctypes.c_int64),
-                ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("nnzb", ctypes.c_int64)]
+                ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("nnzb", ctypes.c_int64),
+                ("pcg_capped", ctypes.c_int64)]
 
 
 _lib = None
@@ -120,7 +121,7 @@ def load():
         "tc_step_batch": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(Pose), ctypes.POINTER(ctypes.c_int32)],
         "tc_stress": [P, P],
         "tc_traction": [P, P, P, P],
-        "tc_pressure_map": [P, P, P],
+        "tc_pressure_map": [P, ctypes.POINTER(Grid), P, P],
         "tc_contact_force": [P, P],
         "tc_energy_gradient": [P, P, P],
         "tc_surface_faces": [P, P, P],
@@ -184,6 +185,12 @@ def make_pose(p):
     return out
 
 
+def make_grid(g):
+    """dict(axis_u, axis_v, origin, pixel, H, W) -> Grid."""
+    return Grid(int(g["axis_u"]), int(g["axis_v"]), (ctypes.c_double * 2)(*[float(v) for v in g["origin"]]),
+                (ctypes.c_double * 2)(*[float(v) for v in g["pixel"]]), int(g["H"]), int(g["W"]))
+
+
 class _TorchAllocator:
     """tc_allocator backed by the PyTorch caching allocator."""
 
@@ -207,7 +214,9 @@ class _TorchAllocator:
 class Env:
     """One simulated sensor: gel pad + rigid indenter + pixel grid."""
 
-    def __init__(self, env, precision=None, stream=None, torch_allocator=True):
+    def __init__(self, env, precision=None, stream=None, torch_allocator=True, allocator=None):
+        """allocator: an object whose `.struct` is an Allocator (tc_allocator)
+        to use instead of the PyTorch caching allocator."""
         torch = _torch()
         lib = load()
         self.torch, self.lib = torch, lib
@@ -228,12 +237,12 @@ class Env:
                          o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1))
         ind = TriMesh(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
         g = env.get("grid")
-        grid = None
-        if g is not None:
-            grid = Grid(g["axis_u"], g["axis_v"], (ctypes.c_double * 2)(*g["origin"]),
-                        (ctypes.c_double * 2)(*g["pixel"]), g["H"], g["W"])
+        grid = make_grid(g) if g is not None else None
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self._allocator = _TorchAllocator(torch) if torch_allocator else None
+        if allocator is not None:
+            self._allocator = allocator
+        else:
+            self._allocator = _TorchAllocator(torch) if torch_allocator else None
         handle = ctypes.c_void_p()
         pose = make_pose(env["start_pose"])
         code = lib.tc_create_scene(ctypes.byref(mesh), ctypes.byref(mat), fixed.ctypes.data, len(fixed),
@@ -272,13 +281,21 @@ class Env:
                                     ctypes.c_void_p(tt.data_ptr())), "tc_traction")
         return t, p, tt
 
-    def pressure_map(self, out=None, mask=None, want_mask=True):
-        H, W = self.info["H"], self.info["W"]
+    def pressure_map(self, out=None, mask=None, want_mask=True, grid=None):
+        """(H, W) float32 map and uint8 mask on `grid` (a dict like the env's
+        "grid" entry), or on the grid given at create time when None."""
+        if grid is None:
+            H, W = self.info["H"], self.info["W"]
+            g = None
+        else:
+            H, W = int(grid["H"]), int(grid["W"])
+            g = make_grid(grid)
         if out is None:
             out = self.torch.empty((H, W), dtype=self.torch.float32, device="cuda")
         if mask is None and want_mask:
             mask = self.torch.empty((H, W), dtype=self.torch.uint8, device="cuda")
-        _check(self.lib.tc_pressure_map(self.h, ctypes.c_void_p(out.data_ptr()),
+        _check(self.lib.tc_pressure_map(self.h, ctypes.byref(g) if g is not None else None,
+                                        ctypes.c_void_p(out.data_ptr()),
                                         ctypes.c_void_p(mask.data_ptr()) if mask is not None else None),
                "tc_pressure_map")
         return out, mask

@@ -142,3 +142,61 @@ def test_no_grid_and_far_indenter():
     with pytest.raises(TcError):
         g.pressure_map()
     g.close()
+
+
+def _other_grids(env):
+    """Grids besides the create-time one: finer, coarser, shifted, and swapped
+    axes (rows along the other side)."""
+    g0 = env["grid"]
+    out = []
+    for (fh, fw), shift, swap in [((2, 2), (0.0, 0.0), False), ((0.5, 0.75), (0.0, 0.0), False),
+                                  ((1, 1), (0.3, -0.2), False), ((1, 1), (0.0, 0.0), True),
+                                  ((1.5, 1.25), (0.1, 0.1), False)]:
+        H, W = max(1, int(g0["H"] * fh)), max(1, int(g0["W"] * fw))
+        pix = (g0["pixel"][0] * g0["W"] / W, g0["pixel"][1] * g0["H"] / H)
+        origin = (g0["origin"][0] + shift[0] * pix[0], g0["origin"][1] + shift[1] * pix[1])
+        g = dict(axis_u=g0["axis_u"], axis_v=g0["axis_v"], origin=origin, pixel=pix, H=H, W=W)
+        if swap:
+            g = dict(axis_u=g0["axis_v"], axis_v=g0["axis_u"], origin=origin[::-1], pixel=pix[::-1], H=W, W=H)
+        out.append(g)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_pressure_map_on_caller_grids(precision):
+    """tc_pressure_map(env, grid): each grid is binned on first use (masks
+    bit-exact against the oracle's exact binning of that grid, maps within
+    1e-3), kept (a second call is bit-identical), and more grids than the
+    cache holds still give the right maps; NULL is the create-time grid;
+    invalid grids are refused."""
+    from paper_2606_20426_gb300 import TcError
+    env = workloads.small_env(0, steps=1)
+    g = _gpu_env(env, precision)
+    g.step(env["poses"][0])
+    x = g.positions()
+    base, _ = g.pressure_map()
+    grids = _other_grids(env)
+    first = {}
+    for rnd in range(2):
+        for i, gr in enumerate(grids):
+            e2 = dict(env)
+            e2["grid"] = gr
+            ref = Scene(e2)
+            mref, mask_ref = ref.pressure_map(x=x)
+            m, mask = g.pressure_map(grid=gr)
+            m, mask = m.cpu().numpy(), mask.cpu().numpy()
+            assert m.shape == (gr["H"], gr["W"])
+            assert np.array_equal(mask, mask_ref)
+            assert np.abs(mref).max() > 0 and rel_fro(m, mref) <= 1e-3
+            if rnd == 0:
+                first[i] = m
+            else:
+                assert np.array_equal(m, first[i])
+    again, _ = g.pressure_map(grid=env["grid"])
+    assert np.array_equal(again.cpu().numpy(), base.cpu().numpy())
+    for bad in [dict(env["grid"], H=0), dict(env["grid"], axis_u=1, axis_v=1),
+                dict(env["grid"], pixel=(0.0, 1e-3)), dict(env["grid"], axis_v=3)]:
+        with pytest.raises(TcError) as ei:
+            g.pressure_map(grid=bad, out=base.new_empty((max(bad["H"], 1), bad["W"])), mask=None, want_mask=False)
+        assert ei.value.code == 1
+    g.close()
