@@ -35,6 +35,7 @@ import scipy.sparse.linalg as spla
 from . import material as mat
 from . import mesh as msh
 from . import geometry as geo
+from . import friction as fric
 from .ccd import accd
 
 
@@ -126,6 +127,11 @@ class Scene:
         self.gabs = 1e-12 * self.E * L * L
         self.ptol = 1e-4 * self.dhat
         self.max_substeps = 256
+        # lagged friction (dynamic scenes only): friction ratio and velocity threshold
+        self.mu_f = float(o.get("friction_mu", 0.0))
+        self.eps_v = float(o.get("friction_eps_v", 0.01))
+        self.friction = self.dynamic and self.mu_f > 0
+        self._fric = None     # (lagged pairs, x at the step start, indenter at the step start)
         # state
         self.x = X.copy()
         self.v = np.zeros_like(X)
@@ -255,10 +261,17 @@ class Scene:
             terms.append((gv[:, slots], g[:, dof], Hg))
         return total, terms
 
+    def friction_terms(self, x, Y, need_hess=True):
+        """Lagged friction potential of the current substep (0 when off)."""
+        if self._fric is None:
+            return 0.0, []
+        pairs, x_t, Y_t = self._fric
+        return fric.potential(self, pairs, x, x_t, Y, Y_t, self.mu_f, self.eps_v * self.h, need_hess)
+
     def energy(self, x, Y, cand, x_tilde=None):
         Ee, _, _ = self.elastic(x, need_hess=False)
         Eb, _ = self.barrier_terms(x, Y, cand, need_hess=False)
-        E = Ee + Eb
+        E = Ee + Eb + self.friction_terms(x, Y, need_hess=False)[0]
         if self.dynamic:
             dx = x - x_tilde
             E += 0.5 / (self.h * self.h) * float(np.sum(self.mass[:, None] * dx * dx))
@@ -268,6 +281,9 @@ class Scene:
         cand = self.candidates(x, Y)
         Ee, ge, He = self.elastic(x)
         Eb, terms = self.barrier_terms(x, Y, cand)
+        Ef, fterms = self.friction_terms(x, Y)
+        Eb += Ef
+        terms = terms + fterms
         n3 = 3 * self.nv
         g = np.zeros(n3)
         dof = (3 * self.T[:, :, None] + np.arange(3)[None, None, :]).reshape(-1, 12)
@@ -355,6 +371,8 @@ class Scene:
         s = 0.0
         for sub in range(self.max_substeps):
             Ys = (1.0 - s) * Y0 + s * Y1
+            if self.friction:  # lagged at the converged state before this substep's advance
+                self._fric = (fric.lag(self, x, Ys), x_t, Y0)
             frac, _ = self.ccd_alpha(x, np.zeros_like(x), Ys, Y1)
             s = 1.0 if frac >= 1.0 else s + (1.0 - s) * frac
             Ys = (1.0 - s) * Y0 + s * Y1
@@ -422,10 +440,13 @@ class Scene:
 
     def contact_force(self, x=None):
         """Total force the indenter exerts on the gel: sum_k f_k with
-        f_k = -kappa dB/dx_k (Algorithm 2, f_k = -g_k / dt^2)."""
+        f_k = -kappa dB/dx_k (Algorithm 2, f_k = -g_k / dt^2), plus the
+        lagged friction force -dD/dx_k of the last substep when friction is
+        on."""
         x = self.x if x is None else x
         Y = self.indenter(self.pose)
         _, terms = self.barrier_terms(x, Y, self.candidates(x, Y))
+        terms = terms + self.friction_terms(x, Y)[1]
         f = np.zeros(3)
         for gv, gg, _ in terms:
             f -= gg.reshape(len(gv), -1, 3).sum(axis=(0, 1))
