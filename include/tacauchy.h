@@ -89,10 +89,23 @@ typedef struct { double E, nu, density; } tc_material;
  *               PCG dot-product accumulators in double; barrier distance in
  *               double for pairs closer than 1e-2 dhat).
  *   contact_axis thickness axis 0/1/2; -1 = thinnest bounding-box axis
- *               (Sec. III-A). */
+ *               (Sec. III-A).
+ *   friction_mu friction ratio of the lagged IPC friction (Sec. III-B gives
+ *               0.5); 0 = frictionless.  Acts only when dt > 0.
+ *   friction_eps_v velocity threshold of the friction smoothing in m/s
+ *               (Sec. III-B gives 0.01); <= 0 selects 0.01.
+ * Friction (IPC lagged friction, Li et al. 2020): at the start of each
+ * indenter substep every contact pair within dhat fixes its normal force
+ * lambda = kappa m(c) |b'(d)|, the normal of its closest-point vector and its
+ * closest-point weights; the substep's potential adds
+ * sum_k mu lambda_k f0(|P_k rel_k|), rel_k the relative displacement of the
+ * pair's closest points since the step start (indenter points moving with the
+ * kinematic pose), P_k the projection on the lagged tangent plane, f0 the C1
+ * smoothing of |.| below eps_v dt. */
 typedef struct {
   double dhat, kappa, dt, newton_rtol;
   int32_t newton_max, pcg_max, precision, contact_axis;
+  double friction_mu, friction_eps_v;
 } tc_scene_opts;
 
 /* Rigid indenter surface in its body frame.  V: host nv x 3; F: host nf x 3. */
@@ -229,6 +242,22 @@ tc_status tc_traction(tc_env* env, float* t, float* p, float* t_tau);
  * out: device float H x W; mask: device uint8 H x W (1 = pixel covered by a
  * contact face) or NULL. */
 tc_status tc_pressure_map(tc_env* env, const tc_grid* grid, float* out, uint8_t* mask);
+
+/* Stress and pressure maps of several envs at once (Sec. III-C, Eq. 4 and
+ * Algorithm 1 over every env): one launch computes sigma of every tet and the
+ * pressure and area of every contact face of all the envs, averages to their
+ * contact vertices and splats to their pixel grids (the create-time grids),
+ * with a grid-wide barrier between those three phases.  The outputs equal,
+ * bit for bit, what tc_stress and tc_pressure_map(env, NULL, ...) write for
+ * each env.  envs: host array of n distinct envs of one precision and device
+ * (none with a server request pending); sigma_out, map_out, mask_out: host
+ * arrays of n device pointers (layouts as tc_stress and tc_pressure_map), each
+ * array and each entry may be NULL to skip that output (a mask needs its map,
+ * a map needs an env created with a grid: else TC_ERR_INVALID_ARG).  The work
+ * runs on the first env's stream after every other env's stream has drained;
+ * n = 0 is a no-op.  Not in the paper (which extracts one env per call). */
+tc_status tc_extract_batch(tc_env** envs, int32_t n, float* const* sigma_out, float* const* map_out,
+                           uint8_t* const* mask_out);
 
 /* Incremental potential at the current positions and indenter pose
  * (Algorithm 2's minimisation objective: elastic energy + kappa * barrier

@@ -9,4 +9,4 @@ The compute lives in libtacauchy.so (CUDA, C ABI in include/tacauchy.h);
 """
 from . import tacauchy  # noqa: F401
 from .tacauchy import (Env, Server, TcError, autotune_pcg, load, pcg_shape, step_batch,  # noqa: F401
-                       stress_from_F)
+                       stress_from_F, extract_batch)

@@ -269,11 +269,19 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   env.newton_max = opts->newton_max > 0 ? opts->newton_max : 1024;
   env.pcg_max = opts->pcg_max > 0 ? opts->pcg_max : 1000;
   env.thick_axis = opts->contact_axis;
+  if (!(opts->friction_mu >= 0.0) || !std::isfinite(opts->friction_mu)) {
+    delete h;
+    return TC_ERR_INVALID_ARG;
+  }
+  env.mu_f = opts->friction_mu;
+  env.eps_v = opts->friction_eps_v > 0 && std::isfinite(opts->friction_eps_v) ? opts->friction_eps_v : 0.01;
+  env.friction = env.dynamic && env.mu_f > 0.0;
   // Newton step tolerance: 1e-4 dhat in FP64; FP32 gradients carry rounding
   // noise of ~1e-5 of the contact force, whose Newton step is ~10 nm, so the
   // mixed mode stops at 1e-3 dhat.
   env.ptol = (env.precision == TC_FP64 ? 1e-4 : 1e-3) * env.dhat;
   env.pose = *start_pose;
+  env.pose_start = *start_pose;
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int v = 0; v < mesh->nv; ++v)
     for (int d = 0; d < 3; ++d) {
@@ -424,6 +432,36 @@ tc_status tc_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint8_t* m
                                   : tc::pressure_map<float>(env, grid, out, mask);
 }
 
+tc_status tc_extract_batch(tc_env** envs, int32_t n, float* const* sigma_out, float* const* map_out,
+                           uint8_t* const* mask_out) {
+  if (n < 0 || (n > 0 && !envs)) return TC_ERR_INVALID_ARG;
+  if (n == 0) return TC_OK;
+  std::vector<Env*> set;
+  std::vector<float*> sig(n, nullptr), map(n, nullptr);
+  std::vector<uint8_t*> mask(n, nullptr);
+  for (int i = 0; i < n; ++i) {
+    if (!envs[i] || envs[i]->impl.busy.load()) return TC_ERR_INVALID_ARG;
+    Env& e = envs[i]->impl;
+    if (e.precision != envs[0]->impl.precision || e.device != envs[0]->impl.device) return TC_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (envs[j] == envs[i]) return TC_ERR_INVALID_ARG;
+    sig[i] = sigma_out ? sigma_out[i] : nullptr;
+    map[i] = map_out ? map_out[i] : nullptr;
+    mask[i] = mask_out ? mask_out[i] : nullptr;
+    if (mask[i] && !map[i]) return TC_ERR_INVALID_ARG;
+    if (map[i] && e.H * e.W == 0) return TC_ERR_INVALID_ARG;
+    set.push_back(&e);
+  }
+  Env& lead = *set[0];
+  for (Env* e : set)
+    if (e->stream != lead.stream && cudaStreamSynchronize(e->stream) != cudaSuccess) return TC_ERR_CUDA;
+  tc::ProfGuard pg(lead);
+  const tc_status st = lead.precision == TC_FP64 ? tc::extract_batch<double>(set, sig, map, mask, lead.stream)
+                                                 : tc::extract_batch<float>(set, sig, map, mask, lead.stream);
+  if (lead.prof) lead.prof->collect();
+  return st;
+}
+
 tc_status tc_contact_force(tc_env* h, double* out) {
   if (!h || !out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
@@ -550,6 +588,7 @@ void tc_destroy(tc_env* h) {
   env.arena.release_all();
   cudaStreamSynchronize(env.stream);
   if (env.sc_host) cudaFreeHost(env.sc_host);
+  if (env.x_host) cudaFreeHost(env.x_host);
   delete h;
 }
 

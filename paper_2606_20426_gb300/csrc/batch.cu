@@ -268,6 +268,29 @@ tc_status alloc_candidates(Env& env, int cap) {
   return TC_OK;
 }
 
+// Lagged-friction pair arrays sized for the current candidate capacity (the
+// lagged pairs of a primitive are among its candidates).  Call with the
+// batch stream idle.
+template <class R> static tc_status ensure_friction(Env& env, cudaStream_t batch_stream) {
+  if (!env.friction || (env.fr_cap == env.cand_cap && env.fr_n[0])) return TC_OK;
+  Arena& a = env.arena;
+  const int n[3] = {env.nvc, env.nec, env.nfc};
+  const int cap = env.cand_cap;
+  for (int k = 0; k < 3; ++k) {
+    a.put(env.fr_n[k]);
+    a.put(env.fr_ip[k]);
+    a.put(env.fr_val[k]);
+    env.fr_n[k] = a.alloc<int32_t>(std::max(n[k], 1));
+    env.fr_ip[k] = a.alloc<int32_t>((int64_t)cap * std::max(n[k], 1));
+    env.fr_val[k] = a.alloc<R>((int64_t)8 * cap * std::max(n[k], 1));
+    if (!env.fr_n[k] || !env.fr_ip[k] || !env.fr_val[k]) return TC_ERR_OOM;
+    TC_CHECK(cudaMemsetAsync(env.fr_n[k], 0, sizeof(int32_t) * std::max(n[k], 1), env.stream));
+  }
+  env.fr_cap = cap;
+  if (env.stream != batch_stream) TC_CHECK(cudaStreamSynchronize(env.stream));
+  return TC_OK;
+}
+
 static Motion make_motion(const tc_pose& a, const tc_pose& b, int use_dir) {
   Motion m;
   std::memcpy(m.Ra, a.R, sizeof(m.Ra));
@@ -387,6 +410,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     b_step_vectors<R>(X.host, 0, X.stream);
     for (int i : S) {
       tasks[i].pose0 = tasks[i].env->pose;
+      tasks[i].env->pose_start = tasks[i].env->pose;
       tasks[i].phase = StepCtl::ADVANCE;
     }
   }
@@ -411,6 +435,18 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
     }
     std::vector<Scalars> sc;
     if (!set.empty() && (st = ccd_phase<R>(X, set, mot, false, sc)) != TC_OK) return st;
+    // lagged friction of the substep, at the converged state and the pose
+    // before the advance (the candidate lists cover the advance's sweep)
+    std::vector<Env*> fset;
+    for (Env* e : set)
+      if (e->friction) {
+        if ((st = ensure_friction<R>(*e, X.stream)) != TC_OK) return st;
+        fset.push_back(e);
+      }
+    if (!fset.empty()) {
+      if ((st = X.build(fset, nullptr, nullptr)) != TC_OK) return st;
+      b_friction_lag<R>(X.host, X.stream);
+    }
     for (size_t j = 0; j < live.size(); ++j) {
       StepCtl& c = tasks[live[j]];
       const double frac = sc[j].ccd_t;

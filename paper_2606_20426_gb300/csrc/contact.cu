@@ -345,6 +345,171 @@ TC_D void prefix128(int* s_off) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------ friction
+// Lagged IPC friction (Li et al. 2020) with the friction ratio and velocity
+// threshold of Sec. III-B.  At the start of each indenter substep every
+// candidate pair within dhat (at the converged gel state and the pre-advance
+// pose) fixes its normal force lambda = kappa m(c) |b'(d)|, the world-frame
+// unit normal n of its closest-point vector r = sum_i w_i x_i, and the
+// weights w (all in FP64, rounded once).  During the substep's Newton solve
+// the pair adds mu lambda f0(y), y = |P rel|, P = I - n n^T, rel = sum_i w_i
+// (x_i - x_i^t) the closest points' relative displacement since the step
+// start (gel points: u - u0; indenter points: (R - R0) V + (t - t0)), with
+// f0 the C1 smoothing of |.| below eps_x = eps_v dt.  Gradient w.r.t. rel:
+// mu lambda (f1 / y) P rel; Hessian mu lambda [(f1 / y) P + (f1' y - f1) / y^3
+// u u^T], PSD (eigenvalues f1' >= 0 along u, f1 / y across it, 0 along n).
+
+// slot of gel point l in the pair's 4 points, and the indenter slots
+template <int GK> TC_HD int gel_pair_slot(int l) { return GK == GF ? 1 + l : l; }
+
+template <class R, int GK>
+TC_D void friction_lag_prim(const EnvView<R>& e, int prim) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  const int n = prim_count(e, GK);
+  const int kind = GK == GE ? 1 : 0;
+  const int kept = min(e.cand_n[GK][prim], e.cand_cap);
+  int cnt = 0;
+  if (kept > 0) {
+    double bw[3][3];
+    Origin o;
+    contact_prim_points<R, GK>(e, e.u, prim, bw, &o);
+    Vec3<double> xg[NGP];
+    for (int l = 0; l < NGP; ++l) xg[l] = rel<double>(bw[l], o.d);
+    for (int j = 0; j < kept; ++j) {
+      const int ip = e.cand[GK][(int64_t)j * n + prim];
+      Vec3<double> x[4];
+      pair_points<double, R, GK>(e, xg, ip, o, x);
+      int which;
+      const double d = sqrt(pair_dist2<double>(kind, x, &which));
+      if (!(d < e.dhat) || !(d > 0.0) || which < 0) continue;
+      double b, b1, b2;
+      barrier3<double>(d, e.dhat, &b, &b1, &b2);
+      double m = 1.0;
+      if (GK == GE) {
+        double mt, mtt, gt[6];
+        mollifier_t<double>(x, 1e-3 * e.gel_elen2[prim] * e.ind_elen2[ip], &m, &mt, &mtt, gt);
+      }
+      const CandEval<double> ev = eval_cand<double>(kind == 0 ? c_pt_cand[which] : c_ee_cand[which], x);
+      const double rn = sqrt(ev.r.x * ev.r.x + ev.r.y * ev.r.y + ev.r.z * ev.r.z);
+      if (!(rn > 0.0)) continue;
+      const double nb[3] = {ev.r.x / rn, ev.r.y / rn, ev.r.z / rn};
+      double vals[8];
+      vals[0] = e.kappa * m * (-b1);
+      for (int i = 0; i < 3; ++i)  // body -> world
+        vals[1 + i] = e.Rm[3 * i + 0] * nb[0] + e.Rm[3 * i + 1] * nb[1] + e.Rm[3 * i + 2] * nb[2];
+      for (int q = 0; q < 4; ++q) vals[4 + q] = ev.w[q];
+      e.fr_ip[GK][(int64_t)cnt * n + prim] = ip;
+      for (int q = 0; q < 8; ++q) e.fr_val[GK][((int64_t)8 * cnt + q) * n + prim] = (R)vals[q];
+      ++cnt;
+    }
+  }
+  e.fr_n[GK][prim] = cnt;
+}
+
+// one unit = 128 gel primitives of one kind; edges, faces, vertices in one launch
+template <class R> __global__ void __launch_bounds__(128) k_friction_lag(const BatchView<R> bv, int ne, int nf) {
+  int unit = blockIdx.x, gk;
+  if (unit < ne) gk = GE;
+  else if (unit < ne + nf) { gk = GF; unit -= ne; }
+  else { gk = GV; unit -= ne + nf; }
+  const Loc lc = locate(bv.prefix, bv.nenv, K_CV + gk, unit);
+  const EnvView<R>& e = bv.views[lc.env];
+  const int prim = lc.chunk * 128 + (int)threadIdx.x;
+  if (e.mu_f <= R(0) || e.fr_n[gk] == nullptr) return;
+  if (gk == GE) { if (prim < e.nec) friction_lag_prim<R, GE>(e, prim); }
+  else if (gk == GF) { if (prim < e.nfc) friction_lag_prim<R, GF>(e, prim); }
+  else if (prim < e.nvc) friction_lag_prim<R, GV>(e, prim);
+}
+
+template <class R> void b_friction_lag(const BatchHost<R>& b, cudaStream_t s) {
+  const int nv = b.units[K_CV], ne = b.units[K_CE], nf = b.units[K_CF];
+  if (nv + ne + nf == 0) return;
+  TC_LAUNCH("k_friction_lag", s, k_friction_lag<R><<<nv + ne + nf, 128, 0, s>>>(b.bv, ne, nf));
+}
+
+// Friction of gel primitive `prim` at displacement u: returns its energy and,
+// with MODE 1, adds its gradient and Hessian, rotated into the indenter's
+// body frame, to the primitive's accumulators (which the caller rotates back).
+template <class R, int GK, int MODE>
+TC_D double friction_prim(const EnvView<R>& e, const R* __restrict__ u, int prim, R* gacc, R* hacc) {
+  constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
+  constexpr int NG = 3 * NGP;
+  const int n = prim_count(e, GK);
+  const int nv = e.nv;
+  const int cnt = e.fr_n[GK][prim];
+  R dg[NGP][3];
+  for (int l = 0; l < NGP; ++l) {
+    const int v = gel_vertex(e, GK, prim, l);
+    for (int d = 0; d < 3; ++d) dg[l][d] = u[d * nv + v] - e.u0[d * nv + v];
+  }
+  double dR[9];
+  for (int k = 0; k < 9; ++k) dR[k] = e.Rm[k] - e.Rm0[k];
+  const double dt3[3] = {e.tr[0] - e.tr0[0], e.tr[1] - e.tr0[1], e.tr[2] - e.tr0[2]};
+  const R mu = e.mu_f, ex = e.eps_x;
+  const int ik = GK == GV ? 2 : (GK == GE ? 1 : 0);
+  const int nind = GK == GV ? 3 : (GK == GE ? 2 : 1);
+  const int ind_slot0 = GK == GV ? 1 : (GK == GE ? 2 : 0);
+  double energy = 0.0;
+  for (int j = 0; j < cnt; ++j) {
+    const int ip = e.fr_ip[GK][(int64_t)j * n + prim];
+    R val[8];
+    for (int q = 0; q < 8; ++q) val[q] = e.fr_val[GK][((int64_t)8 * j + q) * n + prim];
+    const R lam = val[0];
+    const R nw[3] = {val[1], val[2], val[3]};
+    R relv[3] = {R(0), R(0), R(0)};
+    for (int l = 0; l < NGP; ++l) {
+      const R w = val[4 + gel_pair_slot<GK>(l)];
+      for (int d = 0; d < 3; ++d) relv[d] += w * dg[l][d];
+    }
+    for (int l = 0; l < nind; ++l) {
+      const int iv = ind_vertex(e, ik, ip, l);
+      const double V[3] = {e.IV[iv], e.IV[e.ind_nv + iv], e.IV[2 * e.ind_nv + iv]};
+      const R w = val[4 + ind_slot0 + l];
+      for (int d = 0; d < 3; ++d)
+        relv[d] += w * (R)(dR[3 * d] * V[0] + dR[3 * d + 1] * V[1] + dR[3 * d + 2] * V[2] + dt3[d]);
+    }
+    const R un = relv[0] * nw[0] + relv[1] * nw[1] + relv[2] * nw[2];
+    R ut[3];
+    for (int d = 0; d < 3; ++d) ut[d] = relv[d] - un * nw[d];
+    const R y = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+    const R ml = mu * lam;
+    const R f0 = y < ex ? (-y * y * y / (R(3) * ex * ex) + y * y / ex + ex / R(3)) : y;
+    energy += (double)(ml * f0);
+    if (MODE != 1) continue;
+    const R a = ml * (y < ex ? (R(2) / ex - y / (ex * ex)) : R(1) / y);  // mu lambda f1 / y
+    const R c = y > R(0) ? ml * (y < ex ? -R(1) / (y * ex * ex) : -R(1) / (y * y * y)) : R(0);
+    // world gradient w.r.t. rel and Hessian M = a P + c ut ut^T, rotated to the body frame
+    R gw[3], M[3][3];
+    for (int i = 0; i < 3; ++i) {
+      gw[i] = a * ut[i];
+      for (int k = 0; k < 3; ++k) M[i][k] = a * ((i == k ? R(1) : R(0)) - nw[i] * nw[k]) + c * ut[i] * ut[k];
+    }
+    R Rm[9];
+    for (int k = 0; k < 9; ++k) Rm[k] = (R)e.Rm[k];
+    R gb[3], T1[3][3], Mb[3][3];
+    for (int i = 0; i < 3; ++i) gb[i] = Rm[i] * gw[0] + Rm[3 + i] * gw[1] + Rm[6 + i] * gw[2];  // R^T g
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) T1[i][k] = Rm[i] * M[0][k] + Rm[3 + i] * M[1][k] + Rm[6 + i] * M[2][k];  // R^T M
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 3; ++k) Mb[i][k] = T1[i][0] * Rm[k] + T1[i][1] * Rm[3 + k] + T1[i][2] * Rm[6 + k];  // (R^T M) R
+    R wl[NGP];
+    for (int l = 0; l < NGP; ++l) wl[l] = val[4 + gel_pair_slot<GK>(l)];
+    for (int la = 0; la < NGP; ++la) {
+      for (int i = 0; i < 3; ++i) gacc[3 * la + i] += wl[la] * gb[i];
+      for (int lb = la; lb < NGP; ++lb) {
+        const R s = wl[la] * wl[lb];
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 3; ++k) {
+            const int ra = 3 * la + i, cb = 3 * lb + k;
+            if (ra > cb) continue;
+            hacc[sym_index(ra, cb, NG)] += s * Mb[i][k];
+          }
+      }
+    }
+  }
+  return energy;
+}
+
 template <class R, int GK, int MODE>
 TC_D void contact_unit(const BatchView<R>& bv, const PartLayout& L, int trial, int unit) {
   constexpr int NGP = GK == GV ? 1 : (GK == GE ? 2 : 3);
@@ -455,6 +620,8 @@ TC_D void contact_unit(const BatchView<R>& bv, const PartLayout& L, int trial, i
       __syncthreads();
     }
   }
+  if (threadIdx.x < 128 && mine < n && e.mu_f > R(0) && e.fr_n[GK] != nullptr && e.fr_n[GK][mine] > 0)
+    energy += friction_prim<R, GK, MODE>(e, u, mine, gacc, hacc);
   if (MODE == 1 && threadIdx.x < 128 && mine < n) {
     const int prim = mine;
     // body -> world: g_w = R g_b per point, H_w = R H_b R^T per 3x3 block
@@ -821,6 +988,8 @@ template void b_contact<float>(const BatchHost<float>&, bool, bool, cudaStream_t
 template void b_contact<double>(const BatchHost<double>&, bool, bool, cudaStream_t);
 template void b_ccd<float>(const BatchHost<float>&, cudaStream_t);
 template void b_ccd<double>(const BatchHost<double>&, cudaStream_t);
+template void b_friction_lag<float>(const BatchHost<float>&, cudaStream_t);
+template void b_friction_lag<double>(const BatchHost<double>&, cudaStream_t);
 template void b_force<float>(const BatchHost<float>&, cudaStream_t);
 template void b_force<double>(const BatchHost<double>&, cudaStream_t);
 template int intersect_test<float>(const EnvView<float>&, int*, cudaStream_t);

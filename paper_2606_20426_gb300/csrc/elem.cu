@@ -18,59 +18,11 @@
 // al. 2024): under compression the twist modes turn negative, and clamping
 // them to zero leaves the projected Newton method converging only linearly.
 #include "env.cuh"
+#include "kin.cuh"
 #include "prof.cuh"
 #include "solver.cuh"
 
 namespace tc {
-
-template <class R> struct Mat3 {
-  R m[3][3];
-};
-
-template <class R> TC_D void cof3(const R A[3][3], R C[3][3]) {
-  C[0][0] = A[1][1] * A[2][2] - A[1][2] * A[2][1];
-  C[0][1] = A[1][2] * A[2][0] - A[1][0] * A[2][2];
-  C[0][2] = A[1][0] * A[2][1] - A[1][1] * A[2][0];
-  C[1][0] = A[0][2] * A[2][1] - A[0][1] * A[2][2];
-  C[1][1] = A[0][0] * A[2][2] - A[0][2] * A[2][0];
-  C[1][2] = A[0][1] * A[2][0] - A[0][0] * A[2][1];
-  C[2][0] = A[0][1] * A[1][2] - A[0][2] * A[1][1];
-  C[2][1] = A[0][2] * A[1][0] - A[0][0] * A[1][2];
-  C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
-}
-
-// Load G = Du Dm^-1 for tet e at displacement u (SoA, stride nv).
-template <class R>
-TC_D void load_G(const EnvView<R>& e, const R* u, int el, int4 t, R G[3][3], R Bm[3][3]) {
-  const int nv = e.nv, nt = e.nt;
-  const int v[4] = {t.x, t.y, t.z, t.w};
-  R Du[3][3];
-  for (int i = 0; i < 3; ++i) {
-    const R u0 = u[i * nv + v[0]];
-    for (int a = 0; a < 3; ++a) Du[i][a] = u[i * nv + v[a + 1]] - u0;
-  }
-  for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < 3; ++j) Bm[a][j] = e.Dminv[(int64_t)(a * 3 + j) * nt + el];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) G[i][j] = Du[i][0] * Bm[0][j] + Du[i][1] * Bm[1][j] + Du[i][2] * Bm[2][j];
-}
-
-template <class R> struct Kin {
-  R trG, m2, detG, Jm1, J;
-  R cG[3][3];
-};
-
-template <class R> TC_D Kin<R> kinematics(const R G[3][3]) {
-  Kin<R> k;
-  k.trG = G[0][0] + G[1][1] + G[2][2];
-  k.m2 = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
-         (G[1][1] * G[2][2] - G[1][2] * G[2][1]);
-  cof3<R>(G, k.cG);
-  k.detG = G[0][0] * k.cG[0][0] + G[0][1] * k.cG[0][1] + G[0][2] * k.cG[0][2];
-  k.Jm1 = k.trG + k.m2 + k.detG;
-  k.J = R(1) + k.Jm1;
-  return k;
-}
 
 template <class R> TC_D R psi_of(const R G[3][3], const Kin<R>& k, R mu, R lam_hat) {
   R g2 = 0;
@@ -318,20 +270,11 @@ __global__ void __launch_bounds__(kBlock) k_stress(const EnvView<R> e, const R* 
   const int4 t = e.tets[el];
   R G[3][3], Bm[3][3];
   load_G<R>(e, u, el, t, G, Bm);
-  const Kin<R> k = kinematics<R>(G);
-  const R muJ = e.mu / k.J;
-  const R iso = (e.lam_hat - muJ) * k.Jm1;
-  R bI[3][3];  // b - I = G + G^T + G G^T
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      bI[i][j] = G[i][j] + G[j][i] + G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2];
+  R s6[6];
+  cauchy6<R>(G, kinematics<R>(G), e.mu, e.lam_hat, s6);
   const int64_t nt = e.nt;
-  sig[0 * nt + el] = (float)(muJ * bI[0][0] + iso);
-  sig[1 * nt + el] = (float)(muJ * bI[1][1] + iso);
-  sig[2 * nt + el] = (float)(muJ * bI[2][2] + iso);
-  sig[3 * nt + el] = (float)(muJ * bI[0][1]);
-  sig[4 * nt + el] = (float)(muJ * bI[1][2]);
-  sig[5 * nt + el] = (float)(muJ * bI[2][0]);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sig[c * nt + el] = (float)s6[c];
 }
 
 template <class R> void launch_stress(const EnvView<R>& e, float* sigma, cudaStream_t s) {

@@ -61,6 +61,16 @@ template <class R> struct EnvView {
   R inv_h2;                   // 1/dt^2 (dynamic) or 0
   double dhat, kappa;
   int pcg_max;                // this env's PCG iteration cap
+  // lagged friction (mu_f = 0: off): friction ratio, smoothing width eps_v dt,
+  // indenter pose at the step start, and per gel primitive kind the lagged
+  // pairs: fr_n[k][prim] pairs, pair j's indenter primitive at
+  // fr_ip[k][j * n_k + prim] and its 8 values (lambda, normal xyz, closest-point
+  // weights of the 4 pair points) at fr_val[k][(8 j + q) * n_k + prim]
+  R mu_f, eps_x;
+  double Rm0[9], tr0[3];
+  int32_t* fr_n[3];
+  int32_t* fr_ip[3];
+  R* fr_val[3];
   // topology
   const int4* tets;
   const double* X0;           // rest positions, SoA x|y|z, each nv
@@ -204,7 +214,16 @@ struct Env {
   double dhat = 0, kappa = 0, dt = 0, rtol = 1e-6, gabs = 0, ptol = 0;
   int newton_max = 1024, pcg_max = 1000, thick_axis = 2;
   bool dynamic = false;
+  double mu_f = 0.0, eps_v = 0.01;
+  bool friction = false;      // dynamic and mu_f > 0
   tc_pose pose{};
+  tc_pose pose_start{};       // indenter pose at the start of the current step
+  // lagged friction pairs (allocated on first use, capacity fr_cap = the
+  // candidate capacity per primitive); see EnvView
+  int32_t* fr_n[3] = {nullptr, nullptr, nullptr};
+  int32_t* fr_ip[3] = {nullptr, nullptr, nullptr};
+  void* fr_val[3] = {nullptr, nullptr, nullptr};
+  int fr_cap = 0;
   EnvStats stats;
   // device integer topology
   int4* tets = nullptr;
@@ -261,6 +280,11 @@ struct Env {
   void* utrial = nullptr;
   // extraction scratch (float)
   float *sigma = nullptr, *face_p = nullptr, *face_A = nullptr, *vert_p = nullptr;
+  // tables of a batched extraction led by this env (device from the arena,
+  // pinned host staging), grown on demand
+  void* x_dev = nullptr;
+  void* x_host = nullptr;
+  size_t x_cap = 0;
   Scalars* sc = nullptr;      // device (setup checks)
   Scalars* sc_host = nullptr; // pinned host mirror
   // host copies of integer outputs
@@ -282,6 +306,11 @@ template <class R> EnvView<R> Env::view() const {
   e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
   e.dhat = dhat; e.kappa = kappa; e.pcg_max = pcg_max;
+  e.mu_f = friction ? (R)mu_f : R(0);
+  e.eps_x = friction ? (R)(eps_v * dt) : R(1);
+  for (int k = 0; k < 9; ++k) e.Rm0[k] = pose_start.R[k];
+  for (int k = 0; k < 3; ++k) e.tr0[k] = pose_start.t[k];
+  for (int k = 0; k < 3; ++k) { e.fr_n[k] = fr_n[k]; e.fr_ip[k] = fr_ip[k]; e.fr_val[k] = (R*)fr_val[k]; }
   e.tets = tets; e.X0 = X0; e.X0f = X0f; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
   e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.eslot = (R*)eslot; e.kblk = (R*)kblk;
   e.nnzb = nnzb; e.bsr_rp = bsr_rp; e.bsr_ci = bsr_ci; e.bsr_diag = bsr_diag; e.bsr_val = (R*)bsr_val;
@@ -336,6 +365,12 @@ void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const i
                   const float* vert_p, float* out, uint8_t* mask, cudaStream_t s);
 void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, float alpha, float* sigma,
                           cudaStream_t s);
+// sigma (K8) and the pressure map (K9-K10) of several envs of one precision in
+// one cooperative launch on stream s; per env, sigma / map / mask may be null
+// (a map needs the env's create-time grid).  Synchronises s.
+template <class R>
+tc_status extract_batch(const std::vector<Env*>& envs, const std::vector<float*>& sigma,
+                        const std::vector<float*>& map, const std::vector<uint8_t*>& mask, cudaStream_t s);
 
 }  // namespace tc
 

@@ -8,7 +8,19 @@
 // K10a per contact vertex: p_v = sum_f A_f p_f / sum_f A_f over incident
 //     contact faces (deformed areas), a fixed-order gather.
 // K10b per pixel: barycentric interpolation of p_v over the covering face.
+//
+// The per-env kernels (k_traction, k_vertex_avg, k_splat, and k_stress in
+// elem.cu) serve the single-env calls.  k_extract does all of it for a whole
+// batch of envs in one cooperative launch: phase 1 streams sigma of every tet
+// and the face pressure and area of every contact face of every env, phase 2
+// averages to contact vertices, phase 3 splats to pixels, with a grid-wide
+// barrier between phases.  Each item goes through the same device functions
+// as in the per-env kernels, so the outputs are the same bit for bit.
+#include <algorithm>
+#include <mutex>
+
 #include "env.cuh"
+#include "kin.cuh"
 #include "prof.cuh"
 
 namespace tc {
@@ -21,46 +33,8 @@ __global__ void __launch_bounds__(kBlock)
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   const int nfc = e.nfc;
   if (f >= nfc) return;
-  const int nv = e.nv, nt = e.nt;
-  const int el = cparent[f];
-  const int4 t = e.tets[el];
-  const int v[4] = {t.x, t.y, t.z, t.w};
-  R Du[3][3], Bm[3][3], G[3][3];
-  for (int i = 0; i < 3; ++i) {
-    const R u0 = e.u[i * nv + v[0]];
-    for (int a = 0; a < 3; ++a) Du[i][a] = e.u[i * nv + v[a + 1]] - u0;
-  }
-  for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < 3; ++j) Bm[a][j] = e.Dminv[(int64_t)(a * 3 + j) * nt + el];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) G[i][j] = Du[i][0] * Bm[0][j] + Du[i][1] * Bm[1][j] + Du[i][2] * Bm[2][j];
-  const R trG = G[0][0] + G[1][1] + G[2][2];
-  const R m2 = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) + (G[0][0] * G[2][2] - G[0][2] * G[2][0]) +
-               (G[1][1] * G[2][2] - G[1][2] * G[2][1]);
-  const R detG = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
-                 G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
-  const R Jm1 = trG + m2 + detG;
-  const R muJ = e.mu / (R(1) + Jm1);
-  const R iso = (e.lam_hat - muJ) * Jm1;
-  R S[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      S[i][j] = muJ * (G[i][j] + G[j][i] + G[i][0] * G[j][0] + G[i][1] * G[j][1] + G[i][2] * G[j][2]) +
-                (i == j ? iso : R(0));
-  // deformed face (stored winding is outward), edge vectors as rest + displacement
-  const int a = e.cfaces[f], b = e.cfaces[nfc + f], c = e.cfaces[2 * nfc + f];
-  R e1[3], e2[3];
-  for (int d = 0; d < 3; ++d) {
-    e1[d] = (R)(e.X0[d * nv + b] - e.X0[d * nv + a]) + (e.u[d * nv + b] - e.u[d * nv + a]);
-    e2[d] = (R)(e.X0[d * nv + c] - e.X0[d * nv + a]) + (e.u[d * nv + c] - e.u[d * nv + a]);
-  }
-  R n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-  const R len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  const R il = len > R(0) ? R(1) / len : R(0);
-  for (int d = 0; d < 3; ++d) n[d] *= il;
-  R tv[3];
-  for (int i = 0; i < 3; ++i) tv[i] = S[i][0] * n[0] + S[i][1] * n[1] + S[i][2] * n[2];
-  const R pn = tv[0] * n[0] + tv[1] * n[1] + tv[2] * n[2];
+  R tv[3], n[3], pn, len;
+  face_traction<R>(e, cparent, f, tv, n, pn, len);
   if (t_out)
     for (int i = 0; i < 3; ++i) t_out[(int64_t)i * nfc + f] = (float)tv[i];
   if (p_out) p_out[f] = (float)(-pn);
@@ -76,11 +50,9 @@ void launch_traction(const EnvView<R>& e, const int32_t* cparent, float* t, floa
   if (e.nfc > 0) TC_LAUNCH("k_traction", s, k_traction<R><<<grid_for(e.nfc), kBlock, 0, s>>>(e, cparent, t, p, tt, face_p, face_A));
 }
 
-__global__ void __launch_bounds__(kBlock)
-    k_vertex_avg(int nvc, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
-                 const float* __restrict__ face_p, const float* __restrict__ face_A, float* __restrict__ vert_p) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nvc) return;
+// area-weighted mean over the incident faces of contact vertex s
+TC_D float vertex_mean(int s, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                       const float* __restrict__ face_p, const float* __restrict__ face_A) {
   float num = 0.f, den = 0.f;
   for (int k = off[s]; k < off[s + 1]; ++k) {
     const int f = idx[k] >> 2;
@@ -88,7 +60,29 @@ __global__ void __launch_bounds__(kBlock)
     num += A * face_p[f];
     den += A;
   }
-  vert_p[s] = den > 0.f ? num / den : 0.f;
+  return den > 0.f ? num / den : 0.f;
+}
+
+// barycentric interpolation at pixel i of npix (0 and mask 0 off the surface)
+TC_D void splat_pixel(int i, int npix, const int32_t* __restrict__ pix_face, const float* __restrict__ pix_w,
+                      const int32_t* __restrict__ cface_slot, int nfc, const float* __restrict__ vert_p,
+                      float* __restrict__ out, uint8_t* __restrict__ mask) {
+  const int f = pix_face[i];
+  float v = 0.f;
+  if (f >= 0) {
+    v = pix_w[i] * vert_p[cface_slot[f]] + pix_w[npix + i] * vert_p[cface_slot[nfc + f]] +
+        pix_w[2 * npix + i] * vert_p[cface_slot[2 * nfc + f]];
+  }
+  out[i] = v;
+  if (mask) mask[i] = f >= 0 ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(kBlock)
+    k_vertex_avg(int nvc, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
+                 const float* __restrict__ face_p, const float* __restrict__ face_A, float* __restrict__ vert_p) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nvc) return;
+  vert_p[s] = vertex_mean(s, off, idx, face_p, face_A);
 }
 
 void launch_vertex_avg(int nvc, const int32_t* off, const int32_t* idx, const float* face_p, const float* face_A,
@@ -102,14 +96,7 @@ __global__ void __launch_bounds__(kBlock)
             uint8_t* __restrict__ mask) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= npix) return;
-  const int f = pix_face[i];
-  float v = 0.f;
-  if (f >= 0) {
-    v = pix_w[i] * vert_p[cface_slot[f]] + pix_w[npix + i] * vert_p[cface_slot[nfc + f]] +
-        pix_w[2 * npix + i] * vert_p[cface_slot[2 * nfc + f]];
-  }
-  out[i] = v;
-  if (mask) mask[i] = f >= 0 ? 1 : 0;
+  splat_pixel(i, npix, pix_face, pix_w, cface_slot, nfc, vert_p, out, mask);
 }
 
 void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const int32_t* cface_slot, int nfc,
@@ -117,9 +104,225 @@ void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const i
   if (npix > 0) TC_LAUNCH("k_splat", s, k_splat<<<grid_for(npix), kBlock, 0, s>>>(npix, pix_face, pix_w, cface_slot, nfc, vert_p, out, mask));
 }
 
+// ------------------------------------------------------- batched extraction
+
+template <class R> struct XEnv {
+  EnvView<R> v;
+  const int32_t* cparent;
+  const int32_t* cface_slot;
+  const int32_t* pix_face;
+  const float* pix_w;
+  float *face_p, *face_A, *vert_p;
+  float* sigma;    // 6 x nt or null
+  float* map;      // H x W or null (then no face / vertex / pixel work)
+  uint8_t* mask;   // H x W or null
+  int npix;
+};
+
+template <class R> struct XBatch {
+  const XEnv<R>* env;
+  const int64_t* off;  // 4 rows of nenv + 1 item offsets: tets, faces, contact vertices, pixels
+  int nenv;
+  unsigned* bar;       // grid barrier: arrivals, generation
+  int* err;            // set when a barrier wait gave up
+};
+
+// env whose item range [row[e], row[e+1]) holds item i
+TC_D int env_of(const int64_t* row, int n, int64_t i) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (row[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grid-wide barrier of a cooperative launch (every block is resident, so the
+// last arrival always comes).  The wait is bounded all the same: after
+// ~2^22 polls a block records the failure in *err and goes on; the host
+// turns it into TC_ERR_CUDA.  Returns false once *err is set.
+TC_D bool grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      int polls = 0;
+      while (*gen == g) {
+        __nanosleep(32);
+        if (++polls > (1 << 22)) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+
+template <class R> __global__ void __launch_bounds__(kBlock) k_extract(const XBatch<R> xb, int with_map) {
+  const int n = xb.nenv;
+  const int64_t* tet_off = xb.off;
+  const int64_t* face_off = xb.off + (n + 1);
+  const int64_t* cv_off = xb.off + 2 * (n + 1);
+  const int64_t* pix_off = xb.off + 3 * (n + 1);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // phase 1: sigma per tet (K8), face pressure and area per contact face (K9)
+  const int64_t ntet = tet_off[n], nface = face_off[n];
+  for (int64_t i = first; i < ntet + nface; i += stride) {
+    if (i < ntet) {
+      const int e = env_of(tet_off, n, i);
+      const XEnv<R>& x = xb.env[e];
+      const int el = (int)(i - tet_off[e]);
+      R G[3][3], Bm[3][3], s6[6];
+      load_G<R>(x.v, x.v.u, el, x.v.tets[el], G, Bm);
+      cauchy6<R>(G, kinematics<R>(G), x.v.mu, x.v.lam_hat, s6);
+      const int64_t nt = x.v.nt;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) x.sigma[c * nt + el] = (float)s6[c];
+    } else {
+      const int64_t j = i - ntet;
+      const int e = env_of(face_off, n, j);
+      const XEnv<R>& x = xb.env[e];
+      const int f = (int)(j - face_off[e]);
+      R tv[3], nrm[3], pn, len;
+      face_traction<R>(x.v, x.cparent, f, tv, nrm, pn, len);
+      x.face_p[f] = (float)(-pn);
+      x.face_A[f] = (float)(R(0.5) * len);
+    }
+  }
+  if (!with_map) return;
+  if (!grid_barrier(xb.bar, xb.err)) return;
+  // phase 2: area-weighted means at the contact vertices (K10a)
+  const int64_t ncv = cv_off[n];
+  for (int64_t i = first; i < ncv; i += stride) {
+    const int e = env_of(cv_off, n, i);
+    const XEnv<R>& x = xb.env[e];
+    const int s = (int)(i - cv_off[e]);
+    x.vert_p[s] = vertex_mean(s, x.v.cv_face_off, x.v.cv_face_idx, x.face_p, x.face_A);
+  }
+  if (!grid_barrier(xb.bar, xb.err)) return;
+  // phase 3: the pixel map (K10b)
+  const int64_t npx = pix_off[n];
+  for (int64_t i = first; i < npx; i += stride) {
+    const int e = env_of(pix_off, n, i);
+    const XEnv<R>& x = xb.env[e];
+    splat_pixel((int)(i - pix_off[e]), x.npix, x.pix_face, x.pix_w, x.cface_slot, x.v.nfc, x.vert_p, x.map, x.mask);
+  }
+}
+
+// Resident blocks per SM of k_extract<R> (for the cooperative grid), once per device.
+template <class R> static int extract_blocks_per_sm(int dev) {
+  static std::mutex m;
+  static int cache[64] = {};
+  std::lock_guard<std::mutex> g(m);
+  if (dev < 0 || dev >= 64) return 1;
+  if (!cache[dev]) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_extract<R>, kBlock, 0) != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    cache[dev] = b;
+  }
+  return cache[dev];
+}
+
+template <class R>
+tc_status extract_batch(const std::vector<Env*>& envs, const std::vector<float*>& sigma,
+                        const std::vector<float*>& map, const std::vector<uint8_t*>& mask, cudaStream_t s) {
+  const int n = (int)envs.size();
+  if (n == 0) return TC_OK;
+  Env& lead = *envs[0];
+  // device table: XEnv[n] | off[4 (n+1)] | barrier[2] + err (in the lead env's arena, grown on demand)
+  const size_t env_bytes = ((sizeof(XEnv<R>) * n + 255) / 256) * 256;
+  const size_t off_bytes = ((sizeof(int64_t) * 4 * (n + 1) + 255) / 256) * 256;
+  const size_t need = env_bytes + off_bytes + 256;
+  if (need > lead.x_cap) {
+    if (lead.x_dev) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return TC_ERR_CUDA;
+      lead.arena.put(lead.x_dev);
+    }
+    if (lead.x_host) cudaFreeHost(lead.x_host);
+    lead.x_dev = nullptr;
+    lead.x_host = nullptr;
+    lead.x_cap = 0;
+    lead.x_dev = lead.arena.alloc<unsigned char>((int64_t)need);
+    if (!lead.x_dev) return TC_ERR_OOM;
+    if (cudaMallocHost(&lead.x_host, need) != cudaSuccess) {
+      lead.x_host = nullptr;
+      return TC_ERR_OOM;
+    }
+    lead.x_cap = need;
+  }
+  unsigned char* h = (unsigned char*)lead.x_host;
+  XEnv<R>* hx = (XEnv<R>*)h;
+  int64_t* hoff = (int64_t*)(h + env_bytes);
+  bool any_map = false;
+  for (int r = 0; r < 4; ++r) hoff[r * (n + 1)] = 0;
+  for (int e = 0; e < n; ++e) {
+    Env& v = *envs[e];
+    const bool m = map[e] != nullptr && v.H * v.W > 0;
+    any_map |= m;
+    XEnv<R>& x = hx[e];
+    x.v = v.view<R>();
+    x.cparent = v.cparent;
+    x.cface_slot = v.cface_slot;
+    x.pix_face = v.pix_face;
+    x.pix_w = v.pix_w;
+    x.face_p = v.face_p;
+    x.face_A = v.face_A;
+    x.vert_p = v.vert_p;
+    x.sigma = sigma[e];
+    x.map = m ? map[e] : nullptr;
+    x.mask = m ? mask[e] : nullptr;
+    x.npix = v.H * v.W;
+    hoff[0 * (n + 1) + e + 1] = hoff[0 * (n + 1) + e] + (sigma[e] ? v.nt : 0);
+    hoff[1 * (n + 1) + e + 1] = hoff[1 * (n + 1) + e] + (m ? v.nfc : 0);
+    hoff[2 * (n + 1) + e + 1] = hoff[2 * (n + 1) + e] + (m ? v.nvc : 0);
+    hoff[3 * (n + 1) + e + 1] = hoff[3 * (n + 1) + e] + (m ? (int64_t)v.H * v.W : 0);
+  }
+  unsigned char* d = (unsigned char*)lead.x_dev;
+  if (cudaMemcpyAsync(d, h, env_bytes + off_bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) return TC_ERR_CUDA;
+  unsigned* bar = (unsigned*)(d + env_bytes + off_bytes);
+  int* err = (int*)(bar + 2);
+  if (cudaMemsetAsync(bar, 0, 16, s) != cudaSuccess) return TC_ERR_CUDA;
+  int64_t most = 0;
+  for (int r = 0; r < 4; ++r) most = std::max(most, hoff[r * (n + 1) + n] + (r == 0 ? hoff[1 * (n + 1) + n] : 0));
+  if (most == 0) return TC_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return TC_ERR_CUDA;
+  const int64_t resident = (int64_t)sms * extract_blocks_per_sm<R>(dev);
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(resident, (most + kBlock - 1) / kBlock));
+  XBatch<R> xb{(const XEnv<R>*)d, (const int64_t*)(d + env_bytes), n, bar, err};
+  int with_map = any_map ? 1 : 0;
+  void* args[] = {(void*)&xb, (void*)&with_map};
+  cudaError_t ce = cudaSuccess;
+  TC_LAUNCH("k_extract", s, ce = cudaLaunchCooperativeKernel((const void*)k_extract<R>, dim3(blocks), dim3(kBlock), args, 0, s));
+  if (ce != cudaSuccess) return TC_ERR_CUDA;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return TC_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return TC_ERR_CUDA;
+  return herr ? TC_ERR_CUDA : TC_OK;
+}
+
 template void launch_traction<float>(const EnvView<float>&, const int32_t*, float*, float*, float*, float*, float*,
                                      cudaStream_t);
 template void launch_traction<double>(const EnvView<double>&, const int32_t*, float*, float*, float*, float*, float*,
                                       cudaStream_t);
+template tc_status extract_batch<float>(const std::vector<Env*>&, const std::vector<float*>&,
+                                        const std::vector<float*>&, const std::vector<uint8_t*>&, cudaStream_t);
+template tc_status extract_batch<double>(const std::vector<Env*>&, const std::vector<float*>&,
+                                         const std::vector<float*>&, const std::vector<uint8_t*>&, cudaStream_t);
 
 }  // namespace tc

@@ -129,15 +129,20 @@ void Server::admit_locked(Worker& w, std::vector<Req*>& out) {
   }
 }
 
-template <class R> static tc_status extract(Env& env, Req& r, cudaStream_t s) {
-  EnvView<R> e = env.view<R>();
-  if (r.sigma) launch_stress<R>(e, r.sigma, s);
-  if (r.map && env.H * env.W > 0) {
-    launch_traction<R>(e, env.cparent, nullptr, nullptr, nullptr, env.face_p, env.face_A, s);
-    launch_vertex_avg(env.nvc, env.cv_face_off, env.cv_face_idx, env.face_p, env.face_A, env.vert_p, s);
-    launch_splat(env.H * env.W, env.pix_face, env.pix_w, env.cface_slot, env.nfc, env.vert_p, r.map, r.mask, s);
+// Stress and pressure maps of the requests a round finished, all of one
+// precision, in one batched extraction launch on the worker's stream.
+template <class R> static tc_status extract(const std::vector<Req*>& reqs, cudaStream_t s) {
+  if (reqs.empty()) return TC_OK;
+  std::vector<Env*> envs;
+  std::vector<float*> sig, map;
+  std::vector<uint8_t*> mask;
+  for (Req* r : reqs) {
+    envs.push_back(r->env);
+    sig.push_back(r->sigma);
+    map.push_back(r->map);
+    mask.push_back(r->mask);
   }
-  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+  return extract_batch<R>(envs, sig, map, mask, s);
 }
 
 void Worker::run() {
@@ -184,15 +189,21 @@ void Worker::run() {
       s64.tasks.clear();
       for (Req* r : live) done.push_back({r, st});
     } else {
+      std::vector<Req*> x32, x64;
       for (const StepDone& d : fin) {
         Req* r = nullptr;
         for (Req* q : live)
           if (q->ticket == d.tag) r = q;
         if (!r) continue;
-        tc_status rs = d.status;
-        if (rs == TC_OK && (r->sigma || r->map))
-          rs = r->env->precision == TC_FP64 ? extract<double>(*r->env, *r, stream) : extract<float>(*r->env, *r, stream);
-        done.push_back({r, rs});
+        if (d.status == TC_OK && (r->sigma || r->map)) (r->env->precision == TC_FP64 ? x64 : x32).push_back(r);
+        done.push_back({r, d.status});
+      }
+      // the requests finished in this round are extracted together
+      const tc_status xs32 = extract<float>(x32, stream), xs64 = extract<double>(x64, stream);
+      for (auto& d : done) {
+        if (d.second != TC_OK || !(d.first->sigma || d.first->map)) continue;
+        const tc_status xs = d.first->env->precision == TC_FP64 ? xs64 : xs32;
+        if (xs != TC_OK) d.second = xs;
       }
       if (!done.empty() && cudaStreamSynchronize(stream) != cudaSuccess)
         for (auto& d : done) d.second = TC_ERR_CUDA;

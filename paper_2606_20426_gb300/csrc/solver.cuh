@@ -37,6 +37,8 @@ template <class R> void b_elem(const BatchHost<R>& b, bool hess, bool trial, cud
 template <class R> void b_contact(const BatchHost<R>& b, bool hess, bool trial, cudaStream_t s);
 template <class R> void b_ccd(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_force(const BatchHost<R>& b, cudaStream_t s);
+// lagged friction pairs of every env (mu_f > 0) at its current state and pose
+template <class R> void b_friction_lag(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_assemble(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_trial_energy(const BatchHost<R>& b, cudaStream_t s);
 template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, bool warm, cudaStream_t s);

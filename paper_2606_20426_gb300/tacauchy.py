@@ -26,7 +26,7 @@ EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_tract
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
            "tc_profile_read", "tc_pressure_map_noalloc", "tc_server_create", "tc_submit", "tc_poll", "tc_wait",
            "tc_server_info", "tc_server_stream", "tc_server_destroy", "tc_pcg_shape", "tc_autotune_pcg",
-           "tc_energy_gradient"]
+           "tc_energy_gradient", "tc_extract_batch"]
 
 
 class TcError(RuntimeError):
@@ -46,7 +46,8 @@ class Material(ctypes.Structure):
 class SceneOpts(ctypes.Structure):
     _fields_ = [("dhat", ctypes.c_double), ("kappa", ctypes.c_double), ("dt", ctypes.c_double),
                 ("newton_rtol", ctypes.c_double), ("newton_max", ctypes.c_int32), ("pcg_max", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("contact_axis", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("contact_axis", ctypes.c_int32),
+                ("friction_mu", ctypes.c_double), ("friction_eps_v", ctypes.c_double)]
 
 
 class TriMesh(ctypes.Structure):
@@ -122,6 +123,8 @@ def load():
         "tc_stress": [P, P],
         "tc_traction": [P, P, P, P],
         "tc_pressure_map": [P, ctypes.POINTER(Grid), P, P],
+        "tc_extract_batch": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P),
+                             ctypes.POINTER(P)],
         "tc_contact_force": [P, P],
         "tc_energy_gradient": [P, P, P],
         "tc_surface_faces": [P, P, P],
@@ -234,7 +237,8 @@ class Env:
         mesh = Mesh(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0])
         mat = Material(m["E"], m["nu"], m["density"])
         opts = SceneOpts(o["dhat"], o.get("kappa", 0.0), o.get("dt", 0.0), o.get("newton_rtol", 1e-6),
-                         o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1))
+                         o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1),
+                         o.get("friction_mu", 0.0), o.get("friction_eps_v", 0.01))
         ind = TriMesh(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0])
         g = env.get("grid")
         grid = make_grid(g) if g is not None else None
@@ -478,6 +482,22 @@ def step_batch(envs, poses, raise_on_error=False):
         for code in out:
             _check(code, "tc_step_batch")
     return out
+
+
+def extract_batch(envs, sigmas=None, maps=None, masks=None):
+    """Stress (6, nt) and pressure map / mask (H, W) of every env in one
+    launch (tc_extract_batch).  sigmas, maps, masks: lists of CUDA tensors (or
+    None entries), one per env, or None to skip that output for all."""
+    envs = list(envs)
+    n = len(envs)
+    lib = load()
+    handles = (ctypes.c_void_p * max(n, 1))(*[e.h for e in envs])
+
+    def ptrs(ts):
+        if ts is None:
+            return None
+        return (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() if t is not None else None for t in ts])
+    _check(lib.tc_extract_batch(handles, n, ptrs(sigmas), ptrs(maps), ptrs(masks)), "tc_extract_batch")
 
 
 def stress_from_F(F, E, nu, out=None, stream=None):

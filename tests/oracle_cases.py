@@ -13,6 +13,8 @@ Cases (Algorithm 2's step, dynamic dt = 1/60 s unless stated):
   parallel-edges small pad under a cylinder lying along the pad's x edges
       (gel and indenter edges exactly parallel: the edge-edge mollifier is
       active), quasi-static.
+  pad-friction the pad-sphere case with friction ratio 0.5 and velocity
+      threshold 0.01 m/s (Sec. III-B), its slip doubled.
 """
 import copy
 import math
@@ -21,8 +23,9 @@ import numpy as np
 
 from synth import indenters, meshes, workloads
 
-CASES = ["pad-sphere", "pad-cylinder", "pad-box", "bench-59k", "close-pairs", "parallel-edges"]
-STEPS = {"pad-sphere": 3, "pad-cylinder": 3, "pad-box": 3, "bench-59k": 1, "close-pairs": 1, "parallel-edges": 2}
+CASES = ["pad-sphere", "pad-cylinder", "pad-box", "bench-59k", "close-pairs", "parallel-edges", "pad-friction"]
+STEPS = {"pad-sphere": 3, "pad-cylinder": 3, "pad-box": 3, "bench-59k": 1, "close-pairs": 1, "parallel-edges": 2,
+         "pad-friction": 3}
 
 
 def _pose(tx, ty, tz):
@@ -31,6 +34,14 @@ def _pose(tx, ty, tz):
 
 def build_case(name):
     """The environment dictionary of a case (inputs only)."""
+    if name == "pad-friction":
+        env = copy.deepcopy(workloads.gelsight_env(3, steps=4, target_tets=4000, grid_hw=(60, 80)))
+        t0 = env["start_pose"]["t"]
+        for p in env["poses"]:
+            p["t"][:2] = t0[:2] + 2.0 * (p["t"][:2] - t0[:2])
+        env["opts"]["friction_mu"] = 0.5
+        env["opts"]["friction_eps_v"] = 0.01
+        return env
     if name.startswith("pad-"):
         seed = {"pad-sphere": 3, "pad-cylinder": 0, "pad-box": 1}[name]
         env = workloads.gelsight_env(seed, steps=4, target_tets=4000, grid_hw=(60, 80))

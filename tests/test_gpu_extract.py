@@ -200,3 +200,38 @@ def test_pressure_map_on_caller_grids(precision):
             g.pressure_map(grid=bad, out=base.new_empty((max(bad["H"], 1), bad["W"])), mask=None, want_mask=False)
         assert ei.value.code == 1
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_extract_batch_equals_per_env_calls(precision):
+    """tc_extract_batch over envs of different sizes (one cooperative launch)
+    writes, bit for bit, what tc_stress and tc_pressure_map write per env,
+    also when some envs ask for sigma only or the map only."""
+    import torch
+    from paper_2606_20426_gb300 import extract_batch
+    cfgs = [workloads.small_env(0, steps=1), workloads.pad_env(2, steps=1), workloads.small_env(3, steps=1),
+            workloads.gelsight_env(4, steps=1, target_tets=6000, grid_hw=(90, 120))]
+    envs = [_gpu_env(c, precision) for c in cfgs]
+    for g, c in zip(envs, cfgs):
+        g.set_positions(_smooth_positions(c["X"], amp=5e-5, seed=len(c["X"])))
+    ref = [(g.stress().clone(),) + tuple(t.clone() for t in g.pressure_map()) for g in envs]
+    dev = "cuda"
+    sig = [torch.full((6, g.info["nt"]), float("nan"), device=dev) for g in envs]
+    maps = [torch.full((g.info["H"], g.info["W"]), float("nan"), device=dev) for g in envs]
+    masks = [torch.full((g.info["H"], g.info["W"]), 9, dtype=torch.uint8, device=dev) for g in envs]
+    extract_batch(envs, sig, maps, masks)
+    for (s0, m0, k0), s1, m1, k1 in zip(ref, sig, maps, masks):
+        assert torch.equal(s0, s1) and torch.equal(m0, m1) and torch.equal(k0, k1)
+    # partial requests: sigma of envs 0 and 2 only, maps of 1 and 3 only
+    sig2 = [torch.zeros_like(s) for s in sig]
+    map2 = [torch.zeros_like(m) for m in maps]
+    extract_batch(envs, [sig2[0], None, sig2[2], None], [None, map2[1], None, map2[3]], None)
+    assert torch.equal(sig2[0], ref[0][0]) and torch.equal(sig2[2], ref[2][0])
+    assert torch.equal(map2[1], ref[1][1]) and torch.equal(map2[3], ref[3][1])
+    assert torch.count_nonzero(sig2[1]).item() == 0 and torch.count_nonzero(map2[0]).item() == 0
+    # a batch of one
+    one = torch.zeros_like(maps[3])
+    extract_batch(envs[3:], None, [one], None)
+    assert torch.equal(one, ref[3][1])
+    for g in envs:
+        g.close()

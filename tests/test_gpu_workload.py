@@ -74,6 +74,20 @@ def test_graded_pad_three_dynamic_steps_each_indenter(oracle_runs, name):
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graded_pad_with_friction(oracle_runs, precision):
+    """Lagged IPC friction (ratio 0.5, threshold 0.01 m/s) under a sliding
+    sphere: the total contact force, tangential part included, matches the
+    oracle within 0.5 %, and the friction really acts (its tangential force
+    is a sizeable fraction of mu times the normal force)."""
+    env, g = _gpu_run("pad-friction", precision)
+    ref = oracle_runs["pad-friction"].get(timeout=560)
+    _check(env, g, ref)
+    f = g.contact_force()
+    assert np.hypot(f[0], f[1]) > 0.2 * 0.5 * abs(f[2])
+    g.close()
+
+
 def test_bench_env_first_step(oracle_runs):
     """The 59,220-tet env the benchmark steps (seed 0, a cylinder), its first
     load pose, FP32 mixed."""
