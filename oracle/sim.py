@@ -452,6 +452,49 @@ class Scene:
             f -= gg.reshape(len(gv), -1, 3).sum(axis=(0, 1))
         return f
 
+    def vertex_contact_forces(self, x=None):
+        """Algorithm 2's contact decomposition at every contact-surface vertex
+        k (sorted ids, as self.cverts): the contact force f_k = -g_k of the
+        barrier (and friction) part of the potential (the potential is divided
+        by dt^2, so this is Algorithm 2's -g_k / dt^2), the unit vertex normal
+        n_k (the area-weighted mean of the incident deformed contact faces'
+        outward normals), the vertex area A_k (a third of each incident face's
+        deformed area), f_n = (f.n) n, f_tau = f - f_n and p_k = |f_k| / A_k.
+        Returns (f, f_n, f_tau, p, n, A)."""
+        x = self.x if x is None else x
+        Y = self.indenter(self.pose)
+        _, terms = self.barrier_terms(x, Y, self.candidates(x, Y))
+        terms = terms + self.friction_terms(x, Y)[1]
+        g = np.zeros((self.nv, 3))
+        for gv, gg, _ in terms:
+            np.add.at(g, gv.ravel(), gg.reshape(-1, 3))
+        f = -g[self.cverts]
+        nk, Ak = self.vertex_normals_areas(x)
+        fn = np.einsum("ki,ki->k", f, nk)[:, None] * nk
+        return f, fn, f - fn, np.linalg.norm(f, axis=1) / Ak, nk, Ak
+
+    def vertex_normals_areas(self, x=None):
+        """Per contact-surface vertex: the unit normal (area-weighted mean of
+        the incident deformed contact faces' outward normals) and the area (a
+        third of the incident faces' deformed areas)."""
+        x = self.x if x is None else x
+        fc = self.cfaces
+        c = np.cross(x[fc[:, 1]] - x[fc[:, 0]], x[fc[:, 2]] - x[fc[:, 0]])   # 2 A_f n_f
+        nk = np.zeros((len(self.cverts), 3))
+        Ak = np.zeros(len(self.cverts))
+        for k in range(len(self.cverts)):
+            fs = self.csr_idx[self.csr_off[k]:self.csr_off[k + 1]]
+            s = c[fs].sum(axis=0)
+            nk[k] = s / np.linalg.norm(s)
+            Ak[k] = np.sum(0.5 * np.linalg.norm(c[fs], axis=1)) / 3.0
+        return nk, Ak
+
+    def force_pressure_map(self, x=None):
+        """The contact-force pressure p_k = |f_k| / A_k of Algorithm 2 on the
+        pixel grid (the same barycentric splat as the stress-based map)."""
+        p = self.vertex_contact_forces(x)[3]
+        return self.pressure_map(p_vertex=p)
+
     def reaction_force(self, x=None):
         """Sum over fixed vertices of the elastic force the gel exerts on its
         support (equals the contact force at quasi-static equilibrium)."""

@@ -401,3 +401,42 @@ def test_dynamic_energy_matches_gradient_by_finite_differences():
         d[sc.fixed] = 0.0
         fd = (sc.energy(x + eps * d, Y, cand, x_tilde) - sc.energy(x - eps * d, Y, cand, x_tilde)) / (2 * eps)
         assert fd == pytest.approx(float(np.sum(g * d)), rel=1e-5)
+
+
+# ----------------------------------------------- Algorithm 2's vertex forces
+
+def test_vertex_contact_forces_sum_rules(stepped):
+    """The per-vertex decomposition of Algorithm 2: the forces add up to the
+    total contact force, f_n + f_tau = f with f_tau normal to n, the vertex
+    areas partition the contact surface's area, the normals are unit and
+    outward, and p = |f| / A."""
+    _, sc, _ = stepped
+    f, fn, ft, p, n, A = sc.vertex_contact_forces()
+    assert np.allclose(f.sum(axis=0), sc.contact_force(), rtol=1e-12, atol=1e-15)
+    assert np.allclose(fn + ft, f, atol=1e-14 * np.abs(f).max())
+    assert np.abs(np.einsum("ki,ki->k", ft, n)).max() <= 1e-12 * np.abs(f).max()
+    assert np.allclose(np.linalg.norm(n, axis=1), 1.0)
+    assert np.all(n[:, 2] > 0.9)
+    x = sc.x
+    c = np.cross(x[sc.cfaces[:, 1]] - x[sc.cfaces[:, 0]], x[sc.cfaces[:, 2]] - x[sc.cfaces[:, 0]])
+    assert A.sum() == pytest.approx(0.5 * np.linalg.norm(c, axis=1).sum(), rel=1e-12)
+    assert np.allclose(p * A, np.linalg.norm(f, axis=1), rtol=1e-12)
+    # the pressed vertices carry a force into the gel (-z), the others none
+    assert f[:, 2].min() < 0 and np.count_nonzero(np.linalg.norm(f, axis=1)) < len(f)
+
+
+def test_vertex_normal_and_area_worked_example():
+    """A hub with two faces: one flat (area 1/2, normal +z) and one tilted by
+    45 degrees (area sqrt(2)/2, normal (0, 1, 1)/sqrt(2)).  The hub's area is
+    (1/2 + sqrt(2)/2) / 3 and its normal the normalised area-weighted sum
+    (0, 0, 1/2) + (0, 1/2, 1/2), i.e. (0, 1, 2) / sqrt(5); the rim vertices
+    take their single face's normal and a third of its area."""
+    x = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [-1, 0, 0], [0, -1, 1]], dtype=np.float64)
+    sc = Scene.__new__(Scene)
+    sc.x, sc.cfaces = x, np.array([[0, 1, 2], [0, 3, 4]])
+    sc.cverts, sc.csr_off, sc.csr_idx = msh.vertex_face_csr(sc.cfaces)
+    n, A = sc.vertex_normals_areas()
+    assert np.allclose(n[0], np.array([0, 1, 2]) / np.sqrt(5), atol=1e-15)
+    assert A[0] == pytest.approx((0.5 + np.sqrt(2) / 2) / 3, rel=1e-15)
+    assert np.allclose(n[1], [0, 0, 1]) and np.allclose(n[4], np.array([0, 1, 1]) / np.sqrt(2))
+    assert A[2] == pytest.approx(0.5 / 3) and A[3] == pytest.approx(np.sqrt(2) / 6)
