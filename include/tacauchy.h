@@ -259,6 +259,34 @@ tc_status tc_pressure_map(tc_env* env, const tc_grid* grid, float* out, uint8_t*
 tc_status tc_extract_batch(tc_env** envs, int32_t n, float* const* sigma_out, float* const* map_out,
                            uint8_t* const* mask_out);
 
+/* Depth map of the deformed contact surface (the depth that constrains the
+ * optical rendering of Sec. III-D): at every pixel centre of `grid` (host, or
+ * NULL for the create-time grid) covered by a deformed contact face projected
+ * on the grid plane, the face's outward height (coordinate along the thickness
+ * axis, sign-flipped when the contact side is the low side), interpolated
+ * barycentrically in FP64 and rounded to FP32; where several faces cover a
+ * centre the largest height wins (the surface nearest the indenter).
+ * height: device float H x W (0 where uncovered); mask: device uint8 H x W
+ * (1 = covered) or NULL.  No graphics API: one thread per contact face. */
+tc_status tc_depth_map(tc_env* env, const tc_grid* grid, float* height, uint8_t* mask);
+
+/* Algorithm 2's contact decomposition at every contact-surface vertex k (in
+ * increasing vertex id: the vertices of tc_surface_faces' faces), at the
+ * current state: the contact force f_k = -g_k / dt^2 (minus the barrier and
+ * friction part of the gradient of the potential, which is scaled by dt^2),
+ * the unit normal n_k (area-weighted mean of the incident deformed contact
+ * faces' outward normals), the area A_k (a third of those faces' deformed
+ * areas), f_n = (f.n) n, f_tau = f - f_n and the pressure p_k = |f_k| / A_k.
+ * f, f_n, f_tau: device float 3 x nvc (component-major); p: device float nvc;
+ * any may be NULL. */
+tc_status tc_vertex_forces(tc_env* env, float* f, float* f_n, float* f_tau, float* p);
+
+/* The contact-force pressure p_k = |f_k| / A_k of tc_vertex_forces on a pixel
+ * grid, by the barycentric interpolation of tc_pressure_map (grid: host, or
+ * NULL for the create-time grid; out device float H x W; mask device uint8
+ * H x W or NULL).  A second pressure map beside the stress-based one. */
+tc_status tc_force_pressure_map(tc_env* env, const tc_grid* grid, float* out, uint8_t* mask);
+
 /* Incremental potential at the current positions and indenter pose
  * (Algorithm 2's minimisation objective: elastic energy + kappa * barrier
  * sum, plus the inertia term in the dynamic case) and its gradient w.r.t. the

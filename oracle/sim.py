@@ -103,6 +103,10 @@ class Scene:
         # Algorithm 1, steps 1-3
         self.faces, self.parent = msh.boundary_faces(T)
         self.band = msh.contact_band(X, self.fixed, o.get("contact_axis", -1))
+        # outward direction of the contact side along the thickness axis
+        self.thick_axis = msh.thickness_axis(X, o.get("contact_axis", -1))
+        mid = 0.5 * (X[:, self.thick_axis].min() + X[:, self.thick_axis].max())
+        self.out_sign = 1.0 if (len(self.fixed) == 0 or X[self.fixed, self.thick_axis].mean() <= mid) else -1.0
         self.cface_ids = msh.contact_faces(self.faces, self.band)
         self.cfaces = self.faces[self.cface_ids].astype(np.int64)
         self.cparent = self.parent[self.cface_ids].astype(np.int64)
@@ -494,6 +498,46 @@ class Scene:
         pixel grid (the same barycentric splat as the stress-based map)."""
         p = self.vertex_contact_forces(x)[3]
         return self.pressure_map(p_vertex=p)
+
+    def depth_map(self, x=None, grid=None):
+        """Height of the deformed contact surface seen from the contact side,
+        on the pixel grid: every deformed contact face is projected on the
+        grid plane ((axis_u, axis_v) coordinates); at each pixel centre
+        covered by a projected face (closed triangle, either orientation) the
+        face's outward height (the thickness-axis coordinate times the
+        outward sign) is interpolated barycentrically; the map holds the
+        largest such height over the covering faces, rounded to FP32 (the
+        surface nearest the indenter, a z-buffer), and 0 with mask 0 where no
+        face covers the centre.  The first stage of the optical rendering of
+        Sec. III-D (the depth the renderer is constrained to)."""
+        x = self.x if x is None else x
+        g = self.grid if grid is None else grid
+        au, av, H, W = g["axis_u"], g["axis_v"], g["H"], g["W"]
+        pu = g["origin"][0] + (np.arange(W) + 0.5) * g["pixel"][0]
+        pv = g["origin"][1] + (np.arange(H) + 0.5) * g["pixel"][1]
+        best = np.full(H * W, -np.inf, dtype=np.float32)
+        U, V = x[:, au], x[:, av]
+        h = self.out_sign * x[:, self.thick_axis]
+        for a, b, c in self.cfaces:
+            A2 = (U[b] - U[a]) * (V[c] - V[a]) - (V[b] - V[a]) * (U[c] - U[a])
+            if A2 == 0:
+                continue
+            cs = np.nonzero((pu >= min(U[a], U[b], U[c])) & (pu <= max(U[a], U[b], U[c])))[0]
+            rs = np.nonzero((pv >= min(V[a], V[b], V[c])) & (pv <= max(V[a], V[b], V[c])))[0]
+            if len(cs) == 0 or len(rs) == 0:
+                continue
+            PU, PV = np.meshgrid(pu[cs], pv[rs])
+            ea = (U[c] - U[b]) * (PV - V[b]) - (V[c] - V[b]) * (PU - U[b])
+            eb = (U[a] - U[c]) * (PV - V[c]) - (V[a] - V[c]) * (PU - U[c])
+            ec = (U[b] - U[a]) * (PV - V[a]) - (V[b] - V[a]) * (PU - U[a])
+            inside = ((ea >= 0) & (eb >= 0) & (ec >= 0)) | ((ea <= 0) & (eb <= 0) & (ec <= 0))
+            R, C = np.meshgrid(rs, cs, indexing="ij")
+            pix = (R * W + C)[inside]
+            val = ((ea[inside] * h[a] + eb[inside] * h[b] + ec[inside] * h[c]) / A2).astype(np.float32)
+            np.maximum.at(best, pix, val)
+        mask = np.isfinite(best)
+        out = np.where(mask, best, np.float32(0.0)).astype(np.float32)
+        return out.reshape(H, W), mask.reshape(H, W).astype(np.uint8)
 
     def reaction_force(self, x=None):
         """Sum over fixed vertices of the elastic force the gel exerts on its

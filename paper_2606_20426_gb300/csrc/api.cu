@@ -164,6 +164,34 @@ template <class R> static tc_status pressure_map(Env& env, const tc_grid* grid, 
   return TC_OK;
 }
 
+// Contact pass at the current state (fills the contact slots), then the
+// per-vertex decomposition; with a grid, p goes to the env's vertex scratch
+// and is splatted on that grid.
+template <class R>
+static tc_status vertex_forces(Env& env, float* f, float* fn, float* ft, float* p, const tc_grid* grid, bool map,
+                               float* out, uint8_t* mask) {
+  const int32_t* pf = nullptr;
+  const float* pw = nullptr;
+  int npix = 0;
+  if (map) {
+    const tc_status gs = grid_table(env, grid, &pf, &pw, &npix);
+    if (gs != TC_OK) return gs;
+  }
+  double tot[3];
+  tc_status st = contact_force_at_state<R>(exec_of<R>(env), env, tot);
+  if (st != TC_OK) return st;
+  if (map) {
+    launch_vertex_forces<R>(env.view<R>(), nullptr, nullptr, nullptr, env.vert_p, env.stream);
+    launch_splat(npix, pf, pw, env.cface_slot, env.nfc, env.vert_p, out, mask, env.stream);
+  } else {
+    launch_vertex_forces<R>(env.view<R>(), f, fn, ft, p, env.stream);
+  }
+  TC_CHECK(cudaGetLastError());
+  TC_CHECK(cudaStreamSynchronize(env.stream));
+  if (env.prof) env.prof->collect();
+  return TC_OK;
+}
+
 template <class R> static tc_status get_positions(Env& env, double* x) {
   const int nv = env.nv;
   std::vector<R> u(3 * (size_t)nv);
@@ -467,6 +495,39 @@ tc_status tc_contact_force(tc_env* h, double* out) {
   Env& env = h->impl;
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::contact_force<double>(env, out) : tc::contact_force<float>(env, out);
+}
+
+tc_status tc_depth_map(tc_env* h, const tc_grid* grid, float* height, uint8_t* mask) {
+  if (!h || !height) return TC_ERR_INVALID_ARG;
+  Env& env = h->impl;
+  if (grid && !tc::grid_valid(grid)) return TC_ERR_INVALID_ARG;
+  if (!grid && env.H * env.W == 0) return TC_ERR_INVALID_ARG;
+  const tc_grid& g = grid ? *grid : env.grid0;
+  tc::ProfGuard pg(env);
+  const tc_status st = env.precision == TC_FP64 ? tc::launch_depth_map<double>(env, g, height, mask, env.stream)
+                                                : tc::launch_depth_map<float>(env, g, height, mask, env.stream);
+  if (st != TC_OK) return st;
+  if (cudaStreamSynchronize(env.stream) != cudaSuccess) return TC_ERR_CUDA;
+  if (env.prof) env.prof->collect();
+  return TC_OK;
+}
+
+tc_status tc_vertex_forces(tc_env* h, float* f, float* f_n, float* f_tau, float* p) {
+  if (!h) return TC_ERR_INVALID_ARG;
+  Env& env = h->impl;
+  if (env.busy.load()) return TC_ERR_INVALID_ARG;
+  tc::ProfGuard pg(env);
+  return env.precision == TC_FP64 ? tc::vertex_forces<double>(env, f, f_n, f_tau, p, nullptr, false, nullptr, nullptr)
+                                  : tc::vertex_forces<float>(env, f, f_n, f_tau, p, nullptr, false, nullptr, nullptr);
+}
+
+tc_status tc_force_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint8_t* mask) {
+  if (!h || !out) return TC_ERR_INVALID_ARG;
+  Env& env = h->impl;
+  if (env.busy.load()) return TC_ERR_INVALID_ARG;
+  tc::ProfGuard pg(env);
+  return env.precision == TC_FP64 ? tc::vertex_forces<double>(env, nullptr, nullptr, nullptr, nullptr, grid, true, out, mask)
+                                  : tc::vertex_forces<float>(env, nullptr, nullptr, nullptr, nullptr, grid, true, out, mask);
 }
 
 tc_status tc_energy_gradient(tc_env* h, double* energy, double* grad) {

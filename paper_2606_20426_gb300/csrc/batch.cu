@@ -25,6 +25,14 @@ namespace tc {
 // smallest and largest forcing term of the inexact Newton solve in the mixed mode
 constexpr double kEtaFloor32 = 0.1;
 constexpr double kEtaCap32 = 0.1;
+// forcing term of the verification solves in the mixed mode: a step that
+// passes a convergence test with the loose forcing term is taken, and the
+// substep only ends when a step solved to this tolerance passes it too.  A
+// loosely solved step can be small while the iterate is far from the
+// minimiser along soft directions (tangential sliding under a flat
+// frictionless face: block-Jacobi PCG stopped at a 10 % residual leaves those
+// modes nearly untouched, so Newton crawls along them with tiny steps).
+constexpr double kEtaTight32 = 1e-3;
 // continuation of an accepted full step: taken when the energy fell by more
 // than kExtendRatio times the model's predicted decrease, to at most
 // kExtendMax times the step
@@ -455,6 +463,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       c.sub++;
       c.newton = 0;
       c.g0 = -1.0;
+      c.tight = false;
       c.phase = StepCtl::NEWTON;
       if (trace_on())
         std::fprintf(stderr, "[tc] req %llu substep %d advance frac=%.6e s=%.9f\n", (unsigned long long)c.tag, c.sub,
@@ -507,6 +516,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       // steepest-descent steps.
       double et = std::min(e.precision == TC_FP64 ? 0.5 : kEtaCap32, std::sqrt(gn / std::max(c.g0, 1e-300)));
       et = std::max(et, e.precision == TC_FP64 ? 1e-10 : kEtaFloor32);
+      if (e.precision != TC_FP64 && c.tight) et = kEtaTight32;
       P.push_back(N[j]);
       eta.push_back(et * et * sc.gnorm2);  // squared PCG stopping tolerance (eta |g|)^2
     }
@@ -565,12 +575,19 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       // converged: full step below ptol, or below 10 ptol with a predicted
       // decrease under the energy's rounding level -- take it without the
       // energy test
+      const bool loose = e.precision != TC_FP64 && !c.tight;
       if (pmax <= e.ptol || (pmax <= 10.0 * e.ptol && decrement <= e_noise)) {
         if (nonfinite) {
           fail(c, TC_ERR_NONFINITE);
           continue;
         }
         std::swap(e.u, e.utrial);
+        if (loose) {  // take the step, then verify with a tightly solved one
+          c.tight = true;
+          c.newton++;
+          c.phase = StepCtl::NEWTON;
+          continue;
+        }
         finish_substep(c);
         continue;
       }
@@ -580,6 +597,10 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         c.phase = StepCtl::NEWTON;
         // rounding floor: the step is tiny and the energy did not move
         if (Et == c.E0 && pmax <= 10.0 * e.ptol) {
+          if (loose) {
+            c.tight = true;
+            continue;
+          }
           finish_substep(c);
           continue;
         }

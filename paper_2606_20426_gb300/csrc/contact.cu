@@ -919,6 +919,62 @@ __global__ void k_force(const BatchView<R> bv) {
   }
 }
 
+// Algorithm 2's contact decomposition per contact vertex s, from the contact
+// slots of the last contact pass: f = -(vertex slot + its shares of the
+// incident edges' and faces' slots), the unit normal n of sum_f A_f n_f over
+// the incident deformed contact faces, the area A = sum_f A_f / 3,
+// f_n = (f.n) n, f_tau = f - f_n, p = |f| / A (any output may be null).
+template <class R>
+__global__ void __launch_bounds__(kBlock)
+    k_vertex_forces(const EnvView<R> e, float* __restrict__ f_out, float* __restrict__ fn_out,
+                    float* __restrict__ ft_out, float* __restrict__ p_out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nvc = e.nvc, nec = e.nec, nfc = e.nfc, nv = e.nv;
+  if (s >= nvc) return;
+  double f[3];
+  for (int d = 0; d < 3; ++d) f[d] = -(double)e.cv_slot[(int64_t)d * nvc + s];
+  for (int k = e.cv_edge_off[s]; k < e.cv_edge_off[s + 1]; ++k) {
+    const int ed = e.cv_edge_idx[k] >> 2, l = e.cv_edge_idx[k] & 3;
+    for (int d = 0; d < 3; ++d) f[d] -= (double)e.ce_slot[(int64_t)(3 * l + d) * nec + ed];
+  }
+  double cs[3] = {0, 0, 0}, area2 = 0;
+  for (int k = e.cv_face_off[s]; k < e.cv_face_off[s + 1]; ++k) {
+    const int fc = e.cv_face_idx[k] >> 2, l = e.cv_face_idx[k] & 3;
+    for (int d = 0; d < 3; ++d) f[d] -= (double)e.cf_slot[(int64_t)(3 * l + d) * nfc + fc];
+    const int a = e.cfaces[fc], b = e.cfaces[nfc + fc], c = e.cfaces[2 * nfc + fc];
+    double e1[3], e2[3];
+    for (int d = 0; d < 3; ++d) {
+      e1[d] = (e.X0[d * nv + b] - e.X0[d * nv + a]) + (double)(e.u[d * nv + b] - e.u[d * nv + a]);
+      e2[d] = (e.X0[d * nv + c] - e.X0[d * nv + a]) + (double)(e.u[d * nv + c] - e.u[d * nv + a]);
+    }
+    const double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2],
+                 cz = e1[0] * e2[1] - e1[1] * e2[0];
+    cs[0] += cx;
+    cs[1] += cy;
+    cs[2] += cz;
+    area2 += sqrt(cx * cx + cy * cy + cz * cz);
+  }
+  const double cn = sqrt(cs[0] * cs[0] + cs[1] * cs[1] + cs[2] * cs[2]);
+  double n[3] = {0, 0, 0};
+  if (cn > 0)
+    for (int d = 0; d < 3; ++d) n[d] = cs[d] / cn;
+  const double fdn = f[0] * n[0] + f[1] * n[1] + f[2] * n[2];
+  for (int d = 0; d < 3; ++d) {
+    if (f_out) f_out[(int64_t)d * nvc + s] = (float)f[d];
+    if (fn_out) fn_out[(int64_t)d * nvc + s] = (float)(fdn * n[d]);
+    if (ft_out) ft_out[(int64_t)d * nvc + s] = (float)(f[d] - fdn * n[d]);
+  }
+  const double A = area2 / 6.0;
+  if (p_out) p_out[s] = (float)(A > 0 ? sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]) / A : 0.0);
+}
+
+template <class R>
+void launch_vertex_forces(const EnvView<R>& e, float* f, float* fn, float* ft, float* p, cudaStream_t s) {
+  if (e.nvc > 0) TC_LAUNCH("k_vertex_forces", s, k_vertex_forces<R><<<grid_for(e.nvc), kBlock, 0, s>>>(e, f, fn, ft, p));
+}
+template void launch_vertex_forces<float>(const EnvView<float>&, float*, float*, float*, float*, cudaStream_t);
+template void launch_vertex_forces<double>(const EnvView<double>&, float*, float*, float*, float*, cudaStream_t);
+
 template <class R> void b_force(const BatchHost<R>& b, cudaStream_t s) {
   TC_LAUNCH("k_force", s, k_force<R><<<b.nenv, kBlock, 0, s>>>(b.bv));
 }

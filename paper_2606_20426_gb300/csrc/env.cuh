@@ -215,6 +215,7 @@ struct Env {
   int newton_max = 1024, pcg_max = 1000, thick_axis = 2;
   bool dynamic = false;
   double mu_f = 0.0, eps_v = 0.01;
+  double out_sign = 1.0;      // outward direction of the contact side along thick_axis
   bool friction = false;      // dynamic and mu_f > 0
   tc_pose pose{};
   tc_pose pose_start{};       // indenter pose at the start of the current step
@@ -365,6 +366,13 @@ void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const i
                   const float* vert_p, float* out, uint8_t* mask, cudaStream_t s);
 void launch_stress_from_F(const float* F, int64_t n, float mu, float lam_hat, float alpha, float* sigma,
                           cudaStream_t s);
+// Depth map of the deformed contact surface on a grid (Sec. III-D's depth).
+template <class R>
+tc_status launch_depth_map(const Env& env, const tc_grid& grid, float* out, uint8_t* mask, cudaStream_t s);
+// Algorithm 2's per-contact-vertex force decomposition from the contact slots
+// (run a contact pass at the current state first).
+template <class R>
+void launch_vertex_forces(const EnvView<R>& e, float* f, float* fn, float* ft, float* p, cudaStream_t s);
 // sigma (K8) and the pressure map (K9-K10) of several envs of one precision in
 // one cooperative launch on stream s; per env, sigma / map / mask may be null
 // (a map needs the env's create-time grid).  Synchronises s.

@@ -17,6 +17,7 @@
 // barrier between phases.  Each item goes through the same device functions
 // as in the per-env kernels, so the outputs are the same bit for bit.
 #include <algorithm>
+#include <climits>
 #include <mutex>
 
 #include "env.cuh"
@@ -103,6 +104,100 @@ void launch_splat(int npix, const int32_t* pix_face, const float* pix_w, const i
                   const float* vert_p, float* out, uint8_t* mask, cudaStream_t s) {
   if (npix > 0) TC_LAUNCH("k_splat", s, k_splat<<<grid_for(npix), kBlock, 0, s>>>(npix, pix_face, pix_w, cface_slot, nfc, vert_p, out, mask));
 }
+
+// ------------------------------------------------------------ depth map
+// Height of the deformed contact surface seen from the contact side (the
+// depth the optical rendering of Sec. III-D is constrained to): each thread
+// projects one deformed contact face on the grid plane, and every pixel
+// centre inside the closed projected triangle gets the barycentric
+// interpolation of the vertices' outward heights (thickness-axis coordinate
+// times the outward sign); the largest value wins (a z-buffer: atomicMax on
+// an order-preserving integer image of the FP32 value, so the result does
+// not depend on the order of the faces).  Edge functions and interpolation
+// are FP64 with explicitly rounded operations in a fixed order.
+
+struct DepthGrid {
+  int au, av, H, W, ax;
+  double u0, v0, du, dv, sign;
+};
+
+TC_D int depth_key(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : (i ^ 0x7fffffff);
+}
+TC_D float depth_value(int k) { return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff)); }
+TC_D double edge_rn(double au, double av, double bu, double bv, double pu, double pv) {
+  return __dsub_rn(__dmul_rn(__dsub_rn(bu, au), __dsub_rn(pv, av)), __dmul_rn(__dsub_rn(bv, av), __dsub_rn(pu, au)));
+}
+
+template <class R>
+__global__ void __launch_bounds__(kBlock) k_depth_faces(const EnvView<R> e, DepthGrid g, int* __restrict__ key) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= e.nfc) return;
+  const int nv = e.nv;
+  double U[3], V[3], Hh[3];
+  for (int k = 0; k < 3; ++k) {
+    const int v = e.cfaces[k * e.nfc + f];
+    U[k] = __dadd_rn(e.X0[g.au * nv + v], (double)e.u[g.au * nv + v]);
+    V[k] = __dadd_rn(e.X0[g.av * nv + v], (double)e.u[g.av * nv + v]);
+    Hh[k] = __dmul_rn(g.sign, __dadd_rn(e.X0[g.ax * nv + v], (double)e.u[g.ax * nv + v]));
+  }
+  const double A2 = edge_rn(U[0], V[0], U[1], V[1], U[2], V[2]);
+  if (A2 == 0.0) return;
+  const double umin = fmin(U[0], fmin(U[1], U[2])), umax = fmax(U[0], fmax(U[1], U[2]));
+  const double vmin = fmin(V[0], fmin(V[1], V[2])), vmax = fmax(V[0], fmax(V[1], V[2]));
+  // candidate columns / rows around the box, each tested exactly below
+  // (clamped in floating point first, so that the conversions stay in range)
+  const long long c0 = (long long)fmax(0.0, floor((umin - g.u0) / g.du - 0.5) - 1.0);
+  const long long c1 = (long long)fmin((double)g.W - 1.0, ceil((umax - g.u0) / g.du - 0.5) + 1.0);
+  const long long r0 = (long long)fmax(0.0, floor((vmin - g.v0) / g.dv - 0.5) - 1.0);
+  const long long r1 = (long long)fmin((double)g.H - 1.0, ceil((vmax - g.v0) / g.dv - 0.5) + 1.0);
+  for (long long r = r0; r <= r1; ++r) {
+    const double pv = __dadd_rn(g.v0, __dmul_rn((double)r + 0.5, g.dv));
+    if (pv < vmin || pv > vmax) continue;
+    for (long long c = c0; c <= c1; ++c) {
+      const double pu = __dadd_rn(g.u0, __dmul_rn((double)c + 0.5, g.du));
+      if (pu < umin || pu > umax) continue;
+      const double ea = edge_rn(U[1], V[1], U[2], V[2], pu, pv);
+      const double eb = edge_rn(U[2], V[2], U[0], V[0], pu, pv);
+      const double ec = edge_rn(U[0], V[0], U[1], V[1], pu, pv);
+      const bool in = (ea >= 0 && eb >= 0 && ec >= 0) || (ea <= 0 && eb <= 0 && ec <= 0);
+      if (!in) continue;
+      const double h = __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(ea, Hh[0]), __dmul_rn(eb, Hh[1])), __dmul_rn(ec, Hh[2])), A2);
+      atomicMax(&key[r * g.W + c], depth_key((float)h));
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_depth_init(int* key, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) key[i] = INT_MIN;
+}
+
+__global__ void __launch_bounds__(kBlock) k_depth_resolve(float* out, uint8_t* mask, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k = reinterpret_cast<const int*>(out)[i];
+  const bool hit = k != INT_MIN;
+  out[i] = hit ? depth_value(k) : 0.f;
+  if (mask) mask[i] = hit ? 1 : 0;
+}
+
+// The map is built in place: `out` holds the integer keys until resolved.
+template <class R>
+tc_status launch_depth_map(const Env& env, const tc_grid& grid, float* out, uint8_t* mask, cudaStream_t s) {
+  const int npix = grid.H * grid.W;
+  DepthGrid g{grid.axis_u, grid.axis_v, grid.H, grid.W, env.thick_axis, grid.origin[0], grid.origin[1],
+              grid.pixel[0], grid.pixel[1], env.out_sign};
+  int* key = reinterpret_cast<int*>(out);
+  TC_LAUNCH("k_depth_init", s, k_depth_init<<<grid_for(npix), kBlock, 0, s>>>(key, npix));
+  if (env.nfc > 0)
+    TC_LAUNCH("k_depth_faces", s, k_depth_faces<R><<<grid_for(env.nfc), kBlock, 0, s>>>(env.view<R>(), g, key));
+  TC_LAUNCH("k_depth_resolve", s, k_depth_resolve<<<grid_for(npix), kBlock, 0, s>>>(out, mask, npix));
+  return cudaGetLastError() == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+template tc_status launch_depth_map<float>(const Env&, const tc_grid&, float*, uint8_t*, cudaStream_t);
+template tc_status launch_depth_map<double>(const Env&, const tc_grid&, float*, uint8_t*, cudaStream_t);
 
 // ------------------------------------------------------- batched extraction
 

@@ -711,6 +711,7 @@ tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed_ids, i
       top = (sum / nfixed <= 0.5 * (lo[ax] + hi[ax])) ? 1 : 0;
       a.put(part);
     }
+    env.out_sign = top ? 1.0 : -1.0;
     uint8_t* band = a.alloc<uint8_t>(nv);
     int32_t* flag = a.alloc<int32_t>(std::max(env.nf, 1));
     int32_t* pos = a.alloc<int32_t>(std::max(env.nf, 1));

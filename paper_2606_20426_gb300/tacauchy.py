@@ -26,7 +26,8 @@ EXPORTS = ["tc_create_scene", "tc_step", "tc_step_batch", "tc_stress", "tc_tract
            "tc_env_info", "tc_destroy", "tc_status_str", "tc_stress_from_F", "tc_profile_enable",
            "tc_profile_read", "tc_pressure_map_noalloc", "tc_server_create", "tc_submit", "tc_poll", "tc_wait",
            "tc_server_info", "tc_server_stream", "tc_server_destroy", "tc_pcg_shape", "tc_autotune_pcg",
-           "tc_energy_gradient", "tc_extract_batch"]
+           "tc_energy_gradient", "tc_extract_batch", "tc_vertex_forces", "tc_force_pressure_map",
+           "tc_depth_map"]
 
 
 class TcError(RuntimeError):
@@ -126,6 +127,9 @@ def load():
         "tc_extract_batch": [ctypes.POINTER(P), ctypes.c_int32, ctypes.POINTER(P), ctypes.POINTER(P),
                              ctypes.POINTER(P)],
         "tc_contact_force": [P, P],
+        "tc_vertex_forces": [P, P, P, P, P],
+        "tc_depth_map": [P, ctypes.POINTER(Grid), P, P],
+        "tc_force_pressure_map": [P, ctypes.POINTER(Grid), P, P],
         "tc_energy_gradient": [P, P, P],
         "tc_surface_faces": [P, P, P],
         "tc_boundary_faces": [P, P, P],
@@ -311,6 +315,43 @@ class Env:
         g = np.empty((self.info["nv"], 3), dtype=np.float64)
         _check(self.lib.tc_energy_gradient(self.h, ctypes.byref(E), g.ctypes.data), "tc_energy_gradient")
         return E.value, g
+
+    def vertex_forces(self):
+        """Algorithm 2 per contact vertex: (f, f_n, f_tau) as (3, nvc) and p
+        (nvc,) float32 CUDA tensors."""
+        n = self.info["nvc"]
+        t = [self.torch.empty((3, n), dtype=self.torch.float32, device="cuda") for _ in range(3)]
+        p = self.torch.empty((n,), dtype=self.torch.float32, device="cuda")
+        _check(self.lib.tc_vertex_forces(self.h, *[ctypes.c_void_p(x.data_ptr()) for x in t],
+                                         ctypes.c_void_p(p.data_ptr())), "tc_vertex_forces")
+        return t[0], t[1], t[2], p
+
+    def force_pressure_map(self, grid=None, out=None, mask=None):
+        """(H, W) map of the contact-force pressure |f_k| / A_k and its mask."""
+        g = make_grid(grid) if grid is not None else None
+        H, W = (int(grid["H"]), int(grid["W"])) if grid is not None else (self.info["H"], self.info["W"])
+        if out is None:
+            out = self.torch.empty((H, W), dtype=self.torch.float32, device="cuda")
+        if mask is None:
+            mask = self.torch.empty((H, W), dtype=self.torch.uint8, device="cuda")
+        _check(self.lib.tc_force_pressure_map(self.h, ctypes.byref(g) if g is not None else None,
+                                              ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(mask.data_ptr())),
+               "tc_force_pressure_map")
+        return out, mask
+
+    def depth_map(self, grid=None, out=None, mask=None):
+        """(H, W) float32 height of the deformed contact surface seen from the
+        contact side, and its coverage mask (tc_depth_map)."""
+        g = make_grid(grid) if grid is not None else None
+        H, W = (int(grid["H"]), int(grid["W"])) if grid is not None else (self.info["H"], self.info["W"])
+        if out is None:
+            out = self.torch.empty((H, W), dtype=self.torch.float32, device="cuda")
+        if mask is None:
+            mask = self.torch.empty((H, W), dtype=self.torch.uint8, device="cuda")
+        _check(self.lib.tc_depth_map(self.h, ctypes.byref(g) if g is not None else None,
+                                     ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(mask.data_ptr())),
+               "tc_depth_map")
+        return out, mask
 
     def contact_force(self):
         f = np.zeros(3)

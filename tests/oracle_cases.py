@@ -8,8 +8,9 @@ Cases (Algorithm 2's step, dynamic dt = 1/60 s unless stated):
       each indenter family, full depth reached in 4 steps with tangential
       slip; 3 steps are run.
   bench-59k   the 59,220-tet bench env itself (its first load step).
-  close-pairs small pad under a 1 mm sphere with a barrier stiffness of
-      8 N/m, so that contact pairs settle below 1e-2 dhat (quasi-static).
+  close-pairs small pad of 1 mm elements under a 3 mm sphere with a barrier
+      stiffness of 1 N/m, so that contact pairs settle below 1e-2 dhat
+      (quasi-static).
   parallel-edges small pad under a cylinder lying along the pad's x edges
       (gel and indenter edges exactly parallel: the edge-edge mollifier is
       active), quasi-static.
@@ -50,10 +51,12 @@ def build_case(name):
     if name == "bench-59k":
         return workloads.gelsight_env(0, mesh=meshes.graded_pad())
     if name == "close-pairs":
-        # a 1 mm sphere pressed 0.05 mm with kappa = 8 N/m: the barrier carries
-        # ~0.1 N at pair distances of ~5e-3 dhat (about 100 CCD-limited substeps)
-        env = copy.deepcopy(workloads.small_env(6, steps=1, step_depth=0.05e-3, radius=1e-3, level=3))
-        env["opts"]["kappa"] = 8.0
+        # a 3 mm sphere pressed 0.05 mm into a pad of 1 mm elements with kappa =
+        # 1 N/m: the barrier carries the load at pair distances of ~3e-3 dhat
+        # (about 90 CCD-limited substeps)
+        env = copy.deepcopy(workloads.small_env(8, nx=8, ny=8, nz=2, steps=1, step_depth=0.05e-3, radius=3e-3,
+                                                level=4))
+        env["opts"]["kappa"] = 1.0
         return env
     if name == "parallel-edges":
         Lx, Ly, Lz, dhat = 8e-3, 8e-3, 2e-3, 0.05e-3

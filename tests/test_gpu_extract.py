@@ -235,3 +235,31 @@ def test_extract_batch_equals_per_env_calls(precision):
     assert torch.equal(one, ref[3][1])
     for g in envs:
         g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_depth_map_bit_exact(precision):
+    """tc_depth_map (the deformed surface's height field, Sec. III-D's depth)
+    equals the oracle's z-buffer of the same deformed contact faces bit for
+    bit (same FP64 operations in the same order, one rounding to FP32), at
+    rest, after indentation steps, and on another grid."""
+    cfgs = [workloads.small_env(1, steps=2), workloads.gelsight_env(3, steps=4, target_tets=4000, grid_hw=(60, 80))]
+    for c in cfgs:
+        g = _gpu_env(c, precision)
+        ref = Scene(c)
+        for k in range(3):
+            if k:
+                g.step(c["poses"][k - 1])
+            x = g.positions()
+            m, mask = g.depth_map()
+            mref, mask_ref = ref.depth_map(x)
+            assert np.array_equal(mask.cpu().numpy(), mask_ref)
+            assert np.array_equal(m.cpu().numpy(), mref)
+            if k == 2:
+                gr = _other_grids(c)[3]
+                m2, k2 = g.depth_map(grid=gr)
+                r2, rk2 = ref.depth_map(x, grid=gr)
+                assert np.array_equal(k2.cpu().numpy(), rk2) and np.array_equal(m2.cpu().numpy(), r2)
+        # pressed: the surface under the indenter is below the rest height
+        assert mref[mask_ref == 1].min() < ref.X[:, 2].max() - 0.5 * c["depth"] / 2
+        g.close()

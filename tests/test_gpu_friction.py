@@ -86,3 +86,28 @@ def test_zero_friction_is_the_frictionless_path():
         assert np.array_equal(g1.positions(), g2.positions())
         g1.close()
         g2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_vertex_forces_and_force_pressure_map(oracle_dragged, precision):
+    """Algorithm 2's per-vertex decomposition (f, f_n, f_tau, p = |f|/A) and
+    its pixel map, friction included, against the oracle's at the GPU state."""
+    from paper_2606_20426_gb300 import Env
+    env, ref = oracle_dragged
+    g = Env(env, precision=precision)
+    for p_ in env["poses"]:
+        g.step(p_)
+    x = g.positions()
+    f, fn, ft, p = (t.cpu().numpy().astype(np.float64) for t in g.vertex_forces())
+    rf, rfn, rft, rp, _, _ = ref.vertex_contact_forces(x)
+    scale = np.abs(rf).max()
+    tol = 1e-3 if precision == "fp32" else 1e-6
+    assert np.abs(f.T - rf).max() <= tol * scale
+    assert np.abs(fn.T - rfn).max() <= tol * scale and np.abs(ft.T - rft).max() <= tol * scale
+    assert np.abs(p - rp).max() <= tol * np.abs(rp).max()
+    assert np.abs(f.sum(axis=1) - g.contact_force()).max() <= 1e-4 * scale
+    m, mask = g.force_pressure_map()
+    mref, mask_ref = ref.pressure_map(p_vertex=rp)
+    assert np.array_equal(mask.cpu().numpy(), mask_ref)
+    assert rel_fro(m.cpu().numpy(), mref) <= 1e-3
+    g.close()

@@ -440,3 +440,43 @@ def test_vertex_normal_and_area_worked_example():
     assert A[0] == pytest.approx((0.5 + np.sqrt(2) / 2) / 3, rel=1e-15)
     assert np.allclose(n[1], [0, 0, 1]) and np.allclose(n[4], np.array([0, 1, 1]) / np.sqrt(2))
     assert A[2] == pytest.approx(0.5 / 3) and A[3] == pytest.approx(np.sqrt(2) / 6)
+
+
+# ------------------------------------------------ depth map (Sec. III-D)
+
+def test_depth_map_rest_and_affine():
+    """At rest the map is the flat top height everywhere on the pad; under
+    x = A X + c with the top tilted (z' = z + a x + b y) and shifted in the
+    plane, every covered pixel centre shows the tilted plane's height at the
+    point of the rest surface that the map sends there (exact for a plane),
+    and pixels off the moved surface are uncovered."""
+    env = workloads.pad_env(0, steps=1)
+    sc = Scene(env)
+    m, mask = sc.depth_map()
+    assert mask.all() and np.all(m == np.float32(4e-3))
+    A = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [2e-3, -1e-3, 1.0]])
+    c = np.array([0.7e-3, -0.4e-3, 0.0])
+    x = sc.X @ A.T + c
+    m, mask = sc.depth_map(x)
+    U, Vv = _pixel_centres(env["grid"])
+    Xr, Yr = U - c[0], Vv - c[1]                      # rest point mapped to the pixel centre
+    expect = (4e-3 + 2e-3 * Xr - 1e-3 * Yr).astype(np.float32)
+    inside = (Xr > 1e-9) & (Xr < 20e-3 - 1e-9) & (Yr > 1e-9) & (Yr < 20e-3 - 1e-9)
+    outside = (Xr < -1e-9) | (Xr > 20e-3 + 1e-9) | (Yr < -1e-9) | (Yr > 20e-3 + 1e-9)
+    assert np.all(mask[inside] == 1) and np.all(mask[outside] == 0)
+    assert np.abs(m[inside] - expect[inside]).max() <= 2 * np.spacing(np.float32(4e-3))
+
+
+def test_depth_map_takes_the_surface_nearest_the_indenter():
+    """Two overlapping faces at different heights over the same pixels (a
+    fold): the z-buffer keeps the higher one, whichever comes first."""
+    x = np.array([[0, 0, 1.0], [1, 0, 1.0], [0, 1, 1.0], [0, 0, 2.0], [1, 0, 2.0], [0, 1, 2.0]])
+    for faces in ([[0, 1, 2], [3, 4, 5]], [[3, 4, 5], [0, 1, 2]]):
+        sc = Scene.__new__(Scene)
+        sc.cfaces = np.array(faces)
+        sc.thick_axis, sc.out_sign = 2, 1.0
+        g = dict(axis_u=0, axis_v=1, origin=(0.0, 0.0), pixel=(0.1, 0.1), H=10, W=10)
+        m, mask = sc.depth_map(x, grid=g)
+        r, c = np.indices((10, 10))
+        assert np.all(m[mask == 1] == 2.0)
+        assert np.all(mask[r + c <= 8] == 1) and np.all(mask[r + c >= 10] == 0)  # centres on the hypotenuse: either
