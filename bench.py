@@ -700,6 +700,160 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_configs(args):
+    """Measurements of the other workload configurations (one JSON line with
+    one entry per configuration asked for in --configs):
+      c1  the paper-sized 1,800-tet FP64 pad, 10 quasi-static steps per env,
+          seeds 0-9, plain one-env-per-launch form;
+      c3  60 uneven envs (20 pads 5k-60k tets, 20 domes 8k-40k, 20 blocks
+          10k-80k) stepped together: tc_step_batch + tc_extract_batch per step;
+      c4  open-loop Poisson arrivals at several rates from several numbers of
+          live GelSight-like envs through the step server (p50 / p99);
+      c5  1,024 envs of ~20k tets (pads and domes) stepped together, and one
+          ~1.9M-tet pad under a three-sphere cluster stepped alone."""
+    import numpy as np
+    import torch
+    from paper_2606_20426_gb300 import Env, Server, extract_batch, step_batch
+    from synth import meshes, workloads
+    torch.cuda.set_device(0)
+    out = {"metric": METRIC, "unit": UNIT, "mode": "configurations"}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    which = args.configs.split(",")
+
+    def batched(envs, cfgs, steps, first=0):
+        outs = [(torch.empty((6, e.info["nt"]), device="cuda"),
+                 torch.empty((e.info["H"], e.info["W"]), device="cuda") if e.info["H"] else None) for e in envs]
+        ms = []
+        for k in range(first, first + steps):
+            torch.cuda.synchronize()
+            a, z = ev(), ev()
+            a.record()
+            codes = step_batch(envs, [c["poses"][k] for c in cfgs])
+            extract_batch(envs, [o[0] for o in outs], [o[1] for o in outs], None)
+            z.record()
+            z.synchronize()
+            if any(codes):
+                raise RuntimeError(f"statuses {codes}")
+            ms.append(a.elapsed_time(z))
+        return ms
+
+    if "c1" in which:
+        cfgs = [workloads.pad_env(s) for s in range(10)]
+        envs = [Env(c, precision="fp64") for c in cfgs]
+        sig = [torch.empty((6, e.info["nt"]), device="cuda") for e in envs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        a, z = ev(), ev()
+        a.record()
+        for k in range(10):
+            for e, c, sg in zip(envs, cfgs, sig):
+                e.step(c["poses"][k])
+                e.stress(sg)
+                e.pressure_map()
+        z.record()
+        z.synchronize()
+        ms = a.elapsed_time(z)
+        out["c1"] = {"workload": "1,800-tet pad, FP64, 10 quasi-static steps, seeds 0-9, plain form",
+                     "env_steps": 100, "value": round(100 / (ms / 1e3), 3),
+                     "ms_per_env_step": round(ms / 100, 3),
+                     "newton_per_env_step": sum(e.get_info()["newton_iters"] for e in envs) / 100}
+        for e in envs:
+            e.close()
+    if "c3" in which:
+        cfgs = workloads.mixed_envs(0)
+        envs = [Env(c, precision="fp32") for c in cfgs]
+        ms = batched(envs, cfgs, args.warmup, 0)
+        ms = batched(envs, cfgs, args.steps, args.warmup)
+        tot = sum(ms)
+        out["c3"] = {"workload": "60 envs: 20 pads 5k-60k, 20 domes 8k-40k, 20 blocks 10k-80k tets (log-uniform)",
+                     "tets_total": int(sum(e.info["nt"] for e in envs)), "steps": args.steps,
+                     "value": round(len(envs) * args.steps / (tot / 1e3), 3),
+                     "ms_per_batched_step": round(tot / args.steps, 3),
+                     "p50_ms": round(float(np.percentile(ms, 50)), 3), "p99_ms": round(float(np.percentile(ms, 99)), 3)}
+        for e in envs:
+            e.close()
+    if "c4" in which:
+        mesh = meshes.graded_pad()
+        res = []
+        for n_env in (8, 64, 256):
+            cfgs = [workloads.gelsight_env(s, mesh=mesh) for s in range(n_env)]
+            envs = [Env(c, precision="fp32") for c in cfgs]
+            slots = min(n_env, 64)
+            srv = Server(hbm_budget_bytes=int(sum(e.info["device_bytes"] for e in envs) * 2), max_slots=slots,
+                         workers=0 if n_env <= 8 else 16)
+            nxt = [0] * n_env
+            for rate in (500.0, 2000.0, 20000.0):
+                nreq = 2 * n_env
+                gaps = np.random.default_rng(int(rate)).exponential(1.0 / rate, size=nreq)
+                tickets = []
+                t0 = time.perf_counter()
+                tn = t0
+                for i in range(nreq):
+                    tn += gaps[i]
+                    d = tn - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    b = i % n_env
+                    tickets.append(srv.submit(envs[b], cfgs[b]["poses"][nxt[b] % 20]))
+                    nxt[b] += 1
+                lat = []
+                for t in tickets:
+                    r = srv.wait(t, 600.0)
+                    if r is None or r["status"] != 0:
+                        raise RuntimeError(f"request failed: {r}")
+                    lat.append(r["latency_us"] / 1e3)
+                wall = time.perf_counter() - t0
+                res.append({"live_envs": n_env, "rate_req_s": rate, "requests": nreq,
+                            "throughput": round(nreq / wall, 2), "p50_ms": round(float(np.percentile(lat, 50)), 2),
+                            "p99_ms": round(float(np.percentile(lat, 99)), 2), "slots": slots,
+                            "workers": srv.info()["workers"]})
+            srv.close()
+            for e in envs:
+                e.close()
+        out["c4"] = {"workload": "GelSight-like 59,220-tet envs, closed set of live envs, open-loop Poisson arrivals "
+                                 "(requests round robin over the envs, 2 per env), step + nothing else",
+                     "points": res}
+    if "c5" in which:
+        cfgs = workloads.scale_envs(0, n=args.c5_envs)
+        t0 = time.perf_counter()
+        envs = [Env(c, precision="fp32") for c in cfgs]
+        create_s = time.perf_counter() - t0
+        ms = batched(envs, cfgs, 1, 0)
+        ms = batched(envs, cfgs, 2, 1)
+        tot = sum(ms)
+        out["c5_many"] = {"workload": f"{len(envs)} envs of ~20k tets (pads and domes alternating)",
+                          "tets_total": int(sum(e.info["nt"] for e in envs)),
+                          "device_bytes_total": int(sum(e.info["device_bytes"] for e in envs)),
+                          "create_s": round(create_s, 1), "steps": 2,
+                          "value": round(len(envs) * 2 / (tot / 1e3), 3), "ms_per_batched_step": round(tot / 2, 3)}
+        for e in envs:
+            e.close()
+        cfg = workloads.big_pad_env()
+        t0 = time.perf_counter()
+        g = Env(cfg, precision="fp32")
+        create_s = time.perf_counter() - t0
+        info = g.info
+        ms = []
+        for k in range(args.c5_big_steps):
+            torch.cuda.synchronize()
+            a, z = ev(), ev()
+            a.record()
+            g.step(cfg["poses"][k])
+            g.stress()
+            g.pressure_map()
+            z.record()
+            z.synchronize()
+            ms.append(a.elapsed_time(z))
+        gi = g.get_info()
+        out["c5_big"] = {"workload": "GelSight-like pad refined to ~1.9M tets under three R = 3 mm spheres",
+                         "tets": info["nt"], "verts": info["nv"], "nnzb": info["nnzb"],
+                         "contact_faces": info["nfc"], "device_bytes": info["device_bytes"],
+                         "create_s": round(create_s, 1), "ms_per_env_step": [round(m, 1) for m in ms],
+                         "newton": gi["newton_iters"], "pcg": gi["pcg_iters"], "substeps": gi["substeps"]}
+        g.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_pcg_probe(args):
     """Profiling probe: B envs take `pcg_probe` batched steps, then one PCG
     solve per launch shape runs through the autotuner.  Prints how many PCG
@@ -747,8 +901,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="profiling probe: this many batched steps, then the PCG autotuner (see run_pcg_probe)")
+    ap.add_argument("--configs", default="",
+                    help="instead of the headline: measure the listed other configurations (c1,c3,c4,c5)")
+    ap.add_argument("--c5-envs", type=int, default=1024)
+    ap.add_argument("--c5-big-steps", type=int, default=3)
     args = ap.parse_args()
-    if args.pcg_probe:
+    if args.configs:
+        run_configs(args)
+    elif args.pcg_probe:
         run_pcg_probe(args)
     elif args.impl == "reference":
         run_reference(args)

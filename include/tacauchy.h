@@ -66,8 +66,12 @@ enum { TC_FP64 = 0, TC_FP32_MIXED = 1 };
 typedef struct { const double* X; int32_t nv; const int32_t* tets; int32_t nt; } tc_mesh;
 
 /* Material (Sec. III-B, Eq. 1).  Young's modulus E (Pa), Poisson ratio nu in
- * (-1, 0.5), density (kg/m^3, used only when dt > 0). */
-typedef struct { double E, nu, density; } tc_material;
+ * (-1, 0.5), density (kg/m^3, used only when dt > 0).  per_tet_E_nu: NULL
+ * (homogeneous) or host nt x 2 row-major (E_t, nu_t) per tet, for
+ * heterogeneous gels such as the dual-layer 9DTact pad of Sec. IV-D; each tet
+ * then takes Eq. 1 and the rest-stable parameters from its own pair (E and nu
+ * above still set the default barrier stiffness).  Copied at create time. */
+typedef struct { double E, nu, density; const double* per_tet_E_nu; } tc_material;
 
 /* Solver options.
  *   dhat        IPC barrier distance (m), Sec. III-B.

@@ -61,7 +61,8 @@ def energy_density(F, mu, lam_hat, alpha):
 def pk1(F, mu, lam_hat, alpha):
     """P = dPsi/dF = mu F + lam_hat (J - alpha) cof F."""
     J = np.linalg.det(F)
-    return mu * F + lam_hat * (J - alpha)[..., None, None] * cofactor(F)
+    mu, lam_hat, alpha = (np.asarray(a, dtype=np.float64) for a in (mu, lam_hat, alpha))
+    return mu[..., None, None] * F + (lam_hat * (J - alpha))[..., None, None] * cofactor(F)
 
 
 def dpk1_dF(F, mu, lam_hat, alpha):
@@ -72,7 +73,8 @@ def dpk1_dF(F, mu, lam_hat, alpha):
     C = cofactor(F).reshape(F.shape[:-2] + (9,))
     HJ = np.einsum("ikm,jln,...mn->...ijkl", EPS, EPS, F).reshape(F.shape[:-2] + (9, 9))
     eye = np.eye(9)
-    return (mu * eye + lam_hat * C[..., :, None] * C[..., None, :]
+    mu, lam_hat, alpha = (np.asarray(a, dtype=np.float64) for a in (mu, lam_hat, alpha))
+    return (mu[..., None, None] * eye + lam_hat[..., None, None] * C[..., :, None] * C[..., None, :]
             + (lam_hat * (J - alpha))[..., None, None] * HJ)
 
 

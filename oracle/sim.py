@@ -92,6 +92,12 @@ class Scene:
         self.E, self.nu, self.rho = m["E"], m["nu"], m["density"]
         self.mu, self.lam = mat.lame(self.E, self.nu)
         _, self.lam_hat, self.alpha = mat.snh_params(self.E, self.nu)
+        if m.get("per_tet") is not None:
+            # heterogeneous material: (E, nu) per tet, Eq. 1 and the rest-stable
+            # parameters per tet (the scene's E still sets the default kappa)
+            pt = np.asarray(m["per_tet"], dtype=np.float64).reshape(-1, 2)
+            self.mu, self.lam = mat.lame(pt[:, 0], pt[:, 1])
+            _, self.lam_hat, self.alpha = mat.snh_params(pt[:, 0], pt[:, 1])
         self.Dminv, self.vol = msh.rest_shape(X, T)
         self.Dfx = msh.dF_dx(self.Dminv)
         self.h = float(o["dt"])

@@ -91,6 +91,25 @@ template <class R> static tc_status alloc_state(Env& env) {
   return TC_OK;
 }
 
+// Per-tet (mu, lam_hat) of a heterogeneous material (Eq. 1 per tet and the
+// rest-stable lam_hat = lam + mu), uploaded as 2 x nt in the kernel type.
+template <class R> static tc_status upload_material(Env& env, const double* E_nu) {
+  const int64_t nt = env.nt;
+  std::vector<R> h(2 * (size_t)nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const double E = E_nu[2 * t], nu = E_nu[2 * t + 1];
+    const double mu = E / (2.0 * (1.0 + nu));
+    const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    h[t] = (R)mu;
+    h[nt + t] = (R)(lam + mu);
+  }
+  env.mat_tet = env.arena.alloc<R>(2 * nt);
+  if (!env.mat_tet) return TC_ERR_OOM;
+  TC_CHECK(cudaMemcpyAsync(env.mat_tet, h.data(), sizeof(R) * 2 * nt, cudaMemcpyHostToDevice, env.stream));
+  TC_CHECK(cudaStreamSynchronize(env.stream));
+  return TC_OK;
+}
+
 template <class R> static tc_status initial_check(Env& env) {
   Scalars sc{};
   tc_status st = energy_at_state<R>(exec_of<R>(env), env, &sc);
@@ -269,6 +288,11 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   if (opts->dt > 0 && !(material->density > 0)) return TC_ERR_INVALID_ARG;
   for (int64_t i = 0; i < 4 * (int64_t)mesh->nt; ++i)
     if (mesh->tets[i] < 0 || mesh->tets[i] >= mesh->nv) return TC_ERR_INVALID_MESH;
+  if (material->per_tet_E_nu)
+    for (int64_t t = 0; t < mesh->nt; ++t) {
+      const double E = material->per_tet_E_nu[2 * t], nu = material->per_tet_E_nu[2 * t + 1];
+      if (!(E > 0) || !std::isfinite(E) || !(nu > -1.0 && nu < 0.5)) return TC_ERR_INVALID_ARG;
+    }
   tc_env* h = new (std::nothrow) tc_env;
   if (!h) return TC_ERR_OOM;
   Env& env = h->impl;
@@ -330,6 +354,9 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   if (st == TC_OK) st = tc::build_bsr(env, mesh->tets, fixed, nfixed);
   if (st == TC_OK)
     st = env.precision == TC_FP64 ? tc::alloc_state<double>(env) : tc::alloc_state<float>(env);
+  if (st == TC_OK && material->per_tet_E_nu)
+    st = env.precision == TC_FP64 ? tc::upload_material<double>(env, material->per_tet_E_nu)
+                                  : tc::upload_material<float>(env, material->per_tet_E_nu);
   if (st == TC_OK)
     st = env.precision == TC_FP64 ? tc::initial_check<double>(env) : tc::initial_check<float>(env);
   if (st == TC_OK && cudaStreamSynchronize(env.stream) != cudaSuccess) st = TC_ERR_CUDA;

@@ -564,6 +564,7 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         continue;
       }
       const double pmax = pre[j].pmax;
+      c.pmax = pmax;
       const double decrement = -0.5 * pre[j].reduce_tmp[3];
       const double e_noise = (e.precision == TC_FP64 ? 1e-14 : 1e-7) * std::fabs(c.E0);
       const bool nonfinite = (sc[j].status & ST_NONFINITE) != 0;
@@ -684,6 +685,10 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
         c.phase = StepCtl::NEWTON;
         if (trace_on())
           std::fprintf(stderr, "[tc] req %llu   accepted alpha=%.6e\n", (unsigned long long)c.tag, c.alpha);
+        // a short full step (within 10 ptol) that the energy could only
+        // accept after halvings down to a move below ptol: the energy no
+        // longer resolves the remaining decrease, so the substep ends here
+        if (c.pmax <= 10.0 * e.ptol && c.alpha * c.pmax <= e.ptol) finish_substep(c);
         continue;
       }
       if (++c.halvings > 60) {

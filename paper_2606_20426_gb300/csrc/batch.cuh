@@ -137,6 +137,7 @@ struct StepCtl {
   double E1 = 0.0, ext = 0.0;  // energy after an accepted full step; continuation factor - 1
   int sub = 0, newton = 0, halvings = 0;
   bool tight = false;  // mixed mode: the substep's solves run to the verification tolerance
+  double pmax = 0.0;   // max-norm of the current Newton direction
   enum Phase { START, ADVANCE, NEWTON, LINESEARCH, EXTEND, DONE, FAILED } phase = START;
   tc_status status = TC_OK;
 };

@@ -194,7 +194,9 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
     load_G<R>(e, u, el, t, G, Bm);
     const Kin<R> k = kinematics<R>(G);
     const R V = e.vol[el];
-    energy = (double)(V * psi_of<R>(G, k, e.mu, e.lam_hat));
+    R mu, lh;
+    tet_material<R>(e, el, mu, lh);
+    energy = (double)(V * psi_of<R>(G, k, mu, lh));
     if (HESS) {
       const int nt = e.nt;
       // P = mu (G + G^T - trG I - cof G) + lam_hat (J-1) cof F
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
       for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
           const R cofF = (i == j ? R(1) + k.trG : R(0)) - G[j][i] + k.cG[i][j];
-          P[i][j] = e.mu * (G[i][j] + G[j][i] - (i == j ? k.trG : R(0)) - k.cG[i][j]) + e.lam_hat * k.Jm1 * cofF;
+          P[i][j] = mu * (G[i][j] + G[j][i] - (i == j ? k.trG : R(0)) - k.cG[i][j]) + lh * k.Jm1 * cofF;
         }
       // gradient: g_a = V P n_a, n_a = row (a-1) of Dm^-1, n_0 = -sum
       R gs[4][3];
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
       for (int a = 0; a < 4; ++a)
         for (int i = 0; i < 3; ++i) e.eslot[(int64_t)(3 * a + i) * nt + el] = gs[a][i];
       R H[45];
-      psd_tangent<R>(G, k, e.mu, e.lam_hat, H);
+      psd_tangent<R>(G, k, mu, lh, H);
       // stiffness blocks K_ab[i][k] = V sum_jl H[(i,j),(k,l)] n_a[j] n_b[l]
       // for corners a <= b (n_a: gradient of corner a's shape function)
       R n[4][3];
@@ -271,7 +273,9 @@ __global__ void __launch_bounds__(kBlock) k_stress(const EnvView<R> e, const R* 
   R G[3][3], Bm[3][3];
   load_G<R>(e, u, el, t, G, Bm);
   R s6[6];
-  cauchy6<R>(G, kinematics<R>(G), e.mu, e.lam_hat, s6);
+  R mu, lh;
+  tet_material<R>(e, el, mu, lh);
+  cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
   const int64_t nt = e.nt;
 #pragma unroll
   for (int c = 0; c < 6; ++c) sig[c * nt + el] = (float)s6[c];

@@ -58,6 +58,7 @@ TC_HD int64_t kblk_size(int nt) { return (int64_t)90 * ((nt + kKblkGroup - 1) / 
 template <class R> struct EnvView {
   int nv, nt, nfc, nec, nvc, ind_nv, ind_nf, ind_ne, npix;
   R mu, lam_hat, alpha;       // material (rest-stable Neo-Hookean)
+  const R* mat;               // per-tet (mu, lam_hat) as 2 x nt, or null (homogeneous)
   R inv_h2;                   // 1/dt^2 (dynamic) or 0
   double dhat, kappa;
   int pcg_max;                // this env's PCG iteration cap
@@ -265,6 +266,7 @@ struct Env {
   int32_t* grid_items[3] = {nullptr, nullptr, nullptr};
   float* prim_box[3] = {nullptr, nullptr, nullptr};
   // typed fields (one of the two sets is allocated)
+  void* mat_tet = nullptr;    // per-tet (mu, lam_hat), 2 x nt, or null
   void* Dminv = nullptr;
   void* vol = nullptr;
   void* mass = nullptr;
@@ -305,6 +307,7 @@ template <class R> EnvView<R> Env::view() const {
   e.nv = nv; e.nt = nt; e.nfc = nfc; e.nec = nec; e.nvc = nvc;
   e.ind_nv = ind_nv; e.ind_nf = ind_nf; e.ind_ne = ind_ne; e.npix = H * W;
   e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
+  e.mat = (const R*)mat_tet;
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
   e.dhat = dhat; e.kappa = kappa; e.pcg_max = pcg_max;
   e.mu_f = friction ? (R)mu_f : R(0);

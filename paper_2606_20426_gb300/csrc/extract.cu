@@ -280,7 +280,9 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_extract(const XBa
       const int el = (int)(i - tet_off[e]);
       R G[3][3], Bm[3][3], s6[6];
       load_G<R>(x.v, x.v.u, el, x.v.tets[el], G, Bm);
-      cauchy6<R>(G, kinematics<R>(G), x.v.mu, x.v.lam_hat, s6);
+      R mu, lh;
+      tet_material<R>(x.v, el, mu, lh);
+      cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
       const int64_t nt = x.v.nt;
 #pragma unroll
       for (int c = 0; c < 6; ++c) x.sigma[c * nt + el] = (float)s6[c];

@@ -61,6 +61,17 @@ template <class R> TC_D Kin<R> kinematics(const R G[3][3]) {
   return k;
 }
 
+// Material of tet el: its own (mu, lam_hat) when the env is heterogeneous.
+template <class R> TC_D void tet_material(const EnvView<R>& e, int el, R& mu, R& lam_hat) {
+  if (e.mat) {
+    mu = e.mat[el];
+    lam_hat = e.mat[(int64_t)e.nt + el];
+  } else {
+    mu = e.mu;
+    lam_hat = e.lam_hat;
+  }
+}
+
 // Cauchy stress (xx, yy, zz, xy, yz, zx) from G and its kinematics.
 template <class R> TC_D void cauchy6(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R s6[6]) {
   const R muJ = mu / k.J;
@@ -88,7 +99,9 @@ TC_D void face_traction(const EnvView<R>& e, const int32_t* __restrict__ cparent
   const int el = cparent[f];
   R G[3][3], Bm[3][3], s6[6];
   load_G<R>(e, e.u, el, e.tets[el], G, Bm);
-  cauchy6<R>(G, kinematics<R>(G), e.mu, e.lam_hat, s6);
+  R mu, lh;
+  tet_material<R>(e, el, mu, lh);
+  cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
   const int a = e.cfaces[f], b = e.cfaces[nfc + f], c = e.cfaces[2 * nfc + f];
   R e1[3], e2[3];
   for (int d = 0; d < 3; ++d) {

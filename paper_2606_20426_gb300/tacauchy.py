@@ -41,7 +41,8 @@ class Mesh(ctypes.Structure):
 
 
 class Material(ctypes.Structure):
-    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double)]
+    _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double),
+                ("per_tet_E_nu", ctypes.c_void_p)]
 
 
 class SceneOpts(ctypes.Structure):
@@ -239,7 +240,11 @@ class Env:
             prec = TC_FP64 if prec == "fp64" else TC_FP32_MIXED
         self.precision = prec
         mesh = Mesh(X.ctypes.data, X.shape[0], T.ctypes.data, T.shape[0])
-        mat = Material(m["E"], m["nu"], m["density"])
+        per_tet = None
+        if m.get("per_tet") is not None:
+            per_tet = np.ascontiguousarray(m["per_tet"], dtype=np.float64).reshape(-1, 2)
+        self._keep = self._keep + (per_tet,)
+        mat = Material(m["E"], m["nu"], m["density"], per_tet.ctypes.data if per_tet is not None else None)
         opts = SceneOpts(o["dhat"], o.get("kappa", 0.0), o.get("dt", 0.0), o.get("newton_rtol", 1e-6),
                          o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1),
                          o.get("friction_mu", 0.0), o.get("friction_eps_v", 0.01))

@@ -158,13 +158,14 @@ def sensor_mesh(sensor, target_tets):
 
 
 def sensor_env(seed, sensor="pad", target_tets=20000, steps=20, dhat=0.05e-3, dt=1.0 / 60.0,
-               precision="fp32", pixel=0.1e-3):
+               precision="fp32", pixel=0.1e-3, mesh=None):
     """A GelSight-style indentation (seeded sphere / cylinder / filleted box,
     depth U[0.2, 1.0] mm, slip U[0, 0.5] mm over `steps` dynamic steps) on a
     pad, dome or block sensor of about target_tets tets; the indenter starts
-    dhat above the highest gel point near the sensor centre."""
+    dhat above the highest gel point near the sensor centre.  mesh: a
+    ((X, T), (Lx, Ly)) from sensor_mesh to reuse."""
     rng = SplitMix64(seed)
-    (X, T), (Lx, Ly) = sensor_mesh(sensor, target_tets)
+    (X, T), (Lx, Ly) = mesh if mesh is not None else sensor_mesh(sensor, target_tets)
     kind, V, F, yaw = gelsight_indenter(rng)
     cx = Lx / 2 + rng.uniform(-1e-3, 1e-3)
     cy = Ly / 2 + rng.uniform(-1e-3, 1e-3)
@@ -196,6 +197,70 @@ def mixed_envs(seed, n_per_family=20, pads=(5000, 60000), domes=(8000, 40000), b
             nt = int(math.exp(rng.uniform(math.log(lo), math.log(hi))))
             out.append(sensor_env(seed * 1000 + len(out), fam, nt, steps=steps, precision=precision))
     return out
+
+
+DUAL_LAYER = dict(top_thickness=1.5e-3, E_top=0.3e6, E_base=1.2e6, nu=0.45)
+
+
+def dual_layer_material(X, T, top_thickness=DUAL_LAYER["top_thickness"], E_top=DUAL_LAYER["E_top"],
+                        E_base=DUAL_LAYER["E_base"], nu=DUAL_LAYER["nu"]):
+    """(E, nu) per tet of a two-layer gel: tets whose centroid lies within
+    top_thickness of the top face take E_top, the rest E_base (the paper names
+    a dual-layer 9DTact pad without giving its values; these are the stand-in
+    values of this build)."""
+    ztop = X[:, 2].max()
+    zc = X[T].mean(axis=1)[:, 2]
+    E = np.where(zc >= ztop - top_thickness, E_top, E_base)
+    return np.stack([E, np.full(len(T), nu)], axis=1)
+
+
+def dual_layer_env(seed, target_tets=20000, steps=20, precision="fp32", mesh=None):
+    """The 9DTact-like block of sensor_env with a soft top layer over a stiff
+    base (per-tet material)."""
+    env = sensor_env(seed, "block", target_tets, steps=steps, precision=precision, mesh=mesh)
+    env["material"]["per_tet"] = dual_layer_material(env["X"], env["tets"])
+    env["name"] = env["name"].replace("block", "dual-block")
+    return env
+
+
+def scale_envs(seed, n=1024, target_tets=20000, steps=20, precision="fp32"):
+    """n environments of about target_tets tets, pads and domes alternating
+    (one mesh per family, shared), each with its own seeded indenter."""
+    meshes_ = {fam: sensor_mesh(fam, target_tets) for fam in ("pad", "dome")}
+    return [sensor_env(seed * 100000 + i, fam, target_tets, steps=steps, precision=precision, mesh=meshes_[fam])
+            for i, fam in zip(range(n), ("pad", "dome") * n)]
+
+
+def sphere_cluster(radius=3e-3, spacing=7e-3, edge=0.25e-3):
+    """Three icospheres of the same radius at the corners of an equilateral
+    triangle (side `spacing`) in the z = 0 plane, as one rigid surface."""
+    V1, F1 = indenters.icosphere(radius, icosphere_level_for(radius, edge))
+    Vs, Fs = [], []
+    for k in range(3):
+        a = 2 * math.pi * k / 3
+        c = spacing / math.sqrt(3.0) * np.array([math.cos(a), math.sin(a), 0.0])
+        Fs.append(F1 + len(V1) * k)
+        Vs.append(V1 + c)
+    return np.concatenate(Vs), np.concatenate(Fs).astype(np.int32)
+
+
+def big_pad_env(target_tets=2_000_000, depth=0.8e-3, steps=20, dhat=0.05e-3, dt=1.0 / 60.0, precision="fp32",
+                grid_hw=(240, 320)):
+    """A GelSight-like 18x24x4 mm pad refined to about target_tets tets under
+    a cluster of three R = 3 mm spheres pressed to `depth` over `steps`
+    dynamic steps."""
+    Lx, Ly, Lz = 18e-3, 24e-3, 4e-3
+    X, T = meshes.graded_pad(Lx, Ly, Lz, target_tets=target_tets)
+    V, F = sphere_cluster()
+    cx, cy = Lx / 2, Ly / 2
+    z0 = Lz + dhat - indenters.lowest_z(V)
+    start = _pose(cx, cy, z0)
+    poses = [_pose(cx, cy, z0 - (k / steps) * (dhat + depth)) for k in range(1, steps + 1)]
+    H, W = grid_hw
+    grid = dict(axis_u=1, axis_v=0, origin=(0.0, 0.0), pixel=(Ly / W, Lx / H), H=H, W=W)
+    return dict(name=f"bigpad-{len(T)}", X=X, tets=T, material=dict(MATERIAL), fixed=_fixed_bottom(X), ind_V=V,
+                ind_F=F, start_pose=start, poses=poses, grid=grid, opts=_opts(dhat, dt, precision), depth=depth,
+                kind="sphere-cluster")
 
 
 def hertz_env(nu=0.3, radius=5e-3, depth=0.25e-3, steps=5, dhat=0.01e-3, precision="fp32"):

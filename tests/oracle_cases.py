@@ -6,7 +6,9 @@ library, so it can run in spawned worker processes beside the GPU tests).
 Cases (Algorithm 2's step, dynamic dt = 1/60 s unless stated):
   pad-sphere / pad-cylinder / pad-box  graded GelSight-like pad (~3.4k tets),
       each indenter family, full depth reached in 4 steps with tangential
-      slip; 3 steps are run.
+      slip; 3 steps are run.  (Some box seeds are bistable: a filleted edge
+      sliding over gel vertices has two nearby local minima, and FP32 and
+      FP64 arithmetic can settle in different ones; seed 5 is not.)
   bench-59k   the 59,220-tet bench env itself (its first load step).
   close-pairs small pad of 1 mm elements under a 3 mm sphere with a barrier
       stiffness of 1 N/m, so that contact pairs settle below 1e-2 dhat
@@ -16,6 +18,8 @@ Cases (Algorithm 2's step, dynamic dt = 1/60 s unless stated):
       active), quasi-static.
   pad-friction the pad-sphere case with friction ratio 0.5 and velocity
       threshold 0.01 m/s (Sec. III-B), its slip doubled.
+  dual-layer  a 9DTact-like block with a soft top layer over a stiff base
+      (per-tet material), the first of 4 dynamic steps.
 """
 import copy
 import math
@@ -24,9 +28,10 @@ import numpy as np
 
 from synth import indenters, meshes, workloads
 
-CASES = ["pad-sphere", "pad-cylinder", "pad-box", "bench-59k", "close-pairs", "parallel-edges", "pad-friction"]
+CASES = ["pad-sphere", "pad-cylinder", "pad-box", "bench-59k", "close-pairs", "parallel-edges", "pad-friction",
+         "dual-layer"]
 STEPS = {"pad-sphere": 3, "pad-cylinder": 3, "pad-box": 3, "bench-59k": 1, "close-pairs": 1, "parallel-edges": 2,
-         "pad-friction": 3}
+         "pad-friction": 3, "dual-layer": 1}
 
 
 def _pose(tx, ty, tz):
@@ -44,10 +49,12 @@ def build_case(name):
         env["opts"]["friction_eps_v"] = 0.01
         return env
     if name.startswith("pad-"):
-        seed = {"pad-sphere": 3, "pad-cylinder": 0, "pad-box": 1}[name]
+        seed = {"pad-sphere": 3, "pad-cylinder": 0, "pad-box": 5}[name]
         env = workloads.gelsight_env(seed, steps=4, target_tets=4000, grid_hw=(60, 80))
         assert env["kind"] == name[4:]
         return env
+    if name == "dual-layer":
+        return workloads.dual_layer_env(2, target_tets=4000, steps=4)
     if name == "bench-59k":
         return workloads.gelsight_env(0, mesh=meshes.graded_pad())
     if name == "close-pairs":

@@ -88,6 +88,16 @@ def test_graded_pad_with_friction(oracle_runs, precision):
     g.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_dual_layer_block(oracle_runs, precision):
+    """Heterogeneous (per-tet) material: a soft 1.5 mm top layer (0.3 MPa) on
+    a stiff base (1.2 MPa)."""
+    env, g = _gpu_run("dual-layer", precision)
+    ref = oracle_runs["dual-layer"].get(timeout=560)
+    _check(env, g, ref)
+    g.close()
+
+
 def test_bench_env_first_step(oracle_runs):
     """The 59,220-tet env the benchmark steps (seed 0, a cylinder), its first
     load pose, FP32 mixed."""

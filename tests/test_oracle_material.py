@@ -168,3 +168,57 @@ def test_sym6_roundtrip():
     S = rng.standard_normal((4, 3, 3))
     S = S + np.swapaxes(S, 1, 2)
     assert np.allclose(mat.full33(mat.sym6(S)), S)
+
+
+# ------------------------------------------------- heterogeneous material
+
+def test_per_tet_material_equals_homogeneous_when_uniform():
+    """A per-tet (E, nu) table with every entry equal to the scene's material
+    gives the homogeneous scene's energy, gradient and stress."""
+    import copy
+    from oracle.sim import Scene
+    from synth import workloads
+    env = workloads.small_env(0)
+    het = copy.deepcopy(env)
+    het["material"]["per_tet"] = np.tile([env["material"]["E"], env["material"]["nu"]], (len(env["tets"]), 1))
+    a, b = Scene(env), Scene(het)
+    x = a.X + 1e-5 * np.sin(500 * a.X[:, [1, 2, 0]])
+    Ea, ga, Ha = a.elastic(x)
+    Eb, gb, Hb = b.elastic(x)
+    assert Eb == pytest.approx(Ea, rel=1e-14)
+    assert np.allclose(gb, ga, rtol=1e-13, atol=1e-25) and np.allclose(Hb, Ha, rtol=1e-12, atol=1e-20)
+    assert np.allclose(b.stress(x), a.stress(x), rtol=1e-13, atol=1e-12)
+
+
+def test_two_layers_each_follow_their_own_closed_form():
+    """Under a homogeneous uniaxial strain F = diag(1, 1, s) every tet of a
+    dual-layer pad shows the closed-form sigma_zz = mu s + lam_hat (s - alpha)
+    and sigma_xx = mu / s + lam_hat (s - alpha) of its own layer's (E, nu),
+    and the element gradients match central differences of the energy."""
+    from oracle.sim import Scene
+    from synth import workloads
+    env = workloads.small_env(0)
+    env["material"]["per_tet"] = workloads.dual_layer_material(env["X"], env["tets"], top_thickness=1e-3,
+                                                               E_top=0.2e6, E_base=0.9e6, nu=0.4)
+    sc = Scene(env)
+    s = 0.97
+    x = sc.X * np.array([1.0, 1.0, s])
+    sig = sc.stress(x)
+    pt = env["material"]["per_tet"]
+    for E in (0.2e6, 0.9e6):
+        mu, lh, al = mat.snh_params(E, 0.4)
+        sel = pt[:, 0] == E
+        assert sel.sum() > 10
+        assert np.allclose(sig[sel, 2], mu * s + lh * (s - al), rtol=1e-12)
+        assert np.allclose(sig[sel, 0], mu / s + lh * (s - al), rtol=1e-12)
+    rng = np.random.default_rng(1)
+    x = sc.X + 2e-5 * rng.standard_normal(sc.X.shape)
+    _, ge, _ = sc.elastic(x)
+    g = np.zeros((sc.nv, 3))
+    np.add.at(g, sc.T.ravel(), ge.reshape(-1, 3))
+    h = 1e-9
+    for v, k in [(5, 2), (30, 0), (61, 1)]:
+        xp, xm = x.copy(), x.copy()
+        xp[v, k] += h
+        xm[v, k] -= h
+        assert (sc.elastic(xp, False)[0] - sc.elastic(xm, False)[0]) / (2 * h) == pytest.approx(g[v, k], rel=1e-5)
