@@ -36,3 +36,14 @@ def test_invalid_arguments_rejected_without_gpu_work():
     assert lib.tc_create_scene(None, None, None, 0, None, None, None, None, None, None, ctypes.byref(h)) == 1
     assert lib.tc_step(None, None) == 1
     assert lib.tc_stress_from_F(None, -1, 3e5, 0.45, None, None) == 1
+
+
+def test_new_entry_points_reject_null_handles_without_gpu_work():
+    lib = tacauchy.load()
+    assert lib.tc_pressure_map(None, None, None, None) == 1
+    assert lib.tc_depth_map(None, None, None, None) == 1
+    assert lib.tc_vertex_forces(None, None, None, None, None) == 1
+    assert lib.tc_force_pressure_map(None, None, None, None) == 1
+    assert lib.tc_extract_batch(None, 0, None, None, None) == 0      # an empty batch is a no-op
+    assert lib.tc_extract_batch(None, 2, None, None, None) == 1
+    assert lib.tc_extract_batch(None, -1, None, None, None) == 1
