@@ -19,9 +19,13 @@ Modules
   geometry  point-triangle / edge-edge distances and their derivatives, the
             IPC log barrier and edge-edge mollifier.
   ccd       additive continuous collision detection (conservative TOI).
+  friction  IPC lagged friction (Sec. III-B's friction ratio and velocity
+            threshold): lagged pairs, smoothed potential and derivatives.
   sim       the scene: incremental potential, Newton with a sparse direct
             solve, CCD-bounded backtracking line search, indenter substeps,
-            stress / traction / pressure map / contact force (Algorithm 2).
+            stress / traction / pressure map / contact force (Algorithm 2),
+            Algorithm 2's per-vertex force decomposition, the depth map of the
+            deformed contact surface, per-tet materials.
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants, finite differences or brute force.  The paper's own
