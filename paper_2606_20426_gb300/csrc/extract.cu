@@ -12,10 +12,10 @@
 // The per-env kernels (k_traction, k_vertex_avg, k_splat, and k_stress in
 // elem.cu) serve the single-env calls.  k_extract does all of it for a whole
 // batch of envs in one cooperative launch: phase 1 streams sigma of every tet
-// and the face pressure and area of every contact face of every env, phase 2
-// averages to contact vertices, phase 3 splats to pixels, with a grid-wide
-// barrier between phases.  Each item goes through the same device functions
-// as in the per-env kernels, so the outputs are the same bit for bit.
+// and the face pressure and area of every contact face of every env; after a
+// grid-wide barrier, phase 2 forms every pixel of every map, each pixel
+// averaging its three vertices itself.  Each item goes through the same device
+// functions as in the per-env kernels, so the outputs are the same bit for bit.
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -55,13 +55,19 @@ void launch_traction(const EnvView<R>& e, const int32_t* cparent, float* t, floa
 TC_D float vertex_mean(int s, const int32_t* __restrict__ off, const int32_t* __restrict__ idx,
                        const float* __restrict__ face_p, const float* __restrict__ face_A) {
   float num = 0.f, den = 0.f;
-  for (int k = off[s]; k < off[s + 1]; ++k) {
+  for (int k = off[s]; k < off[s + 1]; ++k) {  // explicit roundings: the same value in every kernel
     const int f = idx[k] >> 2;
     const float A = face_A[f];
-    num += A * face_p[f];
-    den += A;
+    num = __fmaf_rn(A, face_p[f], num);
+    den = __fadd_rn(den, A);
   }
-  return den > 0.f ? num / den : 0.f;
+  return den > 0.f ? __fdiv_rn(num, den) : 0.f;
+}
+
+// barycentric combination of the three vertex values (one expression, shared
+// by every path, so that all of them round the same way)
+TC_D float bary(float w0, float w1, float w2, float v0, float v1, float v2) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(w0, v0), __fmul_rn(w1, v1)), __fmul_rn(w2, v2));
 }
 
 // barycentric interpolation at pixel i of npix (0 and mask 0 off the surface)
@@ -71,8 +77,8 @@ TC_D void splat_pixel(int i, int npix, const int32_t* __restrict__ pix_face, con
   const int f = pix_face[i];
   float v = 0.f;
   if (f >= 0) {
-    v = pix_w[i] * vert_p[cface_slot[f]] + pix_w[npix + i] * vert_p[cface_slot[nfc + f]] +
-        pix_w[2 * npix + i] * vert_p[cface_slot[2 * nfc + f]];
+    v = bary(pix_w[i], pix_w[npix + i], pix_w[2 * npix + i], vert_p[cface_slot[f]], vert_p[cface_slot[nfc + f]],
+             vert_p[cface_slot[2 * nfc + f]]);
   }
   out[i] = v;
   if (mask) mask[i] = f >= 0 ? 1 : 0;
@@ -299,21 +305,28 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_extract(const XBa
   }
   if (!with_map) return;
   if (!grid_barrier(xb.bar, xb.err)) return;
-  // phase 2: area-weighted means at the contact vertices (K10a)
-  const int64_t ncv = cv_off[n];
-  for (int64_t i = first; i < ncv; i += stride) {
-    const int e = env_of(cv_off, n, i);
-    const XEnv<R>& x = xb.env[e];
-    const int s = (int)(i - cv_off[e]);
-    x.vert_p[s] = vertex_mean(s, x.v.cv_face_off, x.v.cv_face_idx, x.face_p, x.face_A);
-  }
-  if (!grid_barrier(xb.bar, xb.err)) return;
-  // phase 3: the pixel map (K10b)
+  // phase 2: the pixel map (K10b), each pixel forming the area-weighted
+  // means (K10a) of its face's three contact vertices itself -- the same
+  // fixed-order sums as the per-vertex pass, so the same values, without a
+  // third phase and its barrier (the face values it reads stay in L2)
   const int64_t npx = pix_off[n];
   for (int64_t i = first; i < npx; i += stride) {
     const int e = env_of(pix_off, n, i);
     const XEnv<R>& x = xb.env[e];
-    splat_pixel((int)(i - pix_off[e]), x.npix, x.pix_face, x.pix_w, x.cface_slot, x.v.nfc, x.vert_p, x.map, x.mask);
+    const int p = (int)(i - pix_off[e]);
+    const int np_ = x.npix, nfc = x.v.nfc;
+    const int f = x.pix_face[p];
+    float v = 0.f;
+    if (f >= 0) {
+      const int32_t* off = x.v.cv_face_off;
+      const int32_t* idx = x.v.cv_face_idx;
+      v = bary(x.pix_w[p], x.pix_w[np_ + p], x.pix_w[2 * np_ + p],
+               vertex_mean(x.cface_slot[f], off, idx, x.face_p, x.face_A),
+               vertex_mean(x.cface_slot[nfc + f], off, idx, x.face_p, x.face_A),
+               vertex_mean(x.cface_slot[2 * nfc + f], off, idx, x.face_p, x.face_A));
+    }
+    x.map[p] = v;
+    if (x.mask) x.mask[p] = f >= 0 ? 1 : 0;
   }
 }
 
