@@ -226,6 +226,37 @@ def _roofline(top, infos, pcg_iters_by_env, peak, peak_kind):
     return None
 
 
+def newton_pass_bytes(name, info):
+    """Algorithmic bytes per Newton iteration of one env (FP32) of the two
+    per-iteration passes besides the PCG: the element pass with the Hessian
+    (per tet 16 B ids + 36 B Dm^-1 + 4 B volume read, 48 B gradient slots +
+    360 B stiffness blocks written; 12 B per vertex of displacement read) and
+    the assembly (per tet 4 corner gradient slots of 12 B + 4 B id read, 16
+    corner-block contributions of 36 B + 4 B id read; per BSR block 36 B
+    written; per vertex 12 B gradient + 24 B block-Jacobi inverse written)."""
+    nt, nv, nnzb = info["nt"], info["nv"], info["nnzb"]
+    if name == "k_elem_hess":
+        return nt * (16 + 36 + 4 + 48 + 360) + 12 * nv
+    if name == "k_assemble":
+        return nt * 4 * (12 + 4) + nt * 16 * (36 + 4) + nnzb * 36 + nv * (12 + 24)
+    return None
+
+
+def _newton_fracs(prof, infos, newton_by_env, peak):
+    """HBM fractions of the element (Hessian) and assembly passes over the
+    profiled repeat: bytes = sum over envs of (bytes per Newton iteration x
+    the env's Newton iterations), over the kernel's total time."""
+    out = {}
+    for name in ("k_elem_hess", "k_assemble"):
+        if name not in prof or prof[name][1] == 0:
+            continue
+        ms, n = prof[name]
+        b = sum(newton_pass_bytes(name, i) * k for i, k in zip(infos, newton_by_env))
+        out[name] = {"avg_launch_us": round(ms / n * 1e3, 2), "bytes_per_launch": int(b / n),
+                     "frac": round(b / (ms / 1e3) / 1e9 / peak, 4)}
+    return out
+
+
 def _extraction_fracs(prof, infos, peak):
     """Per-launch HBM fractions of the extraction kernels: k_extract (sigma and
     the map of every env of the batch in one launch: the sum of the four
@@ -539,6 +570,7 @@ def run_ours(args):
                          "form": "tc_step + tc_stress + tc_pressure_map per env, one env after another"}
         # ------------- per-kernel times: a profiled repeat of the batched steps
         pcg0 = [e.get_info()["pcg_iters"] for e in batched]
+        newton0 = [e.get_info()["newton_iters"] for e in batched]
         for e in batched:
             e.profile(True)
         for k in range(args.steps):
@@ -547,6 +579,7 @@ def run_ours(args):
             batched_step()
         torch.cuda.synchronize(dev)
         pcg_by_env = [e.get_info()["pcg_iters"] - p0 for e, p0 in zip(batched, pcg0)]
+        newton_by_env = [e.get_info()["newton_iters"] - n0 for e, n0 in zip(batched, newton0)]
         prof = {}
         for e in batched:
             for name, (ms, n) in e.kernel_times().items():
@@ -586,6 +619,7 @@ def run_ours(args):
         "gpu_launches_note": "kernel launches of the profiled repeat of the batched form",
         "roofline": roof,
         "extraction": _extraction_fracs(prof, infos, peak),
+        "newton_kernels": _newton_fracs(prof, infos, newton_by_env, peak),
         "kernels": kernel_table,
         "solver": {"newton_per_env_step": sum(e.get_info()["newton_iters"] for e in batched) / steps_done,
                    "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in batched) / steps_done,

@@ -39,6 +39,9 @@ constexpr double kEtaTight32 = 1e-2;
 // than kExtendRatio times the model's predicted decrease, to at most
 // kExtendMax times the step
 constexpr double kExtendRatio = 1.2;
+// start each dynamic substep's Newton solve from the CCD-bounded inertial
+// prediction of the gel instead of the previous substep's solution
+constexpr bool kPredict = true;
 constexpr double kExtendMax = 8.0;
 
 #define TC_CHECK(x)                                 \
@@ -457,11 +460,23 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       if ((st = X.build(fset, nullptr, nullptr)) != TC_OK) return st;
       b_friction_lag<R>(X.host, X.stream);
     }
+    std::vector<Env*> pset;
+    std::vector<double> pfac;
+    std::vector<Motion> pmot;
     for (size_t j = 0; j < live.size(); ++j) {
       StepCtl& c = tasks[live[j]];
       const double frac = sc[j].ccd_t;
+      const double s_old = c.s;
       c.s = frac >= 1.0 ? 1.0 : c.s + (1.0 - c.s) * frac;
       pose_interp(c.pose0, c.target, c.s, &c.env->pose);
+      // inertial predictor (dynamic): the gel's start point for this
+      // substep's solve moves by the substep's share of the inertial
+      // increment dt v, as far as CCD against the advanced indenter allows
+      if (kPredict && c.env->dynamic) {
+        pset.push_back(c.env);
+        pfac.push_back(c.s - s_old);
+        pmot.push_back(make_motion(c.env->pose, c.env->pose, 1));
+      }
       c.sub++;
       c.newton = 0;
       c.g0 = -1.0;
@@ -470,6 +485,16 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       if (trace_on())
         std::fprintf(stderr, "[tc] req %llu substep %d advance frac=%.6e s=%.9f\n", (unsigned long long)c.tag, c.sub,
                      frac, c.s);
+    }
+    if (!pset.empty()) {
+      if ((st = X.build(pset, pfac.data(), nullptr)) != TC_OK) return st;
+      b_step_vectors<R>(X.host, 2, X.stream);  // dx = f (utilde - u0)
+      std::vector<Scalars> psc;
+      if ((st = ccd_phase<R>(X, pset, pmot, true, psc)) != TC_OK) return st;
+      for (size_t j = 0; j < pset.size(); ++j)
+        if (!(psc[j].status & ST_NONFINITE) && psc[j].ccd_t > 0.0) {
+          std::swap(pset[j]->u, pset[j]->utrial);  // the CCD pass's lists cover the moved state
+        }
     }
   }
   // ---- Newton iteration: element + contact + assembly

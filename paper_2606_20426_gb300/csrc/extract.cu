@@ -12,10 +12,12 @@
 // The per-env kernels (k_traction, k_vertex_avg, k_splat, and k_stress in
 // elem.cu) serve the single-env calls.  k_extract does all of it for a whole
 // batch of envs in one cooperative launch: phase 1 streams sigma of every tet
-// and the face pressure and area of every contact face of every env; after a
-// grid-wide barrier, phase 2 forms every pixel of every map, each pixel
-// averaging its three vertices itself.  Each item goes through the same device
-// functions as in the per-env kernels, so the outputs are the same bit for bit.
+// and the face pressure and area of every contact face of every env, phase 2
+// averages to contact vertices, phase 3 splats to pixels, with a grid-wide
+// barrier between phases.  Each item goes through the same device functions
+// as in the per-env kernels, so the outputs are the same bit for bit.  (A
+// two-phase form in which every pixel averaged its three vertices itself was
+// measured slower: 45 us against 37 us for 8 bench envs.)
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -305,28 +307,21 @@ template <class R> __global__ void __launch_bounds__(kBlock) k_extract(const XBa
   }
   if (!with_map) return;
   if (!grid_barrier(xb.bar, xb.err)) return;
-  // phase 2: the pixel map (K10b), each pixel forming the area-weighted
-  // means (K10a) of its face's three contact vertices itself -- the same
-  // fixed-order sums as the per-vertex pass, so the same values, without a
-  // third phase and its barrier (the face values it reads stay in L2)
+  // phase 2: area-weighted means at the contact vertices (K10a)
+  const int64_t ncv = cv_off[n];
+  for (int64_t i = first; i < ncv; i += stride) {
+    const int e = env_of(cv_off, n, i);
+    const XEnv<R>& x = xb.env[e];
+    const int s = (int)(i - cv_off[e]);
+    x.vert_p[s] = vertex_mean(s, x.v.cv_face_off, x.v.cv_face_idx, x.face_p, x.face_A);
+  }
+  if (!grid_barrier(xb.bar, xb.err)) return;
+  // phase 3: the pixel map (K10b)
   const int64_t npx = pix_off[n];
   for (int64_t i = first; i < npx; i += stride) {
     const int e = env_of(pix_off, n, i);
     const XEnv<R>& x = xb.env[e];
-    const int p = (int)(i - pix_off[e]);
-    const int np_ = x.npix, nfc = x.v.nfc;
-    const int f = x.pix_face[p];
-    float v = 0.f;
-    if (f >= 0) {
-      const int32_t* off = x.v.cv_face_off;
-      const int32_t* idx = x.v.cv_face_idx;
-      v = bary(x.pix_w[p], x.pix_w[np_ + p], x.pix_w[2 * np_ + p],
-               vertex_mean(x.cface_slot[f], off, idx, x.face_p, x.face_A),
-               vertex_mean(x.cface_slot[nfc + f], off, idx, x.face_p, x.face_A),
-               vertex_mean(x.cface_slot[2 * nfc + f], off, idx, x.face_p, x.face_A));
-    }
-    x.map[p] = v;
-    if (x.mask) x.mask[p] = f >= 0 ? 1 : 0;
+    splat_pixel((int)(i - pix_off[e]), x.npix, x.pix_face, x.pix_w, x.cface_slot, x.v.nfc, x.vert_p, x.map, x.mask);
   }
 }
 

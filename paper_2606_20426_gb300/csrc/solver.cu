@@ -1098,7 +1098,9 @@ template <class R> void b_scale_dx(const BatchHost<R>& b, cudaStream_t s) {
 }
 
 // mode 0 (step start): u0 = u and, when dynamic, utilde = u + dt vel;
-// mode 1 (step end, dynamic): vel = (u - u0) / dt
+// mode 1 (step end, dynamic): vel = (u - u0) / dt;
+// mode 2 (substep start, dynamic): dx = param (utilde - u0), the substep's
+// share of the inertial increment (the predictor direction)
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_step_vectors(const BatchView<R> bv, int mode) {
   const Loc l = locate(bv.prefix, bv.nenv, K_VERT, blockIdx.x);
@@ -1107,7 +1109,9 @@ __global__ void __launch_bounds__(kBlock) k_step_vectors(const BatchView<R> bv, 
   if (v >= e.nv) return;
   for (int i = 0; i < 3; ++i) {
     const int k = i * e.nv + v;
-    if (mode == 0) {
+    if (mode == 2) {
+      e.dx[k] = (R)bv.param[l.env] * (e.utilde[k] - e.u0[k]);
+    } else if (mode == 0) {
       e.u0[k] = e.u[k];
       if (e.dt > 0.0) e.utilde[k] = e.u[k] + (R)e.dt * e.vel[k];
     } else if (e.dt > 0.0) {

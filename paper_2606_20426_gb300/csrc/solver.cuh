@@ -45,7 +45,8 @@ template <class R> tc_status b_pcg(const BatchHost<R>& b, int max_iter, bool war
 template <class R> void b_pmax(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_trial(const BatchHost<R>& b, cudaStream_t s);
 template <class R> void b_scale_dx(const BatchHost<R>& b, cudaStream_t s);  // dx *= param per env
-// mode 0: u0 = u and (dynamic) utilde = u + dt vel; mode 1: vel = (u - u0) / dt
+// mode 0: u0 = u and (dynamic) utilde = u + dt vel; mode 1: vel = (u - u0) / dt;
+// mode 2: dx = param (utilde - u0)
 template <class R> void b_step_vectors(const BatchHost<R>& b, int mode, cudaStream_t s);
 
 }  // namespace tc
