@@ -906,6 +906,38 @@ def run_configs(args):
     print(json.dumps(out), flush=True)
 
 
+def run_extract_probe(args):
+    """Profiling probe of the batched extraction: B bench envs take
+    `extract_probe` batched steps, then tc_extract_batch (sigma and the maps
+    of all B envs) runs 8 times with an L2 flush before each; prints the
+    per-launch time of k_extract from the library's event timing.  For ncu:
+    -k regex:k_extract -s 2 -c 1 captures the third launch."""
+    import torch
+    from paper_2606_20426_gb300 import Env, extract_batch, step_batch
+    cfgs = make_envs(args.envs, 0)
+    envs = [Env(c, precision="fp32") for c in cfgs]
+    for k in range(args.extract_probe):
+        codes = step_batch(envs, [c["bench_poses"][k] for c in cfgs])
+        if any(codes):
+            raise RuntimeError(f"tc_step_batch statuses {codes}")
+    outs = [(torch.empty((6, e.info["nt"]), device="cuda"), torch.empty((e.info["H"], e.info["W"]), device="cuda"),
+             torch.empty((e.info["H"], e.info["W"]), dtype=torch.uint8, device="cuda")) for e in envs]
+    flush = L2Flush(torch.device("cuda"))
+    envs[0].profile(True)
+    for r in range(8):
+        flush(r)
+        torch.cuda.synchronize()
+        extract_batch(envs, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    ms, n = envs[0].kernel_times()["k_extract"]
+    b = sum(algorithmic_bytes(k, e.info) for e in envs for k in ("k_stress", "k_traction", "k_vertex_avg", "k_splat"))
+    peak, _ = peaks()
+    us = ms / n * 1e3
+    print(json.dumps({"envs": args.envs, "steps": args.extract_probe, "k_extract_us": round(us, 2),
+                      "bytes_per_launch": int(b), "frac": round(b / (us / 1e6) / 1e9 / peak, 4)}), flush=True)
+    for e in envs:
+        e.close()
+
+
 def run_pcg_probe(args):
     """Profiling probe: B envs take `pcg_probe` batched steps, then one PCG
     solve per launch shape runs through the autotuner.  Prints how many PCG
@@ -953,6 +985,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pcg-probe", type=int, default=0,
                     help="profiling probe: this many batched steps, then the PCG autotuner (see run_pcg_probe)")
+    ap.add_argument("--extract-probe", type=int, default=0,
+                    help="profiling probe: this many batched steps, then timed tc_extract_batch calls")
     ap.add_argument("--configs", default="",
                     help="instead of the headline: measure the listed other configurations (c1,c3,c4,c5)")
     ap.add_argument("--c5-envs", type=int, default=1024)
@@ -960,6 +994,8 @@ def main():
     args = ap.parse_args()
     if args.configs:
         run_configs(args)
+    elif args.extract_probe:
+        run_extract_probe(args)
     elif args.pcg_probe:
         run_pcg_probe(args)
     elif args.impl == "reference":
