@@ -149,6 +149,8 @@ typedef struct {
   int64_t nnzb;              /* 3x3 blocks of the Newton matrix (free rows)  */
   int64_t pcg_capped;        /* PCG solves that stopped at pcg_max above     */
                              /* their tolerance (not an error, see TC_ERR_PCG_MAXITER) */
+  size_t working_bytes;      /* device bytes of the per-step working set      */
+  int32_t working_resident;  /* 1 while the working set is allocated          */
 } tc_info;
 
 /* Scene setup (row a0): rest shape Dm^-1 and volumes, lumped masses, boundary
@@ -381,12 +383,23 @@ tc_status tc_pressure_map_noalloc(const float* x, int32_t nv, const float* sigma
  * Not in the paper, which steps one env per call.  A server owns a pool of
  * worker threads, each with its own CUDA stream, on the device current at
  * creation.  tc_submit queues a request (env, target pose, optional output
- * buffers) and returns a ticket at once.  Before every scheduling round a
- * worker admits queued requests in FIFO order while it and the server have
- * free slots and the device footprint of the envs in flight (the memory each
- * env holds) stays within hbm_budget_bytes; a request waits while an earlier
- * request of the same env is in flight, and a lone request is always
- * admitted.  Each round advances every request of the worker by one phase
+ * buffers) and returns a ticket at once.  Device memory: an env's state is
+ * a persistent part (rest shape, topology, positions, velocities, PCG warm
+ * starts, pixel tables -- held from tc_create_scene to tc_destroy) and a
+ * working set that only a step needs (element stiffness blocks, Newton
+ * matrix values, gradient, PCG vectors, contact slots and candidate lists,
+ * about two thirds of the env's memory).  The server meters the working sets
+ * of the envs submitted to it against hbm_budget_bytes: a working set stays
+ * resident after its request (the next request of that env reuses it), and
+ * when a request needs room, the working sets of that server's envs with no
+ * request in flight are released, least recently used first (an env being
+ * used by a caller at that moment is skipped), and acquired again by their
+ * next call that needs them (results do not change).  Before every
+ * scheduling round a worker admits queued requests in FIFO order while it and
+ * the server have free slots and the request's working set fits the budget;
+ * a request waits while an earlier request of the same env is in flight, a
+ * lone request is always admitted, and a request whose env's working set
+ * alone exceeds the budget completes with TC_ERR_ADMISSION.  Each round advances every request of the worker by one phase
  * group of the implicit step (Algorithm 2, physics line) with one launch set
  * per phase over all of them, so requests that arrive while others are on the
  * GPU join at the next round boundary, and workers overlap on the device.
@@ -412,10 +425,14 @@ typedef struct {
 typedef struct {
   int64_t submitted, completed, rounds;
   int32_t queued, inflight, peak_inflight, max_slots, workers;
-  size_t inflight_bytes, budget_bytes;
+  size_t inflight_bytes;   /* working-set bytes resident for the server's envs */
+  size_t budget_bytes;
+  int64_t evictions;       /* working sets released to make room            */
+  int32_t known_envs;      /* envs whose working sets the server meters      */
 } tc_server_stats;
 
-/* hbm_budget_bytes > 0: bound on the summed footprint of the envs in flight;
+/* hbm_budget_bytes > 0: bound on the summed working sets resident for the
+ * server's envs (see above);
  * max_slots > 0: bound on the number of requests in flight; workers: worker
  * threads, each with its own CUDA stream and scheduler holding up to
  * ceil(max_slots / workers) requests (<= 0: one worker per slot, so every

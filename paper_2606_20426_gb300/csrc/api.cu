@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "batch.cuh"
@@ -51,6 +52,8 @@ template <class R> static tc_status make_exec(Env& env) {
 }
 
 template <class R> static tc_status do_step(Env& env, const tc_pose& target) {
+  const tc_status ws = acquire_working(env);
+  if (ws != TC_OK) return ws;
   std::vector<Env*> one{&env};
   std::vector<tc_pose> tg{target};
   std::vector<tc_status> res;
@@ -59,20 +62,22 @@ template <class R> static tc_status do_step(Env& env, const tc_pose& target) {
   return st != TC_OK ? st : res[0];
 }
 
-template <class R> static tc_status alloc_state(Env& env) {
+// Device state of an env in two parts.  The persistent part (positions,
+// velocities, the step's start and inertial target, the PCG warm starts, the
+// extraction scratch) lives as long as the env.  The working set -- the
+// buffers a step fills and consumes (element stiffness blocks and gradient
+// slots, the Newton matrix's values, gradient, block-Jacobi inverse, PCG
+// vectors, line-search trial, contact slots and candidate lists) -- can be
+// released between steps and acquired again; a step server does so to keep
+// the working sets it holds within its HBM budget.
+template <class R> static tc_status alloc_persistent(Env& env) {
   Arena& a = env.arena;
-  const int64_t nv = env.nv, nt = env.nt;
+  const int64_t nv = env.nv;
   auto A = [&](void** p, int64_t n) {
     *p = a.alloc<R>(n);
     return *p != nullptr;
   };
-  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.utrial, 3 * nv) && A(&env.kblk, kblk_size(nt)) &&
-            A(&env.eslot, 12 * nt) && A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) &&
-            A(&env.Minv, 6 * nv) &&
-            A(&env.dx, 3 * nv) && A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) &&
-            A(&env.p2, 3 * nv) && A(&env.dfirst, 3 * nv) &&
-            A(&env.cv_slot, 9 * (int64_t)std::max(env.nvc, 1)) && A(&env.ce_slot, 27 * (int64_t)std::max(env.nec, 1)) &&
-            A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1));
+  bool ok = A(&env.u, 3 * nv) && A(&env.ut, 3 * nv) && A(&env.dx, 3 * nv) && A(&env.dfirst, 3 * nv);
   if (ok && env.dynamic) ok = A(&env.vel, 3 * nv) && A(&env.utilde, 3 * nv);
   if (!ok) return TC_ERR_OOM;
   TC_CHECK(cudaMemsetAsync(env.u, 0, sizeof(R) * 3 * nv, env.stream));
@@ -82,13 +87,70 @@ template <class R> static tc_status alloc_state(Env& env) {
     TC_CHECK(cudaMemsetAsync(env.vel, 0, sizeof(R) * 3 * nv, env.stream));
     TC_CHECK(cudaMemsetAsync(env.utilde, 0, sizeof(R) * 3 * nv, env.stream));
   }
-  const tc_status sc0 = alloc_candidates(env, 32);
-  if (sc0 != TC_OK) return sc0;
   env.face_p = a.alloc<float>(std::max(env.nfc, 1));
   env.face_A = a.alloc<float>(std::max(env.nfc, 1));
   env.vert_p = a.alloc<float>(std::max(env.nvc, 1));
   if (!env.face_p || !env.face_A || !env.vert_p) return TC_ERR_OOM;
   return TC_OK;
+}
+
+template <class R> static tc_status alloc_working(Env& env) {
+  if (env.work_resident) return TC_OK;
+  Arena& a = env.arena;
+  const int64_t nv = env.nv, nt = env.nt;
+  const size_t before = a.bytes;
+  auto A = [&](void** p, int64_t n) {
+    *p = a.alloc<R>(n);
+    return *p != nullptr;
+  };
+  bool ok = A(&env.utrial, 3 * nv) && A(&env.kblk, kblk_size(nt)) && A(&env.eslot, 12 * nt) &&
+            A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) && A(&env.Minv, 6 * nv) &&
+            A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) && A(&env.p2, 3 * nv) &&
+            A(&env.cv_slot, 9 * (int64_t)std::max(env.nvc, 1)) && A(&env.ce_slot, 27 * (int64_t)std::max(env.nec, 1)) &&
+            A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1));
+  tc_status st = ok ? alloc_candidates(env, std::max(env.cand_cap, 32)) : TC_ERR_OOM;
+  if (st != TC_OK) {
+    release_working(env);
+    return st;
+  }
+  env.work_bytes = a.bytes - before;
+  env.work_resident = true;
+  return TC_OK;
+}
+
+// The API mutexes of several envs, taken in address order.
+struct EnvLocks {
+  std::vector<std::mutex*> m;
+  explicit EnvLocks(const std::vector<Env*>& envs) {
+    for (Env* e : envs) m.push_back(&e->api_mu);
+    std::sort(m.begin(), m.end());
+    for (std::mutex* x : m) x->lock();
+  }
+  ~EnvLocks() {
+    for (auto it = m.rbegin(); it != m.rend(); ++it) (*it)->unlock();
+  }
+};
+
+tc_status acquire_working(Env& env) {
+  return env.precision == TC_FP64 ? alloc_working<double>(env) : alloc_working<float>(env);
+}
+
+void release_working(Env& env) {
+  Arena& a = env.arena;
+  void** bufs[] = {&env.utrial, &env.kblk, &env.eslot, &env.bsr_val, &env.g,  &env.Minv,    &env.r,
+                   &env.z,      &env.p,    &env.q,     &env.p2,      &env.cv_slot, &env.ce_slot, &env.cf_slot};
+  for (void** b : bufs) {
+    a.put(*b);
+    *b = nullptr;
+  }
+  for (int k = 0; k < 3; ++k) {
+    a.put(env.cand[k]);
+    a.put(env.cand_n[k]);
+    env.cand[k] = nullptr;
+    env.cand_n[k] = nullptr;
+  }
+  env.cand_valid = false;
+  env.work_resident = false;
 }
 
 // Per-tet (mu, lam_hat) of a heterogeneous material (Eq. 1 per tet and the
@@ -123,6 +185,8 @@ template <class R> static tc_status initial_check(Env& env) {
 }
 
 template <class R> static tc_status contact_force(Env& env, double* out) {
+  const tc_status ws = acquire_working(env);
+  if (ws != TC_OK) return ws;
   const tc_status st = contact_force_at_state<R>(exec_of<R>(env), env, out);
   if (env.prof) env.prof->collect();
   return st;
@@ -197,7 +261,9 @@ static tc_status vertex_forces(Env& env, float* f, float* fn, float* ft, float* 
     if (gs != TC_OK) return gs;
   }
   double tot[3];
-  tc_status st = contact_force_at_state<R>(exec_of<R>(env), env, tot);
+  tc_status st = acquire_working(env);
+  if (st != TC_OK) return st;
+  st = contact_force_at_state<R>(exec_of<R>(env), env, tot);
   if (st != TC_OK) return st;
   if (map) {
     launch_vertex_forces<R>(env.view<R>(), nullptr, nullptr, nullptr, env.vert_p, env.stream);
@@ -353,7 +419,8 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   if (st == TC_OK) st = tc::setup_scene(env, mesh, fixed, nfixed, indenter, grid);
   if (st == TC_OK) st = tc::build_bsr(env, mesh->tets, fixed, nfixed);
   if (st == TC_OK)
-    st = env.precision == TC_FP64 ? tc::alloc_state<double>(env) : tc::alloc_state<float>(env);
+    st = env.precision == TC_FP64 ? tc::alloc_persistent<double>(env) : tc::alloc_persistent<float>(env);
+  if (st == TC_OK) st = tc::acquire_working(env);
   if (st == TC_OK && material->per_tet_E_nu)
     st = env.precision == TC_FP64 ? tc::upload_material<double>(env, material->per_tet_E_nu)
                                   : tc::upload_material<float>(env, material->per_tet_E_nu);
@@ -372,6 +439,7 @@ tc_status tc_step(tc_env* h, const tc_pose* target) {
   if (!h || !target) return TC_ERR_INVALID_ARG;
   if (!pose_ok(target)) return TC_ERR_NONFINITE;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (env.busy.load()) return TC_ERR_INVALID_ARG;  // a server holds a request of this env
   tc::ProfGuard pg(env);
   tc_status st = env.precision == TC_FP64 ? tc::do_step<double>(env, *target) : tc::do_step<float>(env, *target);
@@ -389,9 +457,16 @@ tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets, tc_sta
     for (int j = 0; j < i; ++j)
       if (envs[j] == envs[i]) return TC_ERR_INVALID_ARG;
   }
+  std::vector<Env*> all;
+  for (int i = 0; i < n; ++i) all.push_back(&envs[i]->impl);
+  tc::EnvLocks locks(all);
   std::vector<Env*> set;
   std::vector<tc_pose> tg;
   std::vector<int> idx;
+  for (int i = 0; i < n; ++i) {
+    const tc_status ws = tc::acquire_working(envs[i]->impl);
+    if (ws != TC_OK) return ws;
+  }
   for (int i = 0; i < n; ++i) {
     if (!pose_ok(&targets[i])) {
       statuses[i] = TC_ERR_NONFINITE;
@@ -437,6 +512,11 @@ tc_status tc_autotune_pcg(tc_env** envs, int32_t n, int32_t mode, tc_pcg_tune* r
       if (envs[j] == envs[i]) return TC_ERR_INVALID_ARG;
     set.push_back(&envs[i]->impl);
   }
+  tc::EnvLocks locks(set);
+  for (Env* e : set) {
+    const tc_status ws = tc::acquire_working(*e);
+    if (ws != TC_OK) return ws;
+  }
   Env& lead = *set[0];
   for (Env* e : set)
     if (e->stream != lead.stream) cudaStreamSynchronize(e->stream);
@@ -459,6 +539,7 @@ tc_status tc_autotune_pcg(tc_env** envs, int32_t n, int32_t mode, tc_pcg_tune* r
 tc_status tc_stress(tc_env* h, float* sigma_out) {
   if (!h || !sigma_out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   tc::ProfGuard pg(env);
   if (env.precision == TC_FP64) tc::launch_stress<double>(env.view<double>(), sigma_out, env.stream);
   else tc::launch_stress<float>(env.view<float>(), sigma_out, env.stream);
@@ -470,6 +551,7 @@ tc_status tc_stress(tc_env* h, float* sigma_out) {
 tc_status tc_traction(tc_env* h, float* t, float* p, float* t_tau) {
   if (!h) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   tc::ProfGuard pg(env);
   if (env.precision == TC_FP64)
     tc::launch_traction<double>(env.view<double>(), env.cparent, t, p, t_tau, nullptr, nullptr, env.stream);
@@ -482,6 +564,7 @@ tc_status tc_traction(tc_env* h, float* t, float* p, float* t_tau) {
 tc_status tc_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint8_t* mask) {
   if (!h || !out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::pressure_map<double>(env, grid, out, mask)
                                   : tc::pressure_map<float>(env, grid, out, mask);
@@ -507,6 +590,7 @@ tc_status tc_extract_batch(tc_env** envs, int32_t n, float* const* sigma_out, fl
     if (map[i] && e.H * e.W == 0) return TC_ERR_INVALID_ARG;
     set.push_back(&e);
   }
+  tc::EnvLocks locks(set);
   Env& lead = *set[0];
   for (Env* e : set)
     if (e->stream != lead.stream && cudaStreamSynchronize(e->stream) != cudaSuccess) return TC_ERR_CUDA;
@@ -520,6 +604,7 @@ tc_status tc_extract_batch(tc_env** envs, int32_t n, float* const* sigma_out, fl
 tc_status tc_contact_force(tc_env* h, double* out) {
   if (!h || !out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::contact_force<double>(env, out) : tc::contact_force<float>(env, out);
 }
@@ -527,6 +612,7 @@ tc_status tc_contact_force(tc_env* h, double* out) {
 tc_status tc_depth_map(tc_env* h, const tc_grid* grid, float* height, uint8_t* mask) {
   if (!h || !height) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (grid && !tc::grid_valid(grid)) return TC_ERR_INVALID_ARG;
   if (!grid && env.H * env.W == 0) return TC_ERR_INVALID_ARG;
   const tc_grid& g = grid ? *grid : env.grid0;
@@ -542,6 +628,7 @@ tc_status tc_depth_map(tc_env* h, const tc_grid* grid, float* height, uint8_t* m
 tc_status tc_vertex_forces(tc_env* h, float* f, float* f_n, float* f_tau, float* p) {
   if (!h) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (env.busy.load()) return TC_ERR_INVALID_ARG;
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::vertex_forces<double>(env, f, f_n, f_tau, p, nullptr, false, nullptr, nullptr)
@@ -551,6 +638,7 @@ tc_status tc_vertex_forces(tc_env* h, float* f, float* f_n, float* f_tau, float*
 tc_status tc_force_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint8_t* mask) {
   if (!h || !out) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (env.busy.load()) return TC_ERR_INVALID_ARG;
   tc::ProfGuard pg(env);
   return env.precision == TC_FP64 ? tc::vertex_forces<double>(env, nullptr, nullptr, nullptr, nullptr, grid, true, out, mask)
@@ -560,8 +648,11 @@ tc_status tc_force_pressure_map(tc_env* h, const tc_grid* grid, float* out, uint
 tc_status tc_energy_gradient(tc_env* h, double* energy, double* grad) {
   if (!h || (!energy && !grad)) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (env.busy.load()) return TC_ERR_INVALID_ARG;
   tc::ProfGuard pg(env);
+  const tc_status ws = tc::acquire_working(env);
+  if (ws != TC_OK) return ws;
   const tc_status st = env.precision == TC_FP64
                            ? tc::energy_gradient_at_state<double>(tc::exec_of<double>(env), env, energy, grad)
                            : tc::energy_gradient_at_state<float>(tc::exec_of<float>(env), env, energy, grad);
@@ -596,12 +687,14 @@ tc_status tc_pixel_table(tc_env* h, int32_t* pix_face, float* pix_w) {
 tc_status tc_get_positions(tc_env* h, double* x) {
   if (!h || !x) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   return env.precision == TC_FP64 ? tc::get_positions<double>(env, x) : tc::get_positions<float>(env, x);
 }
 
 tc_status tc_set_positions(tc_env* h, const double* x) {
   if (!h || !x) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   if (env.busy.load()) return TC_ERR_INVALID_ARG;
   return env.precision == TC_FP64 ? tc::set_positions<double>(env, x) : tc::set_positions<float>(env, x);
 }
@@ -609,6 +702,7 @@ tc_status tc_set_positions(tc_env* h, const double* x) {
 tc_status tc_env_info(tc_env* h, tc_info* info) {
   if (!h || !info) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   info->nv = env.nv;
   info->nt = env.nt;
   info->nf = env.nf;
@@ -629,12 +723,15 @@ tc_status tc_env_info(tc_env* h, tc_info* info) {
   info->device_bytes = env.arena.bytes;
   info->nnzb = env.nnzb;
   info->pcg_capped = env.stats.pcg_capped;
+  info->working_bytes = env.work_bytes;
+  info->working_resident = env.work_resident ? 1 : 0;
   return TC_OK;
 }
 
 tc_status tc_profile_enable(tc_env* h, int32_t on) {
   if (!h) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   cudaStreamSynchronize(env.stream);
   if (on) {
     if (!env.prof) env.prof = new (std::nothrow) tc::Profiler();
@@ -651,6 +748,7 @@ tc_status tc_profile_enable(tc_env* h, int32_t on) {
 tc_status tc_profile_read(tc_env* h, tc_kernel_time* out, int32_t max, int32_t* n) {
   if (!h || !n || (max > 0 && !out)) return TC_ERR_INVALID_ARG;
   Env& env = h->impl;
+  std::lock_guard<std::mutex> api_lock(env.api_mu);
   *n = 0;
   if (!env.prof) return TC_OK;
   cudaStreamSynchronize(env.stream);
@@ -669,6 +767,7 @@ tc_status tc_profile_read(tc_env* h, tc_kernel_time* out, int32_t max, int32_t* 
 void tc_destroy(tc_env* h) {
   if (!h) return;
   Env& env = h->impl;
+  tc::server_forget(env);  // a server that meters this env's working set lets go of it first
   cudaStreamSynchronize(env.stream);
   delete env.prof;
   env.prof = nullptr;

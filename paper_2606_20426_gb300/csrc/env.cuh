@@ -15,6 +15,7 @@
 #pragma once
 #include <atomic>
 #include <cuda_runtime.h>
+#include <mutex>
 #include <stdint.h>
 
 #include <vector>
@@ -296,6 +297,12 @@ struct Env {
   int last_status = TC_OK;
   Profiler* prof = nullptr;  // per-kernel timing, null unless enabled
   void* exec = nullptr;      // BatchExec<R> of this env (batches of one)
+  // working set (see acquire_working): resident or released, and its size
+  bool work_resident = false;
+  size_t work_bytes = 0;
+  std::mutex api_mu;             // held by every public call on the env (and by a server releasing its working set)
+  void* server = nullptr;        // the step server that meters this env's working set, if any
+  uint64_t server_tick = 0;      // its last use by that server (least recently used first out)
   std::atomic<int> busy{0};      // step requests of this env queued or in flight on a server
   std::atomic<int> in_flight{0}; // 1 while one of them is admitted
 
@@ -349,6 +356,14 @@ template <class R> EnvView<R> Env::view() const {
 
 tc_status setup_scene(Env& env, const tc_mesh* mesh, const int32_t* fixed, int32_t nfixed,
                       const tc_trimesh* ind, const tc_grid* grid);
+// The per-step working buffers of an env (element blocks and slots, Newton
+// matrix values, gradient, block-Jacobi inverse, PCG vectors, line-search
+// trial, contact slots, candidate lists): allocated if released (no-op when
+// resident), and released.  Release only when no work of the env is pending.
+tc_status acquire_working(Env& env);
+void release_working(Env& env);
+// A step server that meters the env's working set stops doing so (env destroyed).
+void server_forget(Env& env);
 // Pixel binning of a sensor grid over the env's rest contact surface
 // (device tables allocated from the env's arena); grid checks.
 tc_status bin_pixel_grid(Env& env, const tc_grid* grid, int32_t** pix_face, float** pix_w);

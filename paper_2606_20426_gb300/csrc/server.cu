@@ -77,7 +77,12 @@ struct Server {
   std::deque<uint64_t> queue;
   std::unordered_map<uint64_t, Req> reqs;  // node-based: element addresses are stable
   int inflight = 0, peak_inflight = 0;
-  size_t inflight_bytes = 0;
+  // working sets metered against the budget: every env ever submitted here
+  // (until destroyed) and the bytes of those whose working set is resident
+  std::vector<Env*> known;
+  size_t inflight_bytes = 0;  // resident working-set bytes of the known envs
+  uint64_t tick = 0;
+  int64_t evictions = 0;
   int64_t submitted = 0, completed = 0;
   uint64_t gen = 0;  // bumped whenever a request arrives or capacity frees up
   std::atomic<int64_t> rounds{0};
@@ -87,7 +92,41 @@ struct Server {
 
   void admit_locked(Worker& w, std::vector<Req*>& out);
   void complete_locked(Req& r, tc_status st);
+  void make_room_locked(size_t need, const Env* keep);
+  void forget_locked(Env* e);
 };
+
+void Server::forget_locked(Env* e) {
+  for (size_t i = 0; i < known.size(); ++i)
+    if (known[i] == e) {
+      if (e->work_resident) inflight_bytes -= std::min(inflight_bytes, e->work_bytes);
+      known[i] = known.back();
+      known.pop_back();
+      break;
+    }
+  e->server = nullptr;
+}
+
+// Release the working sets of known envs with no request in flight, least
+// recently used first, until `need` more bytes fit the budget.  An env whose
+// API lock is held by a caller right now is skipped.
+void Server::make_room_locked(size_t need, const Env* keep) {
+  std::vector<Env*> cand;
+  for (Env* e : known)
+    if (e != keep && e->work_resident && !e->in_flight.load()) cand.push_back(e);
+  std::sort(cand.begin(), cand.end(), [](const Env* a, const Env* b) { return a->server_tick < b->server_tick; });
+  for (Env* e : cand) {
+    if (inflight_bytes + need <= budget) break;
+    if (!e->api_mu.try_lock()) continue;
+    if (e->work_resident && !e->in_flight.load()) {
+      cudaStreamSynchronize(e->stream);
+      release_working(*e);
+      inflight_bytes -= std::min(inflight_bytes, e->work_bytes);
+      evictions++;
+    }
+    e->api_mu.unlock();
+  }
+}
 
 void Server::complete_locked(Req& r, tc_status st) {
   r.status = st;
@@ -107,16 +146,24 @@ void Server::admit_locked(Worker& w, std::vector<Req*>& out) {
       ++it;
       continue;
     }
-    r.bytes = r.env->arena.bytes;
-    if (r.bytes > budget) {  // can never fit
+    Env* e = r.env;
+    if (e->server != this && e->server == nullptr) {  // first request of this env: meter its working set
+      e->server = this;
+      known.push_back(e);
+      if (e->work_resident) inflight_bytes += e->work_bytes;
+    }
+    r.bytes = e->work_resident ? 0 : e->work_bytes;
+    if (e->work_bytes > budget) {  // can never fit
       complete_locked(r, TC_ERR_ADMISSION);
       r.env->busy.fetch_sub(1);
       it = queue.erase(it);
       continue;
     }
     if (w.inflight >= slots_per_worker) break;
+    if (inflight_bytes + r.bytes > budget) make_room_locked(r.bytes, e);
     const bool fits = inflight < max_slots && inflight_bytes + r.bytes <= budget;
     if (!fits && inflight > 0) break;
+    e->server_tick = ++tick;
     r.state = 1;
     r.t_admit = Clock::now();
     r.env->in_flight.store(1);
@@ -165,7 +212,18 @@ void Worker::run() {
     S.cv_done.notify_all();  // admission may have completed requests that can never fit
     // the env's earlier work (creation, extraction by the caller) is ordered
     // before its first launch on this worker's stream
+    std::vector<std::pair<Req*, tc_status>> refused;
     for (Req* r : admitted) {
+      // the working set of the env (released earlier to make room for others)
+      tc_status ws;
+      {
+        std::lock_guard<std::mutex> g(r->env->api_mu);
+        ws = acquire_working(*r->env);
+      }
+      if (ws != TC_OK) {
+        refused.push_back({r, ws});
+        continue;
+      }
       if (r->env->stream != stream) cudaStreamSynchronize(r->env->stream);
       if (r->env->precision == TC_FP64) s64.admit(r->env, r->target, r->ticket);
       else s32.admit(r->env, r->target, r->ticket);
@@ -182,7 +240,7 @@ void Worker::run() {
                    std::chrono::duration<double, std::milli>(Clock::now() - t_round).count());
     for (Req* r : live) r->rounds++;
     S.rounds++;
-    std::vector<std::pair<Req*, tc_status>> done;
+    std::vector<std::pair<Req*, tc_status>> done(refused);
     if (st != TC_OK) {
       // a launch or copy failed: every request this worker holds ends with that status
       s32.tasks.clear();
@@ -218,10 +276,13 @@ void Worker::run() {
         r.env->busy.fetch_sub(1);
         S.inflight--;
         inflight--;
-        S.inflight_bytes -= r.bytes;
+        // the working set stays resident (metered) until the server needs
+        // the room for another env; one that could not be acquired is not
+        if (!r.env->work_resident) S.inflight_bytes -= std::min(S.inflight_bytes, r.bytes);
       }
       S.gen++;
     }
+    if (!refused.empty()) S.cv_done.notify_all();
     std::vector<Req*> keep;
     for (Req* r : live) {
       bool fin_r = false;
@@ -232,6 +293,13 @@ void Worker::run() {
     S.cv_done.notify_all();
     S.cv_work.notify_all();  // freed capacity may let an idle worker admit
   }
+}
+
+void server_forget(Env& env) {
+  Server* s = static_cast<Server*>(env.server);
+  if (!s) return;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->forget_locked(&env);
 }
 
 }  // namespace tc
@@ -404,6 +472,8 @@ tc_status tc_server_info(tc_server* h, tc_server_stats* out) {
   out->workers = (int32_t)s.workers.size();
   out->inflight_bytes = s.inflight_bytes;
   out->budget_bytes = s.budget;
+  out->evictions = s.evictions;
+  out->known_envs = (int32_t)s.known.size();
   return TC_OK;
 }
 
@@ -429,6 +499,11 @@ void tc_server_destroy(tc_server* h) {
     s.queue.clear();
   }
   stop_workers(s);
+  {
+    std::lock_guard<std::mutex> lk(s.mu);
+    for (tc::Env* e : s.known) e->server = nullptr;  // their working sets stay as they are
+    s.known.clear();
+  }
   delete h;
 }
 

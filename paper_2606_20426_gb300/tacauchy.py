@@ -86,7 +86,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("rounds", ctypes.c_int64),
                 ("queued", ctypes.c_int32), ("inflight", ctypes.c_int32), ("peak_inflight", ctypes.c_int32),
                 ("max_slots", ctypes.c_int32), ("workers", ctypes.c_int32), ("inflight_bytes", ctypes.c_size_t),
-                ("budget_bytes", ctypes.c_size_t)]
+                ("budget_bytes", ctypes.c_size_t), ("evictions", ctypes.c_int64), ("known_envs", ctypes.c_int32)]
 
 
 class PcgTune(ctypes.Structure):
@@ -101,7 +101,8 @@ class Info(ctypes.Structure):
                 ("W", ctypes.c_int32), ("newton_iters", ctypes.c_int64), ("pcg_iters", ctypes.c_int64),
                 ("substeps", ctypes.c_int64), ("steps", ctypes.c_int64), ("line_search_halvings", ctypes.c_int64),
                 ("kappa", ctypes.c_double), ("device_bytes", ctypes.c_size_t), ("nnzb", ctypes.c_int64),
-                ("pcg_capped", ctypes.c_int64)]
+                ("pcg_capped", ctypes.c_int64), ("working_bytes", ctypes.c_size_t),
+                ("working_resident", ctypes.c_int32)]
 
 
 _lib = None

@@ -130,3 +130,43 @@ def test_pending_env_refused_and_wait_timeout():
     srv.close()
     g.step(s["poses"][1])  # the env is free again
     g.close()
+
+
+def test_budget_meters_working_sets_and_evicts_idle_ones():
+    """A budget that holds the working sets of two of four envs: requests of
+    all four (round robin, three steps each) complete with the results of
+    the same envs stepped alone, bit for bit; the server released idle
+    working sets to make room (evictions > 0), never holds more than the
+    budget once the requests are done, and an evicted env steps again on its
+    own (its working set comes back)."""
+    from paper_2606_20426_gb300 import Env, Server
+    cfgs = [workloads.small_env(s, steps=3) for s in (0, 1, 2, 3)]
+    alone = [Env(c) for c in cfgs]
+    served = [Env(c) for c in cfgs]
+    wb = served[0].get_info()["working_bytes"]
+    assert wb > 0 and all(e.get_info()["working_resident"] == 1 for e in served)
+    budget = int(2.5 * max(e.get_info()["working_bytes"] for e in served))
+    srv = Server(hbm_budget_bytes=budget, max_slots=2, workers=2)
+    for k in range(3):
+        tickets = [srv.submit(e, c["poses"][k]) for e, c in zip(served, cfgs)]
+        for t in tickets:
+            r = srv.wait(t, 120.0)
+            assert r is not None and r["status"] == 0
+        for e, c in zip(alone, cfgs):
+            e.step(c["poses"][k])
+    st = srv.info()
+    assert st["evictions"] > 0 and st["known_envs"] == 4
+    assert st["inflight_bytes"] <= budget
+    resident = sum(e.get_info()["working_resident"] for e in served)
+    assert 1 <= resident <= 2
+    for a, b in zip(alone, served):
+        assert np.array_equal(a.positions(), b.positions())
+    # an evicted env is used directly again
+    idle = [e for e in served if e.get_info()["working_resident"] == 0][0]
+    idle.step(cfgs[served.index(idle)]["poses"][2])
+    assert idle.get_info()["working_resident"] == 1
+    served[3].close()
+    assert srv.info()["known_envs"] == 3
+    srv.close()
+    for e in alone + served[:3]:
+        e.close()
