@@ -604,10 +604,10 @@ template <class R> tc_status StepScheduler<R>::round(std::vector<StepDone>& fini
       // converged: full step below ptol, or below 10 ptol with a predicted
       // decrease under the energy's rounding level -- take it without the
       // energy test
-      // (only the substep that ends the step is verified: the state a
-      // frictionless step ends in is the minimiser of the last substep's
-      // potential, whatever the earlier substeps left)
-      const bool loose = e.precision != TC_FP64 && !c.tight && c.s >= 1.0;
+      // (every substep is verified: an unverified intermediate substep can
+      // leave a close pair on the far side of the barrier's basin, from
+      // which the next substep's minimiser differs)
+      const bool loose = e.precision != TC_FP64 && !c.tight;
       if (pmax <= e.ptol || (pmax <= 10.0 * e.ptol && decrement <= e_noise)) {
         if (nonfinite) {
           fail(c, TC_ERR_NONFINITE);
