@@ -104,7 +104,7 @@ template <class R> static tc_status alloc_working(Env& env) {
     return *p != nullptr;
   };
   bool ok = A(&env.utrial, 3 * nv) && A(&env.kblk, kblk_size(nt)) && A(&env.eslot, 12 * nt) &&
-            A(&env.bsr_val, 9 * (int64_t)std::max(env.nnzb, 1)) && A(&env.g, 3 * nv) && A(&env.Minv, 6 * nv) &&
+            A(&env.bsr_val, 9 * (int64_t)std::max(env.nsell, 1)) && A(&env.g, 3 * nv) && A(&env.Minv, 6 * nv) &&
             A(&env.r, 3 * nv) && A(&env.z, 3 * nv) && A(&env.p, 3 * nv) && A(&env.q, 3 * nv) && A(&env.p2, 3 * nv) &&
             A(&env.cv_slot, 9 * (int64_t)std::max(env.nvc, 1)) && A(&env.ce_slot, 27 * (int64_t)std::max(env.nec, 1)) &&
             A(&env.cf_slot, 54 * (int64_t)std::max(env.nfc, 1));

@@ -122,7 +122,20 @@ template <class R> struct EnvView {
   const int32_t* be_idx;      //   tet*16 + a*4 + b (corner a's row, corner b's column)
   const int32_t* bc_off;      // nnzb + 1: contact contributions of each block
   const int32_t* bc_idx;      //   kind<<30 | a<<28 | b<<26 | primitive
-  R* bsr_val;                 // 9 x nnzb block entries (entry r*3+c of block k at (r*3+c)*nnzb + k)
+  // The block entries are stored sliced (SELL-32): the free rows (non-empty
+  // rows, ascending) form slices of 32; slice s owns slots
+  // [sell_off[s], sell_off[s + 1]), 32 per block position, so block kk of
+  // the row with free index f sits in slot sell_off[f / 32] + 32 kk + f % 32
+  // (a slice is as wide as its longest row; shorter rows leave their tail
+  // slots unused).  A warp reading block kk of 32 consecutive rows reads 32
+  // consecutive slots.
+  int nfree;                  // free rows
+  int nsell;                  // slots (>= nnzb)
+  const int32_t* free_v;      // nfree: vertex of each free row, ascending
+  const int32_t* free_of;     // nv: free index of each vertex, -1 for an empty row
+  const int32_t* sell_off;    // nfree / 32 (rounded up) + 1 slot offsets
+  const int32_t* sell_ci;     // nsell column vertex ids (unused slots: the row itself)
+  R* bsr_val;                 // 9 x nsell block entries (entry r*3+c of slot t at (r*3+c)*nsell + t)
   // indenter (body frame)
   const double* IV;           // 3 x ind_nv SoA
   const float* IVhi;          // IV as FP32 hi + lo pairs (hi = fl(IV), lo = fl(IV - hi))
@@ -273,8 +286,9 @@ struct Env {
   void* mass = nullptr;
   void *u = nullptr, *ut = nullptr, *vel = nullptr, *utilde = nullptr;
   void *eslot = nullptr, *kblk = nullptr, *bsr_val = nullptr;
-  int nnzb = 0;
+  int nnzb = 0, nfree = 0, nsell = 0;
   int32_t *bsr_rp = nullptr, *bsr_ci = nullptr, *bsr_diag = nullptr;
+  int32_t *free_v = nullptr, *free_of = nullptr, *sell_off = nullptr, *sell_ci = nullptr;
   int32_t *be_off = nullptr, *be_idx = nullptr, *bc_off = nullptr, *bc_idx = nullptr;
   void *g = nullptr, *Minv = nullptr, *dx = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   void* p2 = nullptr;
@@ -325,6 +339,8 @@ template <class R> EnvView<R> Env::view() const {
   e.tets = tets; e.X0 = X0; e.X0f = X0f; e.fixed = fixed; e.vt_off = vt_off; e.vt_idx = vt_idx;
   e.Dminv = (const R*)Dminv; e.vol = (const R*)vol; e.eslot = (R*)eslot; e.kblk = (R*)kblk;
   e.nnzb = nnzb; e.bsr_rp = bsr_rp; e.bsr_ci = bsr_ci; e.bsr_diag = bsr_diag; e.bsr_val = (R*)bsr_val;
+  e.nfree = nfree; e.nsell = nsell; e.free_v = free_v; e.free_of = free_of; e.sell_off = sell_off;
+  e.sell_ci = sell_ci;
   e.be_off = be_off; e.be_idx = be_idx; e.bc_off = bc_off; e.bc_idx = bc_idx;
   e.mass = (const R*)mass; e.u = (R*)u; e.ut = (R*)utrial; e.utilde = (R*)utilde; e.g = (R*)g; e.Minv = (R*)Minv;
   e.u0 = (R*)ut; e.vel = (R*)vel; e.dt = dynamic ? dt : 0.0;

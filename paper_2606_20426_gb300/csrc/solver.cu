@@ -1,5 +1,5 @@
 // Newton-step kernels over a batch of envs: per-vertex assembly (K4),
-// matrix-free block-Jacobi PCG (K5), energies for the line search (K7) and
+// block-Jacobi PCG on the assembled block-sparse matrix (K5), energies for the line search (K7) and
 // step updates.
 //
 // Assembly is atomic-free: element and contact passes write their
@@ -88,6 +88,11 @@ template <class R> TC_D void add_contact_block(const EnvView<R>& e, uint32_t cod
     for (int c = 0; c < 3; ++c) B[3 * r + c] += slot[(int64_t)(N + sym_index(3 * a + r, 3 * b + c, N)) * n + prim];
 }
 
+// slot of block kk of the row with free index f (sliced layout, EnvView::bsr_val)
+template <class R> TC_D int64_t sell_slot(const EnvView<R>& e, int f, int kk) {
+  return (int64_t)e.sell_off[f >> 5] + 32 * kk + (f & 31);
+}
+
 template <class R>
 __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, PartLayout L) {
   const Loc l = locate(bv.prefix, bv.nenv, K_VGRP, blockIdx.x);
@@ -120,7 +125,8 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, Part
     }
     // the matrix row (empty for a fixed vertex)
     const R mh = e.mass ? e.mass[v] * e.inv_h2 : R(0);
-    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
+    const int k0 = e.bsr_rp[v], fr = e.free_of[v];
+    for (int k = k0 + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
       R B[9];
       for (int q = 0; q < 9; ++q) B[q] = R(0);
       for (int c = e.be_off[k]; c < e.be_off[k + 1]; ++c) {
@@ -165,8 +171,9 @@ __global__ void __launch_bounds__(kBlock) k_assemble(const BatchView<R> bv, Part
           finite = finite && isfinite((double)M[i]);
         }
       }
+      const int64_t t = sell_slot(e, fr, k - k0);
       for (int q = 0; q < 9; ++q) {
-        e.bsr_val[(int64_t)q * e.nnzb + k] = B[q];
+        e.bsr_val[(int64_t)q * e.nsell + t] = B[q];
         finite = finite && isfinite((double)B[q]);
       }
     }
@@ -290,18 +297,20 @@ __global__ void __launch_bounds__(kBlock) k_pcg_warm(const BatchView<R> bv, Part
   const int lane = threadIdx.x & (kLanes - 1);
   const int v = l.chunk * 32 + threadIdx.x / kLanes;
   const int nv = e.nv;
-  const int64_t nb = e.nnzb;
+  const int64_t nb = e.nsell;
   double gd = 0.0, dq = 0.0;
   R a[3] = {0, 0, 0};
-  if (v < nv)
-    for (int k = e.bsr_rp[v] + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
+  if (v < nv) {
+    const int k0 = e.bsr_rp[v], fr = e.free_of[v];
+    for (int k = k0 + lane; k < e.bsr_rp[v + 1]; k += kLanes) {
       const int j = e.bsr_ci[k];
       const R d0 = e.wd[j], d1 = e.wd[nv + j], d2 = e.wd[2 * nv + j];
-      const R* B = e.bsr_val + k;
+      const R* B = e.bsr_val + sell_slot(e, fr, k - k0);
       a[0] += B[0] * d0 + B[nb] * d1 + B[2 * nb] * d2;
       a[1] += B[3 * nb] * d0 + B[4 * nb] * d1 + B[5 * nb] * d2;
       a[2] += B[6 * nb] * d0 + B[7 * nb] * d1 + B[8 * nb] * d2;
     }
+  }
   for (int i = 0; i < 3; ++i) a[i] = group_sum(a[i]);
   if (v < nv && lane == 0)
     for (int i = 0; i < 3; ++i) {
@@ -390,45 +399,42 @@ __global__ void __launch_bounds__(kBlock) k_pcg_init_env(const BatchView<R> bv, 
 // ------------------------------------------------- PCG, one cluster per env
 // Every env of the batch runs all of its CG iterations in one thread-block
 // cluster (16 CTAs where the GPU co-schedules them, else 8; 1024 threads
-// each) over a contiguous share of the env's rows, so envs iterate
-// independently: an env that converges frees its SMs at once, and no
-// grid-wide barrier ties envs together.  The rows are split so that every
-// CTA holds about the same number of matrix blocks.  Per iteration, two
-// cluster barriers:
+// each) over a contiguous share of the env's matrix slices (32 free rows
+// each, split so that every CTA holds about the same number of block
+// slots), so envs iterate independently: an env that converges frees its
+// SMs at once, and no grid-wide barrier ties envs together.  Per
+// iteration, two cluster barriers:
 //   S  p = z + beta p over the CTA's halo (the columns its rows touch),
 //      staged in shared memory; the CTA's own rows also go to the next p
 //      buffer in HBM (two buffers alternate, so no CTA overwrites values
 //      another may still read)
-//   A  q = A p, one thread per 3x3 block into a shared buffer, then one
-//      thread per row adds its blocks in order; p.q                 | barrier
+//   A  q = A p, one lane per row of a slice, summing the row's blocks in
+//      column order in registers; p.q                             | barrier
 //   B  alpha = r.z / p.q, dx += alpha p, r -= alpha q, z = M^-1 r;
 //      r.z, r.r                                                     | barrier
-// Resident mode (the usual case): when the halo, the CTA's block products
-// and its free rows' r, z, dx, q and M^-1 all fit in shared memory, those
+// Resident mode (the usual case): when the halo, a staging copy of it and
+// the CTA's rows' r, z, dx, q and M^-1 all fit in shared memory, those
 // vectors stay there for the whole solve and only z and p are published to
-// HBM for the neighbours' halos; rows of fixed vertices (empty rows) are
-// skipped through a list of the free rows.  Otherwise every vector lives in
-// HBM and the rows are walked in chunks that fit the product buffer.
-// Dot products accumulate in double-float pairs (FP64 issues at a small
-// fraction of the FP32 rate on this part) with fixed reduction trees; each
-// CTA pushes its partials into a slot of every CTA's shared memory before
-// the cluster barrier, and every CTA adds the slots of all ranks in the same
-// order, so all derive bit-identical alpha, beta and stop decisions (the
-// quotients are taken in float from the double-float sums with one residual
-// correction, so no FP64 division sits on the critical path).  When
-// the halo does not fit the shared-memory budget the SpMV forms p = z + beta
-// p of the neighbours from HBM instead.  Results do not depend on the other
-// envs.
-constexpr int kPcgMaxChunks = 256;
+// HBM for the neighbours' halos.  Otherwise every vector lives in HBM (and
+// when even the halo does not fit, the SpMV forms p = z + beta p of each
+// column from HBM).  Dot products accumulate in double-float pairs (FP64
+// issues at a small fraction of the FP32 rate on this part) with fixed
+// reduction trees; each CTA pushes its partials into a slot of every CTA's
+// shared memory before the cluster barrier, and every CTA adds the slots of
+// all ranks in the same order, so all derive bit-identical alpha, beta and
+// stop decisions (the quotients are taken in float from the double-float
+// sums with one residual correction, so no FP64 division sits on the
+// critical path).  Results do not depend on the other envs.
 constexpr int kPcgMaxCluster = 16;
-// blocks per thread and pass of the SpMV: all their loads are issued before
-// the first product, so a pass waits on L2 once
-template <class R> constexpr int kPcgUnroll = sizeof(R) == 4 ? 2 : 1;
+// blocks per lane and round of the SpMV: all their loads are issued before
+// the first product, so a round waits on L2 once
+template <class R> constexpr int kPcgUnroll = sizeof(R) == 4 ? 3 : 2;
 
-// Rows [r0, r1) of cluster rank `rank`: rank k starts at the first row r
-// whose block offset rp[r] reaches k nnzb / CS, so every rank holds about the
-// same number of blocks and fixed vertices (empty rows) cost nothing.  Rank
-// 0 starts at row 0 and the last rank ends at row nv.  Two rounds of
+// Items [r0, r1) of cluster rank `rank` out of nv items with offsets rp
+// (rp[nv] in total): rank k starts at the first item r whose offset rp[r]
+// reaches k rp[nv] / CS, so every rank holds about the same share.  Rank 0
+// starts at item 0 and the last rank ends at item nv.  (The PCG splits the
+// matrix slices by their slot offsets.)  Two rounds of
 // parallel search over the row pointers; s_w holds 4 ints of scratch.
 template <int NT>
 TC_D void pcg_rows(const int32_t* __restrict__ rp, int nv, int CS, int rank, int* s_w, int& r0, int& r1) {
@@ -506,17 +512,15 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     k_pcg_cluster(const BatchView<R> bv, PartLayout L, int max_iter, int smem_bytes) {
   using A = Acc<R>;
   using AT = typename A::T;
+  constexpr int NW = kPcgThreads / 32;
+  constexpr int U = kPcgUnroll<R>;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   __shared__ AT s_red[3][32];
   __shared__ AT s_all[kPcgMaxCluster][3];  // [rank][0 p.q, 1 r.z, 2 r.r]
   __shared__ R s_coef;
   __shared__ int s_flag;
-  __shared__ int s_chunk[kPcgMaxChunks + 1];
-  __shared__ int s_nchunk;
   __shared__ int s_lohi[2];
   __shared__ int s_rows[4];
-  __shared__ int s_nfree;
-  __shared__ int s_wcnt[32];
   __shared__ AT s_at[2];      // r.z, p.q (thread 0)
   __shared__ double s_sc[2];  // r.r, squared tolerance (thread 0)
   cg::cluster_group cluster = cg::this_cluster();
@@ -525,10 +529,13 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   const int env = blockIdx.x / CS;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const EnvView<R>& ev = bv.views[env];
-  const int nv = ev.nv;
-  const int64_t nb = ev.nnzb;
+  const int nv = ev.nv, nfree = ev.nfree, nsl = (nfree + 31) >> 5;
+  const int64_t ns = ev.nsell;
   const int32_t* __restrict__ rp = ev.bsr_rp;
   const int32_t* __restrict__ ci = ev.bsr_ci;
+  const int32_t* __restrict__ soff = ev.sell_off;
+  const int32_t* __restrict__ sci = ev.sell_ci;
+  const int32_t* __restrict__ fv = ev.free_v;
   const R* __restrict__ val = ev.bsr_val;
   const R* __restrict__ Minv = ev.Minv;
   R* q = ev.q;
@@ -536,102 +543,51 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
   R* z = ev.z;
   R* dx = ev.dx;
   R* pbuf[2] = {ev.p, ev.p2};
-  int r0, r1;
-  pcg_rows<kPcgThreads>(rp, nv, CS, rank, s_rows, r0, r1);
-  // halo of the CTA's rows (columns within a row ascend, so its first and
-  // last blocks bound it) and its number of free rows
+  // the rank's slices [s0, s1), its free rows [f0, f1) and their vertex
+  // range [r0, r1) (the free rows between r0 and r1 are exactly its rows)
+  int s0, s1;
+  pcg_rows<kPcgThreads>(soff, nsl, CS, rank, s_rows, s0, s1);
+  const int f0 = min(32 * s0, nfree), f1 = min(32 * s1, nfree), nf = f1 - f0;
+  const int r0 = nf > 0 ? fv[f0] : 0, r1 = nf > 0 ? fv[f1 - 1] + 1 : 0;
+  // halo of the rows (columns within a row ascend, so its first and last
+  // blocks bound it)
   if (threadIdx.x == 0) {
     s_lohi[0] = r0;
     s_lohi[1] = r1 - 1;
-    s_nfree = 0;
   }
   __syncthreads();
-  {
-    int lo = r0, hi = r1 - 1, nfl = 0;
-    for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
-      const int ka = rp[v], kb = rp[v + 1];
-      if (kb > ka) {
-        lo = min(lo, ci[ka]);
-        hi = max(hi, ci[kb - 1]);
-        ++nfl;
-      }
+  if (nf > 0) {
+    int lo = r0, hi = r1 - 1;
+    for (int f = f0 + (int)threadIdx.x; f < f1; f += kPcgThreads) {
+      const int v = fv[f];
+      lo = min(lo, ci[rp[v]]);
+      hi = max(hi, ci[rp[v + 1] - 1]);
     }
-    if (r1 > r0) {
-      atomicMin(&s_lohi[0], lo);
-      atomicMax(&s_lohi[1], hi);
-    }
-    if (nfl) atomicAdd(&s_nfree, nfl);
+    atomicMin(&s_lohi[0], lo);
+    atomicMax(&s_lohi[1], hi);
   }
   __syncthreads();
   const int cmin = s_lohi[0];
-  const int H = r1 > r0 ? s_lohi[1] - cmin + 1 : 0;
-  const int nf = s_nfree;
-  const int ka0 = rp[r0], nblk = rp[r1] - ka0;
-  // shared memory: halo p | resident vectors and row lists | block products
+  const int H = nf > 0 ? s_lohi[1] - cmin + 1 : 0;
+  // shared memory: p over the halo | (resident) the neighbours' old p, the
+  // rows' r, z, dx, q, M^-1 and their vertex ids
   const size_t stage_bytes = align16((size_t)3 * H * sizeof(R));
   const size_t vec_bytes = align16((size_t)18 * nf * sizeof(R));
-  const size_t lst_bytes = align16((size_t)(2 * nf + 1) * sizeof(int));
-  const bool res = r1 > r0 && stage_bytes + vec_bytes + lst_bytes + (size_t)3 * nblk * sizeof(R) <= (size_t)smem_bytes;
-  const bool staged = res || stage_bytes <= (size_t)smem_bytes / 2;
+  const size_t lst_bytes = align16((size_t)nf * sizeof(int));
+  const bool res = nf > 0 && 2 * stage_bytes + vec_bytes + lst_bytes <= (size_t)smem_bytes;
+  const bool staged = res || stage_bytes <= (size_t)smem_bytes;
   R* sp = reinterpret_cast<R*>(s_dyn);
-  const size_t y_off = staged ? stage_bytes + (res ? vec_bytes + lst_bytes : 0) : 0;
-  R* rs = reinterpret_cast<R*>(s_dyn + stage_bytes);  // resident: r, z, dx, q (3 nf each), M^-1 (6 nf)
+  R* sy = reinterpret_cast<R*>(s_dyn + stage_bytes);
+  R* rs = reinterpret_cast<R*>(s_dyn + 2 * stage_bytes);  // resident: r, z, dx, q (3 nf each), M^-1 (6 nf)
   R* zs = rs + 3 * nf;
   R* dxs = zs + 3 * nf;
   R* qs = dxs + 3 * nf;
   R* ms = qs + 3 * nf;
-  int* lst = reinterpret_cast<int*>(s_dyn + stage_bytes + vec_bytes);  // free rows, ascending
-  int* rps = lst + nf;  // their first block (from ka0); rps[nf] = nblk
-  R* sy = reinterpret_cast<R*>(s_dyn + y_off);
-  const int ycap = (int)((smem_bytes - y_off) / (3 * sizeof(R)));
-  // row chunks of at most ycap blocks (a longer row forms a chunk of its own)
-  if (threadIdx.x == 0 && nblk <= ycap) {  // the usual case: one chunk
-    s_chunk[0] = r0;
-    s_chunk[1] = r1;
-    s_nchunk = r1 > r0 ? 1 : 0;
-  } else if (threadIdx.x == 0) {
-    int n = 0, a = r0;
-    s_chunk[0] = r0;
-    while (a < r1 && n < kPcgMaxChunks) {
-      int b = a + 1;
-      while (b < r1 && rp[b + 1] - rp[a] <= ycap) ++b;
-      if (n == kPcgMaxChunks - 1) b = r1;  // last chunk takes the rest
-      s_chunk[++n] = b;
-      a = b;
-    }
-    s_nchunk = n;
-  }
-  if (res) {
-    // list of the free rows in ascending order (ordered compaction)
-    int base = 0;
-    for (int v0 = r0; v0 < r1; v0 += kPcgThreads) {
-      const int v = v0 + (int)threadIdx.x;
-      int ka = 0;
-      bool f = false;
-      if (v < r1) {
-        ka = rp[v];
-        f = rp[v + 1] > ka;
-      }
-      const unsigned m = __ballot_sync(0xffffffffu, f);
-      if (lane == 0) s_wcnt[wid] = __popc(m);
-      __syncthreads();
-      int off = base, tot = 0;
-      for (int w = 0; w < kPcgThreads / 32; ++w) {
-        const int c = s_wcnt[w];
-        off += w < wid ? c : 0;
-        tot += c;
-      }
-      if (f) {
-        const int idx = off + __popc(m & ((1u << lane) - 1u));
-        lst[idx] = v;
-        rps[idx] = ka - ka0;
-      }
-      base += tot;
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) rps[nf] = nblk;
+  int* lst = reinterpret_cast<int*>(s_dyn + 2 * stage_bytes + vec_bytes);  // vertex of each row
+  if (res)
     for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
-      const int v = lst[idx];
+      const int v = fv[f0 + idx];
+      lst[idx] = v;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         rs[i * nf + idx] = r[i * nv + v];
@@ -641,11 +597,9 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
 #pragma unroll
       for (int i = 0; i < 6; ++i) ms[i * nf + idx] = Minv[i * nv + v];
     }
-  }
   // every CTA of the cluster runs (and has set up its shared memory) before
   // the first partials are pushed into it
   cluster.sync();
-  const int nchunk = s_nchunk;
   const double* es = bv.part + L.env_s + kEnvScalars * env;
   if (threadIdx.x == 0) {
     s_at[0] = A::from_double(es[0]);
@@ -665,33 +619,25 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
     // S. direction update over the halo (or the own rows)
     if (res) {
       // the neighbours' halo rows from HBM: z into the halo buffer and the
-      // old p into the (idle) product buffer by asynchronous copies, so
-      // every load of the thread is in flight at once; each thread then
-      // combines the words it copied
+      // old p into the staging buffer by asynchronous copies, so every load
+      // of the thread is in flight at once; each thread then combines the
+      // words it copied
       const int nlo = r0 - cmin, nother = H - (r1 - r0);
-      if (H <= ycap) {
-        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
-          const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
+      for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+        const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
 #pragma unroll
-          for (int i = 0; i < 3; ++i) {
-            cp_async_word(&sp[i * H + l], &z[i * nv + v]);
-            cp_async_word(&sy[i * H + l], &pc[i * nv + v]);
-          }
-        }
-        cp_async_wait_all();
-        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
-          const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) sp[i * H + l] = sp[i * H + l] + beta * sy[i * H + l];
-        }
-      } else {
-        for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
-          const int v = j < nlo ? cmin + j : r1 + (j - nlo);
-#pragma unroll
-          for (int i = 0; i < 3; ++i) sp[i * H + (v - cmin)] = z[i * nv + v] + beta * pc[i * nv + v];
+        for (int i = 0; i < 3; ++i) {
+          cp_async_word(&sp[i * H + l], &z[i * nv + v]);
+          cp_async_word(&sy[i * H + l], &pc[i * nv + v]);
         }
       }
-      // the own free rows from shared memory
+      cp_async_wait_all();
+      for (int j = (int)threadIdx.x; j < nother; j += kPcgThreads) {
+        const int v = j < nlo ? cmin + j : r1 + (j - nlo), l = v - cmin;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) sp[i * H + l] = sp[i * H + l] + beta * sy[i * H + l];
+      }
+      // the own rows from shared memory
       for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
         const int v = lst[idx], l = v - cmin;
 #pragma unroll
@@ -702,41 +648,45 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
         }
       }
     } else {
-      const int s0 = staged ? cmin : r0, s1 = staged ? cmin + H : r1;
-      for (int v = s0 + (int)threadIdx.x; v < s1; v += kPcgThreads) {
-        const bool own = v >= r0 && v < r1;
+      if (staged)
+        for (int v = cmin + (int)threadIdx.x; v < cmin + H; v += kPcgThreads)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const R x = z[i * nv + v] + beta * pc[i * nv + v];
-          if (staged) sp[i * H + (v - cmin)] = x;
-          if (own) pn[i * nv + v] = x;
-        }
+          for (int i = 0; i < 3; ++i) sp[i * H + (v - cmin)] = z[i * nv + v] + beta * pc[i * nv + v];
+      for (int f = f0 + (int)threadIdx.x; f < f1; f += kPcgThreads) {
+        const int v = fv[f];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) pn[i * nv + v] = z[i * nv + v] + beta * pc[i * nv + v];
       }
     }
     __syncthreads();
-    // A. q = A p
+    // A. q = A p: one lane per row of a slice, its blocks in column order
+    // (block kk of the slice's 32 rows is one coalesced load per entry)
     AT pq_loc = A::zero();
-    for (int c = 0; c < nchunk; ++c) {
-      const int ra = s_chunk[c], rb = s_chunk[c + 1];
-      const int ka = rp[ra], kb = rp[rb];
-      const bool fits = kb - ka <= ycap;
-      if (fits) {
-        for (int k0 = ka + (int)threadIdx.x; k0 < kb; k0 += kPcgUnroll<R> * kPcgThreads) {
-          int jj[kPcgUnroll<R>];
-          R Bv[kPcgUnroll<R>][9];
+    for (int s = s0 + wid; s < s1; s += NW) {
+      const int f = 32 * s + lane;
+      const bool row = f < nfree;
+      int v = 0, len = 0;
+      if (row) {
+        v = res ? lst[f - f0] : fv[f];
+        len = rp[v + 1] - rp[v];
+      }
+      const int64_t base = soff[s] + lane;
+      const int W = (soff[s + 1] - soff[s]) >> 5;
+      R a0 = 0, a1 = 0, a2 = 0;
+      for (int k0 = 0; k0 < W; k0 += U) {
+        int jj[U];
+        R Bv[U][9];
 #pragma unroll
-          for (int u = 0; u < kPcgUnroll<R>; ++u) {
-            const int k = k0 + u * kPcgThreads;
-            if (k < kb) {
-              jj[u] = ci[k];
+        for (int u = 0; u < U; ++u)
+          if (k0 + u < len) {
+            const int64_t t = base + 32 * (k0 + u);
+            jj[u] = sci[t];
 #pragma unroll
-              for (int e9 = 0; e9 < 9; ++e9) Bv[u][e9] = val[k + e9 * nb];
-            }
+            for (int e9 = 0; e9 < 9; ++e9) Bv[u][e9] = val[t + e9 * ns];
           }
 #pragma unroll
-          for (int u = 0; u < kPcgUnroll<R>; ++u) {
-            const int k = k0 + u * kPcgThreads;
-            if (k >= kb) break;
+        for (int u = 0; u < U; ++u)
+          if (k0 + u < len) {
             const int j = jj[u];
             R p0, p1, p2;
             if (staged) {
@@ -750,55 +700,23 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
               p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
             }
             const R* B = Bv[u];
-            const int o = k - ka;
-            sy[o] = B[0] * p0 + B[1] * p1 + B[2] * p2;
-            sy[ycap + o] = B[3] * p0 + B[4] * p1 + B[5] * p2;
-            sy[2 * ycap + o] = B[6] * p0 + B[7] * p1 + B[8] * p2;
+            a0 += B[0] * p0 + B[1] * p1 + B[2] * p2;
+            a1 += B[3] * p0 + B[4] * p1 + B[5] * p2;
+            a2 += B[6] * p0 + B[7] * p1 + B[8] * p2;
           }
-        }
-        __syncthreads();
       }
-      if (res) {
-        for (int idx = (int)threadIdx.x; idx < nf; idx += kPcgThreads) {
-          R a0 = 0, a1 = 0, a2 = 0;
-          const int k1 = rps[idx + 1];
-          for (int k = rps[idx]; k < k1; ++k) {
-            a0 += sy[k];
-            a1 += sy[ycap + k];
-            a2 += sy[2 * ycap + k];
-          }
+      if (row) {
+        R pv0, pv1, pv2;
+        if (res) {
+          const int idx = f - f0;
           qs[idx] = a0;
           qs[nf + idx] = a1;
           qs[2 * nf + idx] = a2;
-          const int l = lst[idx] - cmin;
-          pq_loc = A::add(pq_loc, A::add(A::add(A::prod(sp[l], a0), A::prod(sp[H + l], a1)), A::prod(sp[2 * H + l], a2)));
-        }
-        continue;  // one chunk; the block products are next written after two cluster barriers
-      }
-      for (int v = ra + (int)threadIdx.x; v < rb; v += kPcgThreads) {
-        R a0 = 0, a1 = 0, a2 = 0;
-        const int k0 = rp[v], k1 = rp[v + 1];
-        if (fits) {
-          for (int k = k0 - ka; k < k1 - ka; ++k) {
-            a0 += sy[k];
-            a1 += sy[ycap + k];
-            a2 += sy[2 * ycap + k];
-          }
         } else {
-          for (int k = k0; k < k1; ++k) {  // a row longer than the buffer
-            const int j = ci[k];
-            const R p0 = z[j] + beta * pc[j], p1 = z[nv + j] + beta * pc[nv + j];
-            const R p2 = z[2 * nv + j] + beta * pc[2 * nv + j];
-            const R* B = val + k;
-            a0 += B[0] * p0 + B[nb] * p1 + B[2 * nb] * p2;
-            a1 += B[3 * nb] * p0 + B[4 * nb] * p1 + B[5 * nb] * p2;
-            a2 += B[6 * nb] * p0 + B[7 * nb] * p1 + B[8 * nb] * p2;
-          }
+          q[v] = a0;
+          q[nv + v] = a1;
+          q[2 * nv + v] = a2;
         }
-        q[v] = a0;
-        q[nv + v] = a1;
-        q[2 * nv + v] = a2;
-        R pv0, pv1, pv2;
         if (staged) {
           const int l = v - cmin;
           pv0 = sp[l];
@@ -811,7 +729,6 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
         }
         pq_loc = A::add(pq_loc, A::add(A::add(A::prod(pv0, a0), A::prod(pv1, a1)), A::prod(pv2, a2)));
       }
-      __syncthreads();
     }
     cluster_push<R, 1>(&pq_loc, s_red, s_all, 0, cluster, rank, CS);
     cluster.sync();
@@ -850,8 +767,10 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
         }
       }
     } else {
-      for (int v = r0 + (int)threadIdx.x; v < r1; v += kPcgThreads) {
+      for (int f = f0 + (int)threadIdx.x; f < f1; f += kPcgThreads) {
+        const int v = fv[f];
         R rv[3], zv[3];
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
           const R pv = staged ? sp[i * H + (v - cmin)] : pn[i * nv + v];
           dx[i * nv + v] += alpha * pv;
@@ -863,6 +782,7 @@ __global__ void __launch_bounds__(kPcgThreads, 1024 / kPcgThreads)
         zv[0] = m0 * rv[0] + m3 * rv[1] + m5 * rv[2];
         zv[1] = m3 * rv[0] + m1 * rv[1] + m4 * rv[2];
         zv[2] = m5 * rv[0] + m4 * rv[1] + m2 * rv[2];
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
           z[i * nv + v] = zv[i];
           acc[0] = A::add(acc[0], A::prod(rv[i], zv[i]));
