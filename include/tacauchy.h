@@ -195,7 +195,9 @@ tc_status tc_step_batch(tc_env** envs, int32_t n, const tc_pose* targets,
                         tc_status* statuses);
 
 /* Launch shape of the PCG (one thread-block cluster per env):
- * cluster_ctas in {8, 16} CTAs per env, threads in {512, 1024} per CTA.
+ * cluster_ctas in 1 .. 16 CTAs per env (clusters above 8 CTAs are a
+ * non-portable size the GPU may not co-schedule), threads in {512, 1024} per
+ * CTA.
  * Process-wide for the given precision (TC_FP64 or TC_FP32_MIXED), so an
  * env's result does not depend on the batch it runs in; changing it changes
  * the rounding of later steps.  TC_ERR_CAPACITY if the GPU cannot co-schedule
@@ -211,8 +213,8 @@ typedef struct {
 
 /* Autotuner: assemble the Newton systems of the n envs at their current
  * state (positions are not changed), time their PCG solves under every
- * co-schedulable shape, and select the shape with the least device time per
- * CG iteration of one env.  mode 0 launches each env's solve alone, one
+ * co-schedulable shape of {16, 8} CTAs x {1024, 512} threads, and select the
+ * shape with the least device time per CG iteration of one env.  mode 0 launches each env's solve alone, one
  * after another (the latency of one env's solve: requests on their own
  * server workers); mode 1 launches one solve over all n envs (the
  * throughput of a full batch).  results (host, up to max_results entries,

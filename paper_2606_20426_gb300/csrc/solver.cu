@@ -899,7 +899,7 @@ template <class R> PcgShape pcg_shape() {
 }
 
 template <class R> tc_status set_pcg_shape(int cs, int threads) {
-  if ((cs != 8 && cs != 16) || (threads != 512 && threads != 1024)) return TC_ERR_INVALID_ARG;
+  if (cs < 1 || cs > kPcgMaxCluster || (threads != 512 && threads != 1024)) return TC_ERR_INVALID_ARG;
   const PcgShape sh = pcg_probe_any<R>(cs, threads);
   if (sh.coresident <= 0) return TC_ERR_CAPACITY;
   PcgSel<R>& sel = pcg_sel<R>();

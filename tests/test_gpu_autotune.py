@@ -1,7 +1,9 @@
 """PCG launch-shape selection: tc_autotune_pcg times every co-schedulable
 shape on the envs' current Newton systems (latency and throughput modes)
 without moving the envs, selects one, and stepping afterwards still matches
-the oracle; tc_pcg_shape rejects shapes outside {8, 16} x {512, 1024}."""
+the oracle; tc_pcg_shape rejects shapes outside 1..16 CTAs x {512, 1024}
+threads, and clusters of 12 and 3 CTAs (non-power-of-two splits of the rows)
+give the oracle's state too."""
 import numpy as np
 import pytest
 
@@ -51,7 +53,31 @@ def test_autotune_modes_and_step_after():
 def test_shape_argument_checks():
     from paper_2606_20426_gb300 import TcError, pcg_shape
     with pytest.raises(TcError):
-        pcg_shape("fp32", 4, 1024)
+        pcg_shape("fp32", 0, 1024)
+    with pytest.raises(TcError):
+        pcg_shape("fp32", 17, 1024)
     with pytest.raises(TcError):
         pcg_shape("fp32", 16, 256)
     _restore_default()
+
+
+@pytest.mark.parametrize("cs", [12, 3])
+def test_odd_cluster_sizes_match_oracle(cs):
+    """Cluster sizes that are not powers of two split the rows unevenly; the
+    solve still reaches the oracle's state (FP32 mixed path, two steps)."""
+    from paper_2606_20426_gb300 import Env, TcError, pcg_shape
+    s = workloads.small_env(3)
+    try:
+        try:
+            pcg_shape("fp32", cs, 1024)
+        except TcError:
+            pytest.skip(f"a {cs}-CTA cluster of 1024 threads cannot be co-scheduled here")
+        g = Env(s, precision="fp32")
+        ref = Scene(s)
+        for k in range(2):
+            g.step(s["poses"][k])
+            ref.step(s["poses"][k])
+        assert np.abs(g.positions() - ref.x).max() <= 1e-3 * s["depth"]
+        g.close()
+    finally:
+        _restore_default()
