@@ -11,13 +11,13 @@
 //
 // The per-env kernels (k_traction, k_vertex_avg, k_splat, and k_stress in
 // elem.cu) serve the single-env calls.  k_extract does all of it for a whole
-// batch of envs in one cooperative launch: phase 1 streams sigma of every tet
-// and the face pressure and area of every contact face of every env, phase 2
-// averages to contact vertices, phase 3 splats to pixels, with a grid-wide
-// barrier between phases.  Each item goes through the same device functions
-// as in the per-env kernels, so the outputs are the same bit for bit.  (A
-// two-phase form in which every pixel averaged its three vertices itself was
-// measured slower: 45 us against 37 us for 8 bench envs.)
+// batch of envs in one cooperative launch: the face pressure and area of every
+// contact face, then the contact-vertex means, then the pixels, with a
+// grid-wide barrier between these three phases, while sigma of every tet
+// streams in the gaps (see k_extract).  Each item goes through the same
+// device functions as in the per-env kernels, so the outputs are the same bit
+// for bit.  (A two-phase form in which every pixel averaged its three
+// vertices itself was measured slower: 45 us against 37 us for 8 bench envs.)
 #include <algorithm>
 #include <climits>
 #include <mutex>
@@ -241,28 +241,36 @@ TC_D int env_of(const int64_t* row, int n, int64_t i) {
   return lo;
 }
 
-// Grid-wide barrier of a cooperative launch (every block is resident, so the
-// last arrival always comes).  The wait is bounded all the same: after
-// ~2^22 polls a block records the failure in *err and goes on; the host
-// turns it into TC_ERR_CUDA.  Returns false once *err is set.
-TC_D bool grid_barrier(unsigned* bar, int* err) {
+// Grid-wide barrier of a cooperative launch, in two halves so that a block
+// can do independent work between its arrival and its wait.  Every block is
+// resident, so the last arrival always comes; the wait is bounded all the
+// same: after ~2^22 polls a block records the failure in *err and goes on
+// (the host turns it into TC_ERR_CUDA).  grid_arrive returns, in thread 0,
+// the generation to wait past; grid_wait returns false once *err is set.
+TC_D unsigned grid_arrive(unsigned* bar) {
   __syncthreads();
+  unsigned g = 0;
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
+    g = *(volatile unsigned*)(bar + 1);
     __threadfence();
     if (atomicAdd(bar, 1u) == gridDim.x - 1) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
-    } else {
-      int polls = 0;
-      while (*gen == g) {
-        __nanosleep(32);
-        if (++polls > (1 << 22)) {
-          atomicExch(err, 1);
-          break;
-        }
+    }
+  }
+  return g;
+}
+
+TC_D bool grid_wait(unsigned* bar, int* err, unsigned g) {
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    int polls = 0;
+    while (*gen == g) {
+      __nanosleep(32);
+      if (++polls > (1 << 22)) {
+        atomicExch(err, 1);
+        break;
       }
     }
     __threadfence();
@@ -271,58 +279,127 @@ TC_D bool grid_barrier(unsigned* bar, int* err) {
   return *(volatile int*)err == 0;
 }
 
+// Block b's share [lo, hi) of `total` items: contiguous, in whole groups of 32.
+TC_D void block_share(int64_t total, int64_t& lo, int64_t& hi) {
+  const int64_t g = (total + 31) >> 5, b = blockIdx.x, nb = gridDim.x;
+  lo = min(total, 32 * (g * b / nb));
+  hi = min(total, 32 * (g * (b + 1) / nb));
+}
+
+// Walks the items [lo, hi) of one kind with stride blockDim.x and keeps the
+// env of the current item in registers: the env is found by a binary search
+// over the offsets once, then advanced in order (an item's env never comes
+// before the previous one's), and its fields are loaded only when it changes.
+template <class R, class Ctx, class Load, class Body>
+TC_D void for_items(const XBatch<R>& xb, const int64_t* row, int64_t lo, int64_t hi, Load load, Body body) {
+  int64_t i = lo + threadIdx.x;
+  if (i >= hi) return;
+  int e = env_of(row, xb.nenv, i);
+  int64_t beg = row[e], end = row[e + 1];
+  Ctx c = load(xb.env[e]);
+  for (; i < hi; i += blockDim.x) {
+    if (i >= end) {
+      do {
+        ++e;
+        beg = row[e];
+        end = row[e + 1];
+      } while (i >= end);
+      c = load(xb.env[e]);
+    }
+    body(c, (int)(i - beg));
+  }
+}
+
+template <class R> struct SigmaCtx {
+  KinView<R> k;
+  float* sigma;
+};
+template <class R> struct FaceCtx {
+  KinView<R> k;
+  const int32_t* cparent;
+  float *face_p, *face_A;
+};
+struct VertCtx {
+  const int32_t *off, *idx;
+  const float *face_p, *face_A;
+  float* vert_p;
+};
+struct PixCtx {
+  const int32_t *pix_face, *cface_slot;
+  const float *pix_w, *vert_p;
+  float* map;
+  uint8_t* mask;
+  int npix, nfc;
+};
+
+// sigma (K8) of the tets [lo, hi) of the flattened tet range
+template <class R> TC_D void x_sigma(const XBatch<R>& xb, int64_t lo, int64_t hi) {
+  for_items<R, SigmaCtx<R>>(
+      xb, xb.off, lo, hi, [](const XEnv<R>& x) { return SigmaCtx<R>{kin_view(x.v), x.sigma}; },
+      [](const SigmaCtx<R>& c, int el) {
+        R G[3][3], Bm[3][3], s6[6];
+        load_G<R>(c.k, c.k.u, el, c.k.tets[el], G, Bm);
+        R mu, lh;
+        tet_material<R>(c.k, el, mu, lh);
+        cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
+        const int64_t nt = c.k.nt;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) c.sigma[q * nt + el] = (float)s6[q];
+      });
+}
+
+// One cooperative launch over a batch of envs.  Every block takes an equal
+// contiguous share of each kind of item.  Without maps it streams sigma of
+// its tets.  With maps: the face pressure and area of its contact faces
+// (K9); arrive at a grid barrier; a third of its sigma share (K8) while the
+// other blocks arrive; wait; the area-weighted means of its contact vertices
+// (K10a); arrive; the second third of sigma; wait; the pixels (K10b); the
+// last third of sigma.  The barriers order only the face -> vertex -> pixel
+// chain, and the sigma streams fill the time a block would spend waiting.
 template <class R> __global__ void __launch_bounds__(kBlock) k_extract(const XBatch<R> xb, int with_map) {
   const int n = xb.nenv;
   const int64_t* tet_off = xb.off;
   const int64_t* face_off = xb.off + (n + 1);
   const int64_t* cv_off = xb.off + 2 * (n + 1);
   const int64_t* pix_off = xb.off + 3 * (n + 1);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  // phase 1: sigma per tet (K8), face pressure and area per contact face (K9)
-  const int64_t ntet = tet_off[n], nface = face_off[n];
-  for (int64_t i = first; i < ntet + nface; i += stride) {
-    if (i < ntet) {
-      const int e = env_of(tet_off, n, i);
-      const XEnv<R>& x = xb.env[e];
-      const int el = (int)(i - tet_off[e]);
-      R G[3][3], Bm[3][3], s6[6];
-      load_G<R>(x.v, x.v.u, el, x.v.tets[el], G, Bm);
-      R mu, lh;
-      tet_material<R>(x.v, el, mu, lh);
-      cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
-      const int64_t nt = x.v.nt;
-#pragma unroll
-      for (int c = 0; c < 6; ++c) x.sigma[c * nt + el] = (float)s6[c];
-    } else {
-      const int64_t j = i - ntet;
-      const int e = env_of(face_off, n, j);
-      const XEnv<R>& x = xb.env[e];
-      const int f = (int)(j - face_off[e]);
-      R tv[3], nrm[3], pn, len;
-      face_traction<R>(x.v, x.cparent, f, tv, nrm, pn, len);
-      x.face_p[f] = (float)(-pn);
-      x.face_A[f] = (float)(R(0.5) * len);
-    }
+  int64_t slo, shi;
+  block_share(tet_off[n], slo, shi);
+  if (!with_map) {
+    x_sigma<R>(xb, slo, shi);
+    return;
   }
-  if (!with_map) return;
-  if (!grid_barrier(xb.bar, xb.err)) return;
-  // phase 2: area-weighted means at the contact vertices (K10a)
-  const int64_t ncv = cv_off[n];
-  for (int64_t i = first; i < ncv; i += stride) {
-    const int e = env_of(cv_off, n, i);
-    const XEnv<R>& x = xb.env[e];
-    const int s = (int)(i - cv_off[e]);
-    x.vert_p[s] = vertex_mean(s, x.v.cv_face_off, x.v.cv_face_idx, x.face_p, x.face_A);
-  }
-  if (!grid_barrier(xb.bar, xb.err)) return;
-  // phase 3: the pixel map (K10b)
-  const int64_t npx = pix_off[n];
-  for (int64_t i = first; i < npx; i += stride) {
-    const int e = env_of(pix_off, n, i);
-    const XEnv<R>& x = xb.env[e];
-    splat_pixel((int)(i - pix_off[e]), x.npix, x.pix_face, x.pix_w, x.cface_slot, x.v.nfc, x.vert_p, x.map, x.mask);
-  }
+  const int64_t s1 = slo + ((shi - slo) / 3 & ~(int64_t)31), s2 = s1 + ((shi - slo) / 3 & ~(int64_t)31);
+  int64_t lo, hi;
+  // faces (K9)
+  block_share(face_off[n], lo, hi);
+  for_items<R, FaceCtx<R>>(
+      xb, face_off, lo, hi,
+      [](const XEnv<R>& x) { return FaceCtx<R>{kin_view(x.v), x.cparent, x.face_p, x.face_A}; },
+      [](const FaceCtx<R>& c, int f) {
+        R tv[3], nrm[3], pn, len;
+        face_traction<R>(c.k, c.cparent, f, tv, nrm, pn, len);
+        c.face_p[f] = (float)(-pn);
+        c.face_A[f] = (float)(R(0.5) * len);
+      });
+  unsigned g = grid_arrive(xb.bar);
+  x_sigma<R>(xb, slo, s1);
+  if (!grid_wait(xb.bar, xb.err, g)) return;
+  // contact vertices (K10a)
+  block_share(cv_off[n], lo, hi);
+  for_items<R, VertCtx>(
+      xb, cv_off, lo, hi,
+      [](const XEnv<R>& x) { return VertCtx{x.v.cv_face_off, x.v.cv_face_idx, x.face_p, x.face_A, x.vert_p}; },
+      [](const VertCtx& c, int s) { c.vert_p[s] = vertex_mean(s, c.off, c.idx, c.face_p, c.face_A); });
+  g = grid_arrive(xb.bar);
+  x_sigma<R>(xb, s1, s2);
+  if (!grid_wait(xb.bar, xb.err, g)) return;
+  // pixels (K10b)
+  block_share(pix_off[n], lo, hi);
+  for_items<R, PixCtx>(
+      xb, pix_off, lo, hi,
+      [](const XEnv<R>& x) { return PixCtx{x.pix_face, x.cface_slot, x.pix_w, x.vert_p, x.map, x.mask, x.npix, x.v.nfc}; },
+      [](const PixCtx& c, int i) { splat_pixel(i, c.npix, c.pix_face, c.pix_w, c.cface_slot, c.nfc, c.vert_p, c.map, c.mask); });
+  x_sigma<R>(xb, s2, shi);
 }
 
 // Resident blocks per SM of k_extract<R> (for the cooperative grid), once per device.

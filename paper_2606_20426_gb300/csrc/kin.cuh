@@ -28,9 +28,27 @@ template <class R> TC_D void cof3(const R A[3][3], R C[3][3]) {
   C[2][2] = A[0][0] * A[1][1] - A[0][1] * A[1][0];
 }
 
+// The per-env arrays that sigma and the face traction read, held by value
+// (for kernels that loop over the items of many envs and keep one env's
+// fields in registers).  The functions below take it or an EnvView alike.
+template <class R> struct KinView {
+  int nv, nt, nfc;
+  R mu, lam_hat;
+  const R* mat;
+  const int4* tets;
+  const double* X0;
+  const R* Dminv;
+  const R* u;
+  const int32_t* cfaces;
+};
+
+template <class R> TC_D KinView<R> kin_view(const EnvView<R>& e) {
+  return KinView<R>{e.nv, e.nt, e.nfc, e.mu, e.lam_hat, e.mat, e.tets, e.X0, e.Dminv, e.u, e.cfaces};
+}
+
 // Load G = Du Dm^-1 for tet e at displacement u (SoA, stride nv).
-template <class R>
-TC_D void load_G(const EnvView<R>& e, const R* u, int el, int4 t, R G[3][3], R Bm[3][3]) {
+template <class R, class V>
+TC_D void load_G(const V& e, const R* u, int el, int4 t, R G[3][3], R Bm[3][3]) {
   const int nv = e.nv, nt = e.nt;
   const int v[4] = {t.x, t.y, t.z, t.w};
   R Du[3][3];
@@ -62,7 +80,7 @@ template <class R> TC_D Kin<R> kinematics(const R G[3][3]) {
 }
 
 // Material of tet el: its own (mu, lam_hat) when the env is heterogeneous.
-template <class R> TC_D void tet_material(const EnvView<R>& e, int el, R& mu, R& lam_hat) {
+template <class R, class V> TC_D void tet_material(const V& e, int el, R& mu, R& lam_hat) {
   if (e.mat) {
     mu = e.mat[el];
     lam_hat = e.mat[(int64_t)e.nt + el];
@@ -92,9 +110,8 @@ template <class R> TC_D void cauchy6(const R G[3][3], const Kin<R>& k, R mu, R l
 // normal n of the deformed face (stored winding is outward), t = sigma n
 // (Eq. 5), pn = n.sigma.n (Eq. 7's p_n; the pressure is -pn) and the face
 // area len / 2 (len = |e1 x e2|).
-template <class R>
-TC_D void face_traction(const EnvView<R>& e, const int32_t* __restrict__ cparent, int f, R tv[3], R n[3], R& pn,
-                        R& len) {
+template <class R, class V>
+TC_D void face_traction(const V& e, const int32_t* __restrict__ cparent, int f, R tv[3], R n[3], R& pn, R& len) {
   const int nv = e.nv, nfc = e.nfc;
   const int el = cparent[f];
   R G[3][3], Bm[3][3], s6[6];

@@ -233,7 +233,21 @@ def test_extract_batch_equals_per_env_calls(precision):
     one = torch.zeros_like(maps[3])
     extract_batch(envs[3:], None, [one], None)
     assert torch.equal(one, ref[3][1])
-    for g in envs:
+    # copies of the envs (same positions) thirteen to a batch: many env
+    # changes inside every block's share of each kind of item, every other
+    # env sigma only
+    rep = envs + [_gpu_env(cfgs[i % 4], precision) for i in range(4, 13)]
+    for i in range(4, 13):
+        c = cfgs[i % 4]
+        rep[i].set_positions(_smooth_positions(c["X"], amp=5e-5, seed=len(c["X"])))
+    sig3 = [torch.full_like(sig[i % 4], float("nan")) for i in range(13)]
+    map3 = [torch.full_like(maps[i % 4], float("nan")) if i % 2 == 0 else None for i in range(13)]
+    extract_batch(rep, sig3, map3, None)
+    for i in range(13):
+        assert torch.equal(sig3[i], ref[i % 4][0])
+        if map3[i] is not None:
+            assert torch.equal(map3[i], ref[i % 4][1])
+    for g in rep:
         g.close()
 
 
