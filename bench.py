@@ -772,6 +772,11 @@ def run_configs(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     which = args.configs.split(",")
 
+    def pose_at(c, k):
+        # the load poses, then back along the same path to the start (cycled)
+        cyc = c["poses"] + c["poses"][-2::-1] + [c["start_pose"]]
+        return cyc[k % len(cyc)]
+
     def batched(envs, cfgs, steps, first=0):
         outs = [(torch.empty((6, e.info["nt"]), device="cuda"),
                  torch.empty((e.info["H"], e.info["W"]), device="cuda") if e.info["H"] else None) for e in envs]
@@ -780,7 +785,7 @@ def run_configs(args):
             torch.cuda.synchronize()
             a, z = ev(), ev()
             a.record()
-            codes = step_batch(envs, [c["poses"][k] for c in cfgs])
+            codes = step_batch(envs, [pose_at(c, k) for c in cfgs])
             extract_batch(envs, [o[0] for o in outs], [o[1] for o in outs], None)
             z.record()
             z.synchronize()
