@@ -464,7 +464,7 @@ def run_ours(args):
     # ------------- served form (headline): closed loop, one request in flight per env
     clients.closed_loop(args.warmup)
     # requests run on their own workers, so an env's solve is latency-bound
-    tuned = autotune_pcg(served, mode="latency") if args.autotune else None
+    tuned = autotune_pcg(served, mode=args.autotune_mode) if args.autotune else None
     barrier()
     ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     ev_end = [torch.cuda.Event(enable_timing=True) for _ in wstreams]
@@ -813,9 +813,24 @@ def run_configs(args):
         out["c1"] = {"workload": "1,800-tet pad, FP64, 10 quasi-static steps, seeds 0-9, plain form",
                      "env_steps": 100, "value": round(100 / (ms / 1e3), 3),
                      "ms_per_env_step": round(ms / 100, 3),
-                     "newton_per_env_step": sum(e.get_info()["newton_iters"] for e in envs) / 100}
+                     "newton_per_env_step": sum(e.get_info()["newton_iters"] for e in envs) / 100,
+                     "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in envs) / 100}
         for e in envs:
             e.close()
+        # the same pads stepped together: 10 envs in FP64, and 60 envs (seeds
+        # 0-59) in FP64 and in the FP32 mixed mode, as the paper's 60-env
+        # figure is taken
+        for n, prec in ((10, "fp64"), (60, "fp64"), (60, "fp32")):
+            cfgs = [workloads.pad_env(s) for s in range(n)]
+            envs = [Env(c, precision=prec) for c in cfgs]
+            ms = sum(batched(envs, cfgs, 10, 0))
+            out[f"c1_batched_{n}_{prec}"] = {
+                "workload": f"{n} 1,800-tet pads, {prec}, 10 quasi-static steps, tc_step_batch + tc_extract_batch",
+                "env_steps": 10 * n, "value": round(10 * n / (ms / 1e3), 3), "ms_per_batched_step": round(ms / 10, 3),
+                "newton_per_env_step": sum(e.get_info()["newton_iters"] for e in envs) / (10 * n),
+                "pcg_per_env_step": sum(e.get_info()["pcg_iters"] for e in envs) / (10 * n)}
+            for e in envs:
+                e.close()
     if "c3" in which:
         cfgs = workloads.mixed_envs(0)
         envs = [Env(c, precision="fp32") for c in cfgs]
@@ -983,6 +998,8 @@ def main():
     ap.add_argument("--poisson", type=int, default=1, help="also run open-loop Poisson arrivals")
     ap.add_argument("--workers", type=int, default=0, help="server worker threads (0: one per env)")
     ap.add_argument("--autotune", type=int, default=1, help="pick the PCG launch shape on the bench envs first")
+    ap.add_argument("--autotune-mode", default="latency", choices=["latency", "throughput"],
+                    help="PCG autotuner criterion: each env's solve alone, or one launch over all envs")
     ap.add_argument("--poisson-seconds", type=float, default=4.0)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-procs", type=int, default=15,
