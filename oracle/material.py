@@ -20,6 +20,17 @@ Eq. 4 with lam -> lam_hat and 1 -> alpha:
 It vanishes at rest and linearises to 2 mu eps + lam tr(eps) I, i.e. the
 (E, nu) of Eq. 1 exactly.  ``sigma_paper_literal`` evaluates Eq. 4 as printed.
 
+The full stable Neo-Hookean of Smith et al. 2018 (the law Sec. III-B cites,
+with its log term) is the second material law, selected per scene:
+
+    Psi(F) = mu_s/2 (I_C - 3) + lam_s/2 (J - alpha_s)^2 - mu_s/2 log(I_C + 1) - Psi(I),
+    I_C = tr F^T F,  alpha_s = 1 + 3 mu_s / (4 lam_s),
+
+with mu_s = 4/3 mu and lam_s = lam + 5/6 mu from Eq. 1's (mu, lam), so that it
+too is stress-free at rest and linearises to 2 mu eps + lam tr(eps) I.  Its
+stress is P = mu_s (1 - 1/(I_C + 1)) F + lam_s (J - alpha_s) cof F and its
+Cauchy stress sigma = (mu_s/J)(1 - 1/(I_C + 1)) b + lam_s (J - alpha_s) I.
+
 Vectorisation convention for 9x9 tangents: vec(F)[3*i + j] = F[i, j].
 """
 import numpy as np
@@ -119,3 +130,77 @@ def full33(s6):
     S[..., 1, 2] = S[..., 2, 1] = s6[..., 4]
     S[..., 2, 0] = S[..., 0, 2] = s6[..., 5]
     return S
+
+
+# ------------------------------------------------ full stable Neo-Hookean
+def snh_log_params(E, nu):
+    """(mu_s, lam_s, alpha_s) of the full stable Neo-Hookean (log term):
+    Eq. 1's Lame pair mapped by mu_s = 4/3 mu, lam_s = lam + 5/6 mu (the
+    small-strain limit is then linear elasticity with E, nu), and the rest
+    offset alpha_s = 1 + 3 mu_s / (4 lam_s) that makes P(I) vanish."""
+    mu, lam = lame(E, nu)
+    mu_s = 4.0 / 3.0 * mu
+    lam_s = lam + 5.0 / 6.0 * mu
+    return mu_s, lam_s, 1.0 + 0.75 * mu_s / lam_s
+
+
+def energy_density_log(F, mu_s, lam_s, alpha_s):
+    """Psi(F) of the full stable Neo-Hookean, zero at F = I; finite for every
+    F (I_C + 1 >= 1), including inverted and collapsed elements."""
+    J = np.linalg.det(F)
+    Ic = np.einsum("...ij,...ij->...", F, F)
+    rest = 0.5 * lam_s * (1.0 - alpha_s) ** 2 - 0.5 * mu_s * np.log(4.0)
+    return (0.5 * mu_s * (Ic - 3.0) + 0.5 * lam_s * (J - alpha_s) ** 2
+            - 0.5 * mu_s * np.log(Ic + 1.0) - rest)
+
+
+def pk1_log(F, mu_s, lam_s, alpha_s):
+    """P = dPsi/dF = mu_s (1 - 1/(I_C + 1)) F + lam_s (J - alpha_s) cof F."""
+    J = np.linalg.det(F)
+    Ic = np.einsum("...ij,...ij->...", F, F)
+    mu_s, lam_s, alpha_s = (np.asarray(a, dtype=np.float64) for a in (mu_s, lam_s, alpha_s))
+    return ((mu_s * (1.0 - 1.0 / (Ic + 1.0)))[..., None, None] * F
+            + (lam_s * (J - alpha_s))[..., None, None] * cofactor(F))
+
+
+def dpk1_dF_log(F, mu_s, lam_s, alpha_s):
+    """9x9 tangent: mu_s (1 - 1/(I_C + 1)) I + 2 mu_s/(I_C + 1)^2 vec(F) vec(F)^T
+    + lam_s vec(cof F) vec(cof F)^T + lam_s (J - alpha_s) d^2J/dF^2."""
+    F = np.asarray(F)
+    J = np.linalg.det(F)
+    Ic = np.einsum("...ij,...ij->...", F, F)
+    f = F.reshape(F.shape[:-2] + (9,))
+    C = cofactor(F).reshape(F.shape[:-2] + (9,))
+    HJ = np.einsum("ikm,jln,...mn->...ijkl", EPS, EPS, F).reshape(F.shape[:-2] + (9, 9))
+    mu_s, lam_s, alpha_s = (np.asarray(a, dtype=np.float64) for a in (mu_s, lam_s, alpha_s))
+    a = mu_s * (1.0 - 1.0 / (Ic + 1.0))
+    c = 2.0 * mu_s / (Ic + 1.0) ** 2
+    return (a[..., None, None] * np.eye(9) + c[..., None, None] * f[..., :, None] * f[..., None, :]
+            + lam_s[..., None, None] * C[..., :, None] * C[..., None, :]
+            + (lam_s * (J - alpha_s))[..., None, None] * HJ)
+
+
+def cauchy_log(F, mu_s, lam_s, alpha_s):
+    """sigma = J^-1 P F^T = (mu_s/J)(1 - 1/(I_C + 1)) b + lam_s (J - alpha_s) I."""
+    J = np.linalg.det(F)
+    Ic = np.einsum("...ij,...ij->...", F, F)
+    b = np.einsum("...ik,...jk->...ij", F, F)
+    return ((mu_s * (1.0 - 1.0 / (Ic + 1.0)) / J)[..., None, None] * b
+            + (lam_s * (J - alpha_s))[..., None, None] * np.eye(3))
+
+
+# material laws by name: (parameters from (E, nu), Psi, P, dP/dF, sigma)
+LAWS = {
+    "snh": (snh_params, energy_density, pk1, dpk1_dF, cauchy),
+    "snh_log": (snh_log_params, energy_density_log, pk1_log, dpk1_dF_log, cauchy_log),
+}
+
+
+def law_params(law, E, nu):
+    """The three parameters the law's functions take (the rest-stable law:
+    (mu, lam_hat, alpha); the full stable Neo-Hookean: (mu_s, lam_s, alpha_s))."""
+    if law == "snh":
+        mu, _ = lame(E, nu)
+        _, lam_hat, alpha = snh_params(E, nu)
+        return mu, lam_hat, alpha
+    return snh_log_params(E, nu)

@@ -90,14 +90,22 @@ class Scene:
         self.X, self.T = X, T
         self.nv, self.nt = X.shape[0], T.shape[0]
         self.E, self.nu, self.rho = m["E"], m["nu"], m["density"]
+        # material law: "snh" (the rest-stable reading, default) or "snh_log"
+        # (the full stable Neo-Hookean with its log term)
+        self.law = m.get("model", "snh")
+        if self.law not in mat.LAWS:
+            raise ValueError(f"unknown material law {self.law!r}")
+        _, self._psi, self._pk1, self._dpk1, self._cauchy = mat.LAWS[self.law]
         self.mu, self.lam = mat.lame(self.E, self.nu)
         _, self.lam_hat, self.alpha = mat.snh_params(self.E, self.nu)
+        self.mp = mat.law_params(self.law, self.E, self.nu)
         if m.get("per_tet") is not None:
-            # heterogeneous material: (E, nu) per tet, Eq. 1 and the rest-stable
+            # heterogeneous material: (E, nu) per tet, Eq. 1 and the law's
             # parameters per tet (the scene's E still sets the default kappa)
             pt = np.asarray(m["per_tet"], dtype=np.float64).reshape(-1, 2)
             self.mu, self.lam = mat.lame(pt[:, 0], pt[:, 1])
             _, self.lam_hat, self.alpha = mat.snh_params(pt[:, 0], pt[:, 1])
+            self.mp = mat.law_params(self.law, pt[:, 0], pt[:, 1])
         self.Dminv, self.vol = msh.rest_shape(X, T)
         self.Dfx = msh.dF_dx(self.Dminv)
         self.h = float(o["dt"])
@@ -233,13 +241,13 @@ class Scene:
     # ------------------------------------------------------------- energy
     def elastic(self, x, need_hess=True):
         F = msh.deformation_gradient(x, self.T, self.Dminv)
-        psi = mat.energy_density(F, self.mu, self.lam_hat, self.alpha)
+        psi = self._psi(F, *self.mp)
         Ee = float(np.sum(self.vol * psi))
         if not need_hess:
             return Ee, None, None
-        P = mat.pk1(F, self.mu, self.lam_hat, self.alpha).reshape(-1, 9)
+        P = self._pk1(F, *self.mp).reshape(-1, 9)
         ge = self.vol[:, None] * np.einsum("nki,nk->ni", self.Dfx, P)
-        H9 = mat.project_psd(mat.dpk1_dF(F, self.mu, self.lam_hat, self.alpha))
+        H9 = mat.project_psd(self._dpk1(F, *self.mp))
         He = self.vol[:, None, None] * np.einsum("nki,nkl,nlj->nij", self.Dfx, H9, self.Dfx)
         return Ee, ge, He
 
@@ -405,7 +413,7 @@ class Scene:
 
     def stress(self, x=None):
         """Eq. 4 per tet, six components (xx, yy, zz, xy, yz, zx)."""
-        return mat.sym6(mat.cauchy(self.deformation(x), self.mu, self.lam_hat, self.alpha))
+        return mat.sym6(self._cauchy(self.deformation(x), *self.mp))
 
     def traction(self, x=None, sigma6=None):
         """Algorithm 1 over contact faces: unit outward normal of the deformed
