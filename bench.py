@@ -42,6 +42,11 @@ WORKLOAD = ("gelsight-like graded pad 18x24x4 mm, ~60k tets, sphere/cylinder/box
 NCU_TRAFFIC = {"k_pcg_cluster": {"bytes_per_unit": (56069376 + 892672) / 1458, "sha": "be5966d38386d6c0"}}
 
 
+# L2 -> SM read ceiling per SM (ncu's peak of l1tex__m_xbar2l1tex_read_bytes
+# on GB300: 19,456 B per cycle over 152 SMs)
+L2_BYTES_PER_SM_CYCLE = 128.0
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -590,6 +595,19 @@ def run_ours(args):
     peak, peak_kind = peaks()
     top, kernel_table = _kernel_table(prof)
     roof = _roofline(top, infos, pcg_by_env, peak, peak_kind)
+    if roof and roof["kernel"] == "k_pcg_cluster" and tuned:
+        # the same kernel against the per-SM L2 -> SM read ceiling (the PCG's
+        # working set stays in L2): one env's CG iteration alone, bytes over
+        # the autotuner's time per iteration of the chosen shape, per SM of
+        # its cluster
+        best = min(tuned, key=lambda t: t["us_per_env_iter"])
+        ach = pcg_iteration_bytes(infos[0]) / (best["us_per_env_iter"] * 1e-6) / best["cluster_ctas"] / 1e9
+        ceil = L2_BYTES_PER_SM_CYCLE * (clocks.get("sm_mhz") or 2070.0) * 1e6 / 1e9
+        roof["l2_per_sm"] = {"achieved": round(ach, 1), "peak": round(ceil, 1), "unit": "GB/s", "frac": round(ach / ceil, 4),
+                             "peak_source": "ncu l1tex__m_xbar2l1tex_read_bytes.sum.peak_sustained (19,456 B/cycle) "
+                                            "/ 152 SMs x the median SM clock under load",
+                             "basis": f"{best['cluster_ctas']}-CTA cluster, {best['us_per_env_iter']:.2f} us per CG "
+                                      f"iteration of one env alone"}
     steps_done = max(1, sum(e.get_info()["steps"] for e in batched))
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
