@@ -65,13 +65,26 @@ enum { TC_FP64 = 0, TC_FP32_MIXED = 1 };
  * (det[X1-X0, X2-X0, X3-X0] > 0, else TC_ERR_INVALID_MESH). */
 typedef struct { const double* X; int32_t nv; const int32_t* tets; int32_t nt; } tc_mesh;
 
+/* Material laws (Sec. III-B): TC_MODEL_SNH, the rest-stable Neo-Hookean
+ * Psi = mu/2 (I_C - 3) + lam_hat/2 (J - alpha)^2 - mu^2/(2 lam_hat) with
+ * lam_hat = lam + mu, alpha = 1 + mu/lam_hat (the paper's Eq. 2 / Eq. 4
+ * corrected to a stress-free rest state); TC_MODEL_SNH_LOG, the full stable
+ * Neo-Hookean of Smith et al. 2018 that Sec. III-B cites,
+ * Psi = mu_s/2 (I_C - 3) + lam_s/2 (J - alpha_s)^2 - mu_s/2 log(I_C + 1) - Psi(I)
+ * with mu_s = 4/3 mu, lam_s = lam + 5/6 mu, alpha_s = 1 + 3 mu_s/(4 lam_s).
+ * Both take Eq. 1's (mu, lam) and linearise to the same linear elasticity. */
+enum { TC_MODEL_SNH = 0, TC_MODEL_SNH_LOG = 1 };
+
 /* Material (Sec. III-B, Eq. 1).  Young's modulus E (Pa), Poisson ratio nu in
  * (-1, 0.5), density (kg/m^3, used only when dt > 0).  per_tet_E_nu: NULL
  * (homogeneous) or host nt x 2 row-major (E_t, nu_t) per tet, for
  * heterogeneous gels such as the dual-layer 9DTact pad of Sec. IV-D; each tet
- * then takes Eq. 1 and the rest-stable parameters from its own pair (E and nu
- * above still set the default barrier stiffness).  Copied at create time. */
-typedef struct { double E, nu, density; const double* per_tet_E_nu; } tc_material;
+ * then takes Eq. 1 and the law's parameters from its own pair (E and nu
+ * above still set the default barrier stiffness).  Copied at create time.
+ * model: TC_MODEL_SNH (0, the default of a zero-initialised struct) or
+ * TC_MODEL_SNH_LOG; another value gives TC_ERR_INVALID_ARG.  The
+ * standalone tc_stress_from_F evaluates TC_MODEL_SNH only. */
+typedef struct { double E, nu, density; const double* per_tet_E_nu; int32_t model; } tc_material;
 
 /* Solver options.
  *   dhat        IPC barrier distance (m), Sec. III-B.

@@ -157,17 +157,20 @@ void release_working(Env& env) {
 // rest-stable lam_hat = lam + mu), uploaded as 2 x nt in the kernel type.
 template <class R> static tc_status upload_material(Env& env, const double* E_nu) {
   const int64_t nt = env.nt;
-  std::vector<R> h(2 * (size_t)nt);
+  const bool lg = env.model == TC_MODEL_SNH_LOG;
+  const int planes = lg ? 3 : 2;
+  std::vector<R> h(planes * (size_t)nt);
   for (int64_t t = 0; t < nt; ++t) {
     const double E = E_nu[2 * t], nu = E_nu[2 * t + 1];
     const double mu = E / (2.0 * (1.0 + nu));
     const double lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
     h[t] = (R)mu;
-    h[nt + t] = (R)(lam + mu);
+    h[nt + t] = (R)(lg ? lam + 5.0 / 6.0 * mu : lam + mu);
+    if (lg) h[2 * nt + t] = (R)(mu / 3.0);
   }
-  env.mat_tet = env.arena.alloc<R>(2 * nt);
+  env.mat_tet = env.arena.alloc<R>(planes * nt);
   if (!env.mat_tet) return TC_ERR_OOM;
-  TC_CHECK(cudaMemcpyAsync(env.mat_tet, h.data(), sizeof(R) * 2 * nt, cudaMemcpyHostToDevice, env.stream));
+  TC_CHECK(cudaMemcpyAsync(env.mat_tet, h.data(), sizeof(R) * planes * nt, cudaMemcpyHostToDevice, env.stream));
   TC_CHECK(cudaStreamSynchronize(env.stream));
   return TC_OK;
 }
@@ -351,6 +354,7 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   if (!(material->E > 0) || !(material->nu > -1.0 && material->nu < 0.5) || !(opts->dhat > 0))
     return TC_ERR_INVALID_ARG;
   if (opts->precision != TC_FP64 && opts->precision != TC_FP32_MIXED) return TC_ERR_INVALID_ARG;
+  if (material->model != TC_MODEL_SNH && material->model != TC_MODEL_SNH_LOG) return TC_ERR_INVALID_ARG;
   if (opts->dt > 0 && !(material->density > 0)) return TC_ERR_INVALID_ARG;
   for (int64_t i = 0; i < 4 * (int64_t)mesh->nt; ++i)
     if (mesh->tets[i] < 0 || mesh->tets[i] >= mesh->nv) return TC_ERR_INVALID_MESH;
@@ -377,7 +381,17 @@ tc_status tc_create_scene(const tc_mesh* mesh, const tc_material* material, cons
   env.rho = material->density;
   env.mu = env.E / (2.0 * (1.0 + env.nu));                          // Eq. 1
   env.lam = env.E * env.nu / ((1.0 + env.nu) * (1.0 - 2.0 * env.nu));  // Eq. 1
-  env.lam_hat = env.lam + env.mu;
+  env.model = material->model;
+  if (env.model == TC_MODEL_SNH_LOG) {
+    // full stable Neo-Hookean as the rest-stable form with (mu, lam_hat) =
+    // (3 mu_s / 4, lam_s) = (mu, lam + 5/6 mu) plus the log-term part with
+    // coefficient mu_s / 4 = mu / 3
+    env.lam_hat = env.lam + 5.0 / 6.0 * env.mu;
+    env.kh = env.mu / 3.0;
+  } else {
+    env.lam_hat = env.lam + env.mu;
+    env.kh = 0.0;
+  }
   env.alpha = 1.0 + env.mu / env.lam_hat;
   env.dhat = opts->dhat;
   env.kappa = opts->kappa;

@@ -13,7 +13,12 @@
 // The tangent dP/dF is made PSD with its closed-form eigensystem in the
 // singular basis F = U S V^T: twist modes mu + lam_hat (J - alpha) s_k,
 // flip modes mu - lam_hat (J - alpha) s_k, and three scaling modes from the
-// 3x3 Hessian of Psi in the singular values.  Negative eigenvalues are
+// 3x3 Hessian of Psi in the singular values.  The full stable Neo-Hookean
+// (log term, TC_MODEL_SNH_LOG) is this form with (mu, lam_hat) = (3 mu_s/4,
+// lam_s) plus 2 kh h(x), kh = mu_s/4, h(x) = x - log(1 + x), x = (I_C - 3)/4:
+// P gains kh x/(1+x) F, and the tangent kh x/(1+x) I (every mode) plus
+// kh/(2 (1+x)^2) vec F vec F^T (the scaling modes: s_a s_b in the singular
+// basis).  Negative eigenvalues are
 // replaced by their absolute values (absolute eigenvalue filtering, Chen et
 // al. 2024): under compression the twist modes turn negative, and clamping
 // them to zero leaves the projected Newton method converging only linearly.
@@ -24,11 +29,13 @@
 
 namespace tc {
 
-template <class R> TC_D R psi_of(const R G[3][3], const Kin<R>& k, R mu, R lam_hat) {
+template <class R> TC_D R psi_of(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R kh) {
   R g2 = 0;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) g2 += G[i][j] * G[i][j];
-  return R(0.5) * mu * g2 - mu * (k.m2 + k.detG) + R(0.5) * lam_hat * k.Jm1 * k.Jm1;
+  R psi = R(0.5) * mu * g2 - mu * (k.m2 + k.detG) + R(0.5) * lam_hat * k.Jm1 * k.Jm1;
+  if (kh != R(0)) psi += R(2) * kh * h_log<R>(R(0.25) * (R(2) * k.trG + g2));
+  return psi;
 }
 
 // 3x3 symmetric Jacobi eigen (A overwritten by eigenvalues on the diagonal).
@@ -73,13 +80,21 @@ template <class R> TC_D void eig3(R A[3][3], R V[3][3]) {
 // Filtered tangent H9 = sum_m |lambda_m| q_m q_m^T in packed upper storage,
 // vec index 3 i + j.
 template <class R>
-TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R H[45]) {
+TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R kh, R H[45]) {
   // S' = F^T F - I = G + G^T + G^T G: same eigenvectors as F^T F, accurate
   // s - 1 = c' / (1 + s) at small strain.
   R A[3][3], V[3][3];
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
       A[i][j] = G[i][j] + G[j][i] + G[0][i] * G[0][j] + G[1][i] * G[1][j] + G[2][i] * G[2][j];
+  // log term: c1 on every mode, c2 s_a s_b on the scaling block (x = tr S' / 4)
+  R c1 = R(0), c2 = R(0);
+  if (kh != R(0)) {
+    const R x = R(0.25) * (A[0][0] + A[1][1] + A[2][2]);
+    const R ix = R(1) / (R(1) + x);
+    c1 = kh * x * ix;
+    c2 = R(0.5) * kh * ix * ix;
+  }
   eig3<R>(A, V);
   R c[3] = {A[0][0], A[1][1], A[2][2]};
   // sort descending (columns of V follow)
@@ -133,8 +148,12 @@ TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R H[45]
   for (int pr = 0; pr < 3; ++pr) {
     const int i = pr == 2 ? 1 : 0, j = pr == 0 ? 1 : 2, kk = 3 - i - j;
     // twist: mu + cJ s_k = -mu (s_k - 1) + lam_hat (J - 1) s_k
-    const R lt = -mu * sm1[kk] + lam_hat * k.Jm1 * s[kk];
-    const R lf = R(2) * mu + mu * sm1[kk] - lam_hat * k.Jm1 * s[kk];  // mu - cJ s_k
+    R lt = -mu * sm1[kk] + lam_hat * k.Jm1 * s[kk];
+    R lf = R(2) * mu + mu * sm1[kk] - lam_hat * k.Jm1 * s[kk];  // mu - cJ s_k
+    if (kh != R(0)) {
+      lt += c1;
+      lf += c1;
+    }
 #pragma unroll
     for (int mode = 0; mode < 2; ++mode) {
       const R lam = fabs(mode == 0 ? lt : lf);
@@ -159,6 +178,7 @@ TC_D void psd_tangent(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R H[45]
     for (int b = 0; b < 3; ++b) {
       if (a == b) As[a][b] = mu + lam_hat * Js[a] * Js[a];
       else As[a][b] = lam_hat * Js[a] * Js[b] + cJ * s[3 - a - b];
+      if (kh != R(0)) As[a][b] += (a == b ? c1 : R(0)) + c2 * s[a] * s[b];
     }
   eig3<R>(As, Av);
 #pragma unroll
@@ -194,9 +214,9 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
     load_G<R>(e, u, el, t, G, Bm);
     const Kin<R> k = kinematics<R>(G);
     const R V = e.vol[el];
-    R mu, lh;
-    tet_material<R>(e, el, mu, lh);
-    energy = (double)(V * psi_of<R>(G, k, mu, lh));
+    R mu, lh, kh;
+    tet_material<R>(e, el, mu, lh, kh);
+    energy = (double)(V * psi_of<R>(G, k, mu, lh, kh));
     if (HESS) {
       const int nt = e.nt;
       // P = mu (G + G^T - trG I - cof G) + lam_hat (J-1) cof F
@@ -206,6 +226,16 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
           const R cofF = (i == j ? R(1) + k.trG : R(0)) - G[j][i] + k.cG[i][j];
           P[i][j] = mu * (G[i][j] + G[j][i] - (i == j ? k.trG : R(0)) - k.cG[i][j]) + lh * k.Jm1 * cofF;
         }
+      if (kh != R(0)) {
+        // log term: + kh x/(1+x) F, x = (2 tr G + |G|^2)/4
+        R g2 = 0;
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) g2 += G[i][j] * G[i][j];
+        const R x = R(0.25) * (R(2) * k.trG + g2);
+        const R c = kh * (x / (R(1) + x));
+        for (int i = 0; i < 3; ++i)
+          for (int j = 0; j < 3; ++j) P[i][j] += c * ((i == j ? R(1) : R(0)) + G[i][j]);
+      }
       // gradient: g_a = V P n_a, n_a = row (a-1) of Dm^-1, n_0 = -sum
       R gs[4][3];
       for (int i = 0; i < 3; ++i) {
@@ -220,7 +250,7 @@ __global__ void __launch_bounds__(kBlock) k_elem(const BatchView<R> bv, PartLayo
       for (int a = 0; a < 4; ++a)
         for (int i = 0; i < 3; ++i) e.eslot[(int64_t)(3 * a + i) * nt + el] = gs[a][i];
       R H[45];
-      psd_tangent<R>(G, k, mu, lh, H);
+      psd_tangent<R>(G, k, mu, lh, kh, H);
       // stiffness blocks K_ab[i][k] = V sum_jl H[(i,j),(k,l)] n_a[j] n_b[l]
       // for corners a <= b (n_a: gradient of corner a's shape function)
       R n[4][3];
@@ -273,9 +303,9 @@ __global__ void __launch_bounds__(kBlock) k_stress(const EnvView<R> e, const R* 
   R G[3][3], Bm[3][3];
   load_G<R>(e, u, el, t, G, Bm);
   R s6[6];
-  R mu, lh;
-  tet_material<R>(e, el, mu, lh);
-  cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
+  R mu, lh, kh;
+  tet_material<R>(e, el, mu, lh, kh);
+  cauchy6<R>(G, kinematics<R>(G), mu, lh, kh, s6);
   const int64_t nt = e.nt;
 #pragma unroll
   for (int c = 0; c < 6; ++c) sig[c * nt + el] = (float)s6[c];

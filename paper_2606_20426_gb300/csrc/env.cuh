@@ -58,8 +58,9 @@ TC_HD int64_t kblk_size(int nt) { return (int64_t)90 * ((nt + kKblkGroup - 1) / 
 // Everything a kernel needs, passed by value.
 template <class R> struct EnvView {
   int nv, nt, nfc, nec, nvc, ind_nv, ind_nf, ind_ne, npix;
-  R mu, lam_hat, alpha;       // material (rest-stable Neo-Hookean)
-  const R* mat;               // per-tet (mu, lam_hat) as 2 x nt, or null (homogeneous)
+  R mu, lam_hat, alpha;       // material (rest-stable Neo-Hookean part)
+  R kh;                       // log-term coefficient mu_s / 4 (full stable Neo-Hookean) or 0
+  const R* mat;               // per-tet (mu, lam_hat[, kh]) as 2 (3 with the log law) x nt, or null
   R inv_h2;                   // 1/dt^2 (dynamic) or 0
   double dhat, kappa;
   int pcg_max;                // this env's PCG iteration cap
@@ -226,6 +227,8 @@ struct Env {
   int ind_nv = 0, ind_nf = 0, ind_ne = 0, H = 0, W = 0;
   // material / options
   double E = 0, nu = 0, rho = 0, mu = 0, lam = 0, lam_hat = 0, alpha = 0;
+  int model = 0;              // TC_MODEL_SNH or TC_MODEL_SNH_LOG
+  double kh = 0;              // log-term coefficient (mu_s / 4) of the full stable Neo-Hookean, else 0
   double dhat = 0, kappa = 0, dt = 0, rtol = 1e-6, gabs = 0, ptol = 0;
   int newton_max = 1024, pcg_max = 1000, thick_axis = 2;
   bool dynamic = false;
@@ -280,7 +283,7 @@ struct Env {
   int32_t* grid_items[3] = {nullptr, nullptr, nullptr};
   float* prim_box[3] = {nullptr, nullptr, nullptr};
   // typed fields (one of the two sets is allocated)
-  void* mat_tet = nullptr;    // per-tet (mu, lam_hat), 2 x nt, or null
+  void* mat_tet = nullptr;    // per-tet (mu, lam_hat[, kh]), 2 (3 with the log law) x nt, or null
   void* Dminv = nullptr;
   void* vol = nullptr;
   void* mass = nullptr;
@@ -327,7 +330,7 @@ template <class R> EnvView<R> Env::view() const {
   EnvView<R> e{};
   e.nv = nv; e.nt = nt; e.nfc = nfc; e.nec = nec; e.nvc = nvc;
   e.ind_nv = ind_nv; e.ind_nf = ind_nf; e.ind_ne = ind_ne; e.npix = H * W;
-  e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha;
+  e.mu = (R)mu; e.lam_hat = (R)lam_hat; e.alpha = (R)alpha; e.kh = (R)kh;
   e.mat = (const R*)mat_tet;
   e.inv_h2 = dynamic ? (R)(1.0 / (dt * dt)) : (R)0;
   e.dhat = dhat; e.kappa = kappa; e.pcg_max = pcg_max;

@@ -339,9 +339,9 @@ template <class R> TC_D void x_sigma(const XBatch<R>& xb, int64_t lo, int64_t hi
       [](const SigmaCtx<R>& c, int el) {
         R G[3][3], Bm[3][3], s6[6];
         load_G<R>(c.k, c.k.u, el, c.k.tets[el], G, Bm);
-        R mu, lh;
-        tet_material<R>(c.k, el, mu, lh);
-        cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
+        R mu, lh, kh;
+        tet_material<R>(c.k, el, mu, lh, kh);
+        cauchy6<R>(G, kinematics<R>(G), mu, lh, kh, s6);
         const int64_t nt = c.k.nt;
 #pragma unroll
         for (int q = 0; q < 6; ++q) c.sigma[q * nt + el] = (float)s6[q];

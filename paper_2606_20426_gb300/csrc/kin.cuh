@@ -7,6 +7,10 @@
 // Everything is written in terms of G = F - I = Du Dm^-1:
 //   J - 1 = tr G + m2(G) + det G           (m2: sum of principal 2x2 minors)
 //   sigma = (mu/J)(G + G^T + G G^T) + (lam_hat - mu/J)(J - 1) I      (Eq. 4)
+// The full stable Neo-Hookean (log term) is that form with (mu, lam_hat) =
+// (3 mu_s/4, lam_s) plus the part 2 kh h(x), kh = mu_s/4, h(x) = x - log(1 + x),
+// x = (I_C - 3)/4 = tr(b - I)/4, whose first-order terms cancel those of the
+// rest: sigma gains (kh/J) x/(1 + x) b.
 #pragma once
 #include "env.cuh"
 
@@ -33,7 +37,7 @@ template <class R> TC_D void cof3(const R A[3][3], R C[3][3]) {
 // fields in registers).  The functions below take it or an EnvView alike.
 template <class R> struct KinView {
   int nv, nt, nfc;
-  R mu, lam_hat;
+  R mu, lam_hat, kh;
   const R* mat;
   const int4* tets;
   const double* X0;
@@ -43,7 +47,7 @@ template <class R> struct KinView {
 };
 
 template <class R> TC_D KinView<R> kin_view(const EnvView<R>& e) {
-  return KinView<R>{e.nv, e.nt, e.nfc, e.mu, e.lam_hat, e.mat, e.tets, e.X0, e.Dminv, e.u, e.cfaces};
+  return KinView<R>{e.nv, e.nt, e.nfc, e.mu, e.lam_hat, e.kh, e.mat, e.tets, e.X0, e.Dminv, e.u, e.cfaces};
 }
 
 // Load G = Du Dm^-1 for tet e at displacement u (SoA, stride nv).
@@ -79,19 +83,36 @@ template <class R> TC_D Kin<R> kinematics(const R G[3][3]) {
   return k;
 }
 
-// Material of tet el: its own (mu, lam_hat) when the env is heterogeneous.
-template <class R, class V> TC_D void tet_material(const V& e, int el, R& mu, R& lam_hat) {
+// Material of tet el: its own (mu, lam_hat, kh) when the env is
+// heterogeneous (kh, the log-term coefficient, is 0 for the rest-stable law).
+template <class R, class V> TC_D void tet_material(const V& e, int el, R& mu, R& lam_hat, R& kh) {
   if (e.mat) {
     mu = e.mat[el];
     lam_hat = e.mat[(int64_t)e.nt + el];
+    kh = e.kh != R(0) ? e.mat[2 * (int64_t)e.nt + el] : R(0);
   } else {
     mu = e.mu;
     lam_hat = e.lam_hat;
+    kh = e.kh;
   }
 }
 
+// h(x) = x - log(1 + x) for x >= -3/4 without cancellation near 0: with
+// u = x / (2 + x), log(1 + x) = 2 atanh(u) = 2 (u + u^3/3 + u^5/5 + ...) and
+// x - 2u = u x, so h = u x - 2 u^3 (1/3 + u^2/5 + ... + u^16/19) (|u| < 1/7
+// for |x| < 1/4: the dropped terms are below 1e-16 relative); further out
+// the direct difference loses at most a factor 10 to cancellation.
+template <class R> TC_D R h_log(R x) {
+  if (fabs(x) >= R(0.25)) return x - log1p(x);
+  const R u = x / (R(2) + x), u2 = u * u;
+  R s = R(1) / R(19);
+#pragma unroll
+  for (int k = 17; k >= 3; k -= 2) s = R(1) / R(k) + u2 * s;
+  return u * x - R(2) * u * u2 * s;
+}
+
 // Cauchy stress (xx, yy, zz, xy, yz, zx) from G and its kinematics.
-template <class R> TC_D void cauchy6(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R s6[6]) {
+template <class R> TC_D void cauchy6(const R G[3][3], const Kin<R>& k, R mu, R lam_hat, R kh, R s6[6]) {
   const R muJ = mu / k.J;
   const R iso = (lam_hat - muJ) * k.Jm1;
   R bI[3][3];  // b - I = G + G^T + G G^T
@@ -104,6 +125,17 @@ template <class R> TC_D void cauchy6(const R G[3][3], const Kin<R>& k, R mu, R l
   s6[3] = muJ * bI[0][1];
   s6[4] = muJ * bI[1][2];
   s6[5] = muJ * bI[2][0];
+  if (kh != R(0)) {
+    // log term: (kh/J) x/(1+x) b, x = tr(b - I)/4
+    const R x = R(0.25) * (bI[0][0] + bI[1][1] + bI[2][2]);
+    const R c = kh / k.J * (x / (R(1) + x));
+    s6[0] += c * (R(1) + bI[0][0]);
+    s6[1] += c * (R(1) + bI[1][1]);
+    s6[2] += c * (R(1) + bI[2][2]);
+    s6[3] += c * bI[0][1];
+    s6[4] += c * bI[1][2];
+    s6[5] += c * bI[2][0];
+  }
 }
 
 // Algorithm 1 on contact face f: sigma of its parent tet, the unit outward
@@ -116,9 +148,9 @@ TC_D void face_traction(const V& e, const int32_t* __restrict__ cparent, int f, 
   const int el = cparent[f];
   R G[3][3], Bm[3][3], s6[6];
   load_G<R>(e, e.u, el, e.tets[el], G, Bm);
-  R mu, lh;
-  tet_material<R>(e, el, mu, lh);
-  cauchy6<R>(G, kinematics<R>(G), mu, lh, s6);
+  R mu, lh, kh;
+  tet_material<R>(e, el, mu, lh, kh);
+  cauchy6<R>(G, kinematics<R>(G), mu, lh, kh, s6);
   const int a = e.cfaces[f], b = e.cfaces[nfc + f], c = e.cfaces[2 * nfc + f];
   R e1[3], e2[3];
   for (int d = 0; d < 3; ++d) {

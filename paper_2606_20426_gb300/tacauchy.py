@@ -42,7 +42,11 @@ class Mesh(ctypes.Structure):
 
 class Material(ctypes.Structure):
     _fields_ = [("E", ctypes.c_double), ("nu", ctypes.c_double), ("density", ctypes.c_double),
-                ("per_tet_E_nu", ctypes.c_void_p)]
+                ("per_tet_E_nu", ctypes.c_void_p), ("model", ctypes.c_int32)]
+
+
+# material laws (tc_material.model)
+MODELS = {"snh": 0, "snh_log": 1}
 
 
 class SceneOpts(ctypes.Structure):
@@ -245,7 +249,11 @@ class Env:
         if m.get("per_tet") is not None:
             per_tet = np.ascontiguousarray(m["per_tet"], dtype=np.float64).reshape(-1, 2)
         self._keep = self._keep + (per_tet,)
-        mat = Material(m["E"], m["nu"], m["density"], per_tet.ctypes.data if per_tet is not None else None)
+        law = m.get("model", "snh")
+        if law not in MODELS:
+            raise ValueError(f"unknown material law {law!r}")
+        mat = Material(m["E"], m["nu"], m["density"], per_tet.ctypes.data if per_tet is not None else None,
+                       MODELS[law])
         opts = SceneOpts(o["dhat"], o.get("kappa", 0.0), o.get("dt", 0.0), o.get("newton_rtol", 1e-6),
                          o.get("newton_max", 1024), o.get("pcg_max", 1000), prec, o.get("contact_axis", -1),
                          o.get("friction_mu", 0.0), o.get("friction_eps_v", 0.01))
